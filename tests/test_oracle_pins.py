@@ -1,0 +1,431 @@
+"""Pins for the CPU oracle: each test ties the oracle to something other than
+itself -- closed forms, numbers the paper prints, invariants the paper states,
+library routines for special cases, or brute force on tiny inputs -- so that a
+dropped term, a wrong sign or index, or a transposed operand fails here."""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2008_07437_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_printed_values.json")
+
+
+# ---------------------------------------------------------------- K_nu -----
+
+@pytest.mark.parametrize("x", [1e-3, 0.01, 0.1, 0.5, 1.0, 1.9, 2.0, 2.1, 5.0, 13.0, 40.0, 120.0, 600.0])
+def test_besselk_half_integer_closed_forms(x):
+    # K_{1/2}(x) = sqrt(pi/(2x)) e^-x, K_{3/2} = K_{1/2}(1 + 1/x), K_{5/2} = K_{1/2}(1 + 3/x + 3/x^2)
+    base = math.sqrt(math.pi / (2 * x))
+    exact = {0.5: base, 1.5: base * (1 + 1 / x), 2.5: base * (1 + 3 / x + 3 / x ** 2)}
+    for nu, val in exact.items():
+        got = oracle.besselk_scaled(nu, x)
+        assert got == pytest.approx(val, rel=2e-15), (nu, x)
+
+
+@pytest.mark.parametrize("nu", [0.1, 0.25, 0.75, 1.0, 1.25, 2.2])
+@pytest.mark.parametrize("x", [0.002, 0.3, 1.0, 3.0, 17.0, 80.0])
+def test_besselk_recurrence(nu, x):
+    # K_{nu+1}(x) = K_{nu-1}(x) + (2 nu / x) K_nu(x)
+    lhs = oracle.besselk_scaled(nu + 1, x)
+    rhs = oracle.besselk_scaled(abs(nu - 1), x) + 2 * nu / x * oracle.besselk_scaled(nu, x)
+    assert lhs == pytest.approx(rhs, rel=3e-15)
+
+
+@pytest.mark.parametrize("nu", [0.0, 0.25, 0.75, 1.0, 1.25, 1.75, 2.2, 3.0])
+def test_besselk_matches_scipy(nu):
+    special = pytest.importorskip("scipy.special")
+    for x in np.geomspace(1e-3, 500.0, 61):
+        ref = special.kve(nu, x)
+        assert oracle.besselk_scaled(nu, float(x)) == pytest.approx(ref, rel=5e-14), (nu, x)
+
+
+def test_besselk_small_x_limit():
+    # K_nu(x) ~ Gamma(nu)/2 (2/x)^nu as x -> 0 (nu > 0)
+    for nu in (0.5, 1.0, 1.5):
+        x = 1e-7
+        assert oracle.besselk(nu, x) == pytest.approx(0.5 * math.gamma(nu) * (2 / x) ** nu, rel=1e-5)
+
+
+# ------------------------------------------------------------- Eq. 2 -------
+
+def test_printed_effective_range():
+    g = json.load(open(GOLDEN))["effective_range"]
+    for case in g["cases"]:
+        _, nuij = oracle.matern_params([case["nu"]], np.eye(1))
+        c = oracle.matern(case["h"], g["a"], float(nuij[0, 0]), g["sigma2"])
+        assert abs(c - case["cov"]) < g["printed_digits_tol"], (case, c)
+
+
+def test_printed_effective_range_vs_a():
+    # The printed ER lies between the nu = 0.5 and nu = 1 distances where the
+    # marginal covariance reaches 0.05 (the two marginals of the paper's fields).
+    g = json.load(open(GOLDEN))["effective_range_vs_a"]
+    from scipy.optimize import brentq
+    for a, er in zip(g["a"], g["er"]):
+        lo = brentq(lambda h: oracle.matern(h, a, 0.5, 1.0) - 0.05, 1e-6, 10)
+        hi = brentq(lambda h: oracle.matern(h, a, 1.0, 1.0) - 0.05, 1e-6, 10)
+        assert lo < er < hi * 1.01, (a, er, lo, hi)
+
+
+@pytest.mark.parametrize("h", [1e-4, 0.01, 0.07, 0.3, 1.2])
+def test_matern_half_integer_closed_forms(h):
+    a, s2 = 0.09, 1.7
+    x = h / a
+    assert oracle.matern(h, a, 0.5, s2) == pytest.approx(s2 * math.exp(-x), rel=1e-14)
+    assert oracle.matern(h, a, 1.5, s2) == pytest.approx(s2 * (1 + x) * math.exp(-x), rel=1e-14)
+
+
+def test_matern_zero_distance_limit():
+    for nu in (0.5, 0.8, 1.0, 1.5):
+        assert oracle.matern(0.0, 0.1, nu, 2.5) == 2.5
+        assert oracle.matern(1e-9, 0.1, nu, 2.5) == pytest.approx(2.5, rel=1e-6)
+
+
+def test_rho_closed_form_d2():
+    # d = 2: Gamma(nu + 1) = nu Gamma(nu) turns rho_ij into beta_ij sqrt(nu_i nu_j) / nu_ij
+    nu = [0.5, 1.0, 1.5]
+    beta = np.array([[1, 0.5, 0.3], [0.5, 1, 0.4], [0.3, 0.4, 1.0]])
+    rho, nuij = oracle.matern_params(nu, beta, d=2)
+    for i in range(3):
+        assert rho[i, i] == pytest.approx(1.0, rel=1e-15)
+        for j in range(3):
+            nij = 0.5 * (nu[i] + nu[j])
+            assert nuij[i, j] == nij
+            if i != j:
+                assert rho[i, j] == pytest.approx(beta[i, j] * math.sqrt(nu[i] * nu[j]) / nij, rel=1e-14)
+    # Fig. 5 theta: rho_12 = 0.5 sqrt(0.5) / 0.75
+    rho, _ = oracle.matern_params([0.5, 1.0], np.array([[1, 0.5], [0.5, 1]]))
+    assert rho[0, 1] == pytest.approx(0.5 * math.sqrt(0.5) / 0.75, rel=1e-14)
+
+
+def test_rho_d1_closed_form():
+    # d = 1, nu_i = nu_j = nu: rho = beta * Gamma(nu+1/2)/Gamma(nu) * Gamma(nu)/Gamma(nu+1/2) = beta
+    rho, _ = oracle.matern_params([0.7, 0.7], np.array([[1, 0.3], [0.3, 1]]), d=1)
+    assert rho[0, 1] == pytest.approx(0.3, rel=1e-14)
+
+
+# ------------------------------------------------------------- Sigma -------
+
+def _small_problem(n=40, seed=7, theta=None):
+    th = theta or oracle.Theta([1.0, 1.3], 0.09, [0.5, 1.0], 0.5)
+    locs = inputs.jittered_grid(n, seed)
+    return th, locs
+
+
+def test_sigma_structure():
+    th, locs = _small_problem(30)
+    S = oracle.covgen(th, locs)
+    p = 2
+    assert np.array_equal(S, S.T)
+    rho, _ = oracle.matern_params(th.nu, th.beta)
+    for l in range(30):
+        blk = S[p * l:p * l + p, p * l:p * l + p]
+        assert blk[0, 0] == pytest.approx(th.sigma2[0], rel=1e-15)
+        assert blk[1, 1] == pytest.approx(th.sigma2[1], rel=1e-15)
+        assert blk[0, 1] == pytest.approx(rho[0, 1] * math.sqrt(th.sigma2[0] * th.sigma2[1]), rel=1e-15)
+    # off-diagonal block (l, r) = C(|s_l - s_r|) entry by entry, Rep. I ordering
+    l, r = 3, 17
+    h = float(np.hypot(*(locs[l] - locs[r])))
+    for i in range(p):
+        for j in range(p):
+            rs = rho[i, j] * math.sqrt(th.sigma2[i] * th.sigma2[j])
+            assert S[p * l + i, p * r + j] == pytest.approx(
+                oracle.matern(h, th.a, 0.5 * (th.nu[i] + th.nu[j]), rs), rel=1e-14)
+    assert np.linalg.eigvalsh(S).min() > 0
+
+
+def test_cross_covariance_block_is_rep_i():
+    th, locs = _small_problem(12)
+    new = inputs.jittered_grid(5, 99)
+    S21 = oracle.covgen(th, new, locs)
+    assert S21.shape == (10, 24)
+    full = oracle.covgen(th, np.vstack([new, locs]))
+    assert np.array_equal(S21, full[:10, 10:])
+
+
+# ---------------------------------------------------- Cholesky / solve -----
+
+def _leibniz_det(A):
+    n = A.shape[0]
+    tot = 0.0
+    for perm in itertools.permutations(range(n)):
+        sgn = 1
+        p = list(perm)
+        for i in range(n):
+            while p[i] != i:
+                j = p[i]
+                p[i], p[j] = p[j], p[i]
+                sgn = -sgn
+        prod = 1.0
+        for i in range(n):
+            prod *= A[i, perm[i]]
+        tot += sgn * prod
+    return tot
+
+
+def _cramer_solve(A, b):
+    d = _leibniz_det(A)
+    x = np.empty(len(b))
+    for i in range(len(b)):
+        Ai = A.copy()
+        Ai[:, i] = b
+        x[i] = _leibniz_det(Ai) / d
+    return x
+
+
+@pytest.mark.parametrize("n_loc,p", [(3, 2), (4, 2), (2, 3)])
+def test_tiny_brute_force_det_and_solve(n_loc, p):
+    if p == 2:
+        th = oracle.Theta([1.0, 2.0], 0.3, [0.5, 1.0], 0.6)
+    else:
+        th = oracle.Theta([1.0, 2.0, 0.5], 0.3, [0.5, 1.0, 1.5], [0.5, 0.3, 0.4])
+    locs = inputs.jittered_grid(n_loc, 5)
+    S = oracle.covgen(th, locs)
+    N = S.shape[0]
+    Z = inputs.normals(11, N)
+    r = oracle.loglik(th, locs, Z, keep_factor=True)
+    det = _leibniz_det(S)
+    assert r.logdet == pytest.approx(math.log(det), rel=1e-12, abs=1e-12)
+    x = _cramer_solve(S, Z)
+    assert r.quad == pytest.approx(float(Z @ x), rel=1e-11)
+    expect = -0.5 * N * math.log(2 * math.pi) - 0.5 * math.log(det) - 0.5 * float(Z @ x)
+    assert r.loglik == pytest.approx(expect, rel=1e-12)
+
+
+def test_cholesky_reconstruction_and_library():
+    th, locs = _small_problem(150)
+    S = oracle.covgen(th, locs)
+    L, info = oracle.cholesky(S)
+    assert info == 0
+    assert np.allclose(np.triu(L, 1), 0)
+    assert np.linalg.norm(L @ L.T - S) / np.linalg.norm(S) < 1e-15 * S.shape[0]
+    assert np.allclose(L, np.linalg.cholesky(S), rtol=0, atol=1e-12)
+
+
+def test_cholesky_info_on_indefinite():
+    A = np.diag([1.0, 2.0, -1.0, 4.0])
+    _, info = oracle.cholesky(A)
+    assert info == 3
+    B = np.array([[1.0, 2.0], [2.0, 1.0]])  # eigenvalues 3, -1
+    assert oracle.cholesky(B)[1] == 2
+
+
+def test_forward_backward_solves():
+    th, locs = _small_problem(60)
+    S = oracle.covgen(th, locs)
+    L, _ = oracle.cholesky(S)
+    z = inputs.normals(3, S.shape[0])
+    y = oracle.forward(L, z)
+    assert np.allclose(L @ y, z, atol=1e-10)
+    w = oracle.backward(L, y)
+    assert np.allclose(S @ w, z, atol=1e-8)
+    assert np.allclose(w, np.linalg.solve(S, z), rtol=1e-8, atol=1e-8)
+
+
+# ------------------------------------------------------------- Eq. 1 -------
+
+def test_loglik_zero_data():
+    th, locs = _small_problem(50)
+    N = 100
+    r = oracle.loglik(th, locs, np.zeros(N))
+    sign, logdet = np.linalg.slogdet(oracle.covgen(th, locs))
+    assert sign > 0
+    assert r.quad == 0.0
+    assert r.loglik == pytest.approx(-0.5 * N * math.log(2 * math.pi) - 0.5 * logdet, rel=1e-13)
+
+
+def test_loglik_beta_zero_splits_into_univariate():
+    # beta = 0: the variables are independent (Sec. 4.2), so l is the sum of
+    # the p univariate likelihoods of the per-variable sub-vectors.
+    locs = inputs.jittered_grid(70, 21)
+    th = oracle.Theta([1.0, 0.7], 0.09, [0.5, 1.0], 0.0)
+    Z = inputs.normals(4, 140)
+    full = oracle.loglik(th, locs, Z).loglik
+    parts = 0.0
+    for i in range(2):
+        thi = oracle.Theta([th.sigma2[i]], th.a, [th.nu[i]], np.eye(1))
+        parts += oracle.loglik(thi, locs, Z[i::2]).loglik
+    assert full == pytest.approx(parts, rel=1e-12)
+
+
+def test_loglik_permutation_invariance_rep_i_rep_ii():
+    # Rep. I and Rep. II give the same likelihood (Sec. 5.2); any symmetric
+    # permutation of Sigma and Z leaves Eq. 1 unchanged.
+    th, locs = _small_problem(45)
+    Z = inputs.normals(8, 90)
+    base = oracle.loglik(th, locs, Z).loglik
+    # Rep. II: variable-major order, evaluated with library routines
+    S = oracle.covgen(th, locs)
+    perm = np.concatenate([np.arange(0, 90, 2), np.arange(1, 90, 2)])
+    S2 = S[np.ix_(perm, perm)]
+    z2 = Z[perm]
+    sign, logdet = np.linalg.slogdet(S2)
+    ref = -45 * math.log(2 * math.pi) - 0.5 * logdet - 0.5 * float(z2 @ np.linalg.solve(S2, z2))
+    assert base == pytest.approx(ref, rel=1e-11)
+    # location reordering (Morton)
+    order = oracle.morton_order(locs)
+    zi = Z.reshape(-1, 2)[order].reshape(-1)
+    assert oracle.loglik(th, locs[order], zi).loglik == pytest.approx(base, rel=1e-12)
+
+
+def test_forward_solve_whitens_simulated_draw():
+    # Z = L e  =>  y = L^-1 Z = e and Z' Sigma^-1 Z = e'e.
+    th, locs = _small_problem(80)
+    e = inputs.normals(17, 160)
+    Z = oracle.simulate(th, locs, e)
+    r = oracle.loglik(th, locs, Z)
+    assert np.allclose(r.y, e, rtol=0, atol=1e-9)
+    assert r.quad == pytest.approx(float(e @ e), rel=1e-10)
+
+
+def test_quadratic_form_chi_square_mean():
+    # E[Z' Sigma^-1 Z] = N over seeded draws (chi-square with N dof).
+    th, locs = _small_problem(40)
+    N = 80
+    S = oracle.covgen(th, locs)
+    L, _ = oracle.cholesky(S)
+    qs = []
+    for s in range(200):
+        Z = oracle.lower_matvec(L, inputs.normals(5000 + s, N))
+        qs.append(oracle.forward(L, Z) @ oracle.forward(L, Z))
+    m = float(np.mean(qs))
+    assert abs(m - N) < 4 * math.sqrt(2 * N / 200)
+
+
+# ------------------------------------------------------- Eq. 3 / Eq. 4 -----
+
+def test_predict_at_observed_location_returns_data():
+    th, locs = _small_problem(50)
+    Z = oracle.simulate(th, locs, inputs.normals(9, 100))
+    zhat = oracle.predict(th, locs, Z, locs[[4, 31]])
+    assert np.allclose(zhat, np.concatenate([Z[8:10], Z[62:64]]), atol=1e-8)
+
+
+def test_predict_beta_zero_is_separate_kriging():
+    locs = inputs.jittered_grid(60, 13)
+    new = inputs.jittered_grid(7, 77)
+    th = oracle.Theta([1.0, 2.0], 0.1, [0.5, 1.5], 0.0)
+    Z = inputs.normals(12, 120)
+    zhat = oracle.predict(th, locs, Z, new).reshape(-1, 2)
+    for i in range(2):
+        thi = oracle.Theta([th.sigma2[i]], th.a, [th.nu[i]], np.eye(1))
+        zi = oracle.predict(thi, locs, Z[i::2], new)
+        assert np.allclose(zhat[:, i], zi, rtol=1e-10, atol=1e-12)
+
+
+def test_predict_matches_library_solve():
+    th, locs = _small_problem(40)
+    new = inputs.jittered_grid(6, 55)
+    Z = inputs.normals(19, 80)
+    S = oracle.covgen(th, locs)
+    c0t = oracle.covgen(th, new, locs)
+    ref = c0t @ np.linalg.solve(S, Z)
+    assert np.allclose(oracle.predict(th, locs, Z, new), ref, rtol=1e-9, atol=1e-10)
+
+
+def test_mspe_definition():
+    zhat = np.array([1.0, 2.0, 3.0, 4.0])
+    z = np.array([0.0, 2.0, 3.0, 2.0])
+    assert oracle.mspe(zhat, z, 2) == pytest.approx((1.0 + 4.0) / 2)
+
+
+# ------------------------------------------------------------- Morton ------
+
+def test_morton_keys_bit_interleave():
+    locs = np.array([[0.0, 0.0], [1.0, 1.0], [0.0, 1.0], [1.0, 0.0]])
+    keys = oracle.morton_keys(locs)
+    assert keys[0] == 0
+    assert keys[3] == oracle._spread16(65535)          # x only: even bits
+    assert keys[2] == oracle._spread16(65535) << 1     # y only: odd bits
+    assert keys[1] == 0xFFFFFFFF
+
+
+def test_morton_order_z_pattern():
+    g = np.array([[(i + 0.5) / 4, (j + 0.5) / 4] for j in range(4) for i in range(4)])
+    order = oracle.morton_order(g)
+    # first quadrant (x < 1/2, y < 1/2) comes first, in Z order: (0,0),(1,0),(0,1),(1,1)
+    first4 = [tuple(np.round(g[k] * 4 - 0.5).astype(int)) for k in order[:4]]
+    assert first4 == [(0, 0), (1, 0), (0, 1), (1, 1)]
+
+
+# -------------------------------------------------------------- MLE --------
+
+def test_nelder_mead_quadratic_and_rosenbrock():
+    c = np.array([0.3, -1.2, 2.0])
+    nm = oracle.NelderMead(lambda x: float(np.sum((x - c) ** 2)), np.zeros(3), step=0.5)
+    for _ in range(300):
+        nm.step()
+    assert np.allclose(nm.best[0], c, atol=1e-5)
+    rb = oracle.NelderMead(lambda x: (1 - x[0]) ** 2 + 100 * (x[1] - x[0] ** 2) ** 2, np.array([-1.2, 1.0]), step=0.1)
+    for _ in range(600):
+        rb.step()
+    assert np.allclose(rb.best[0], [1.0, 1.0], atol=1e-4)
+
+
+def test_nelder_mead_first_iteration_by_hand():
+    # f(x) = x0^2 + 2 x1^2 from x0 = (1, 1), step 0.5: the vertices are
+    # (1,1) f=3, (1.5,1) f=4.25, (1,1.5) f=5.5.  Centroid of the two best is
+    # (1.25, 1); reflection of (1, 1.5) gives (1.5, 0.5), f = 2.75 < 3, so an
+    # expansion to (1.75, 0) follows, f = 3.0625 > 2.75: the reflection is kept.
+    nm = oracle.NelderMead(lambda x: x[0] ** 2 + 2 * x[1] ** 2, np.array([1.0, 1.0]), step=0.5)
+    nm.step()
+    assert nm.F == [3.0, 4.25, 5.5]
+    nm.step()
+    assert np.allclose(nm.X[0], [1.5, 0.5]) and nm.F[0] == 2.75
+    assert [tuple(v) for v in nm.X[1:]] == [(1.0, 1.0), (1.5, 1.0)]
+
+
+def test_theta_transform_roundtrip():
+    th = oracle.Theta([1.0, 2.0, 0.5], 0.05, [0.5, 1.0, 1.5], [0.5, 0.3, 0.4])
+    x = oracle.theta_to_x(th)
+    assert len(x) == 10
+    back = oracle.x_to_theta(x, 3)
+    assert np.allclose(back.sigma2, th.sigma2) and back.a == pytest.approx(0.05)
+    assert np.allclose(back.beta, th.beta)
+    assert oracle.beta_is_pd(th.beta)
+    assert not oracle.beta_is_pd(np.array([[1, 0.9, -0.9], [0.9, 1, 0.9], [-0.9, 0.9, 1.0]]))
+
+
+# -------------------------------------------------------------- TLR --------
+
+def test_tlr_reference_ranks_decay_and_order():
+    # Fig. 5: off-diagonal ranks grow towards the diagonal; a tighter accuracy
+    # never lowers a rank.  Morton-ordered bivariate matrix, Fig. 5 theta.
+    g = json.load(open(GOLDEN))["fig5_theta"]
+    th = oracle.Theta(g["sigma2"], g["a"], g["nu"], g["beta"])
+    locs = inputs.jittered_grid(400, 1)
+    locs = locs[oracle.morton_order(locs)]
+    S = oracle.covgen(th, locs)
+    nb = 100
+    r5 = oracle.tlr_reference_ranks(S, nb, 1e-5)
+    r9 = oracle.tlr_reference_ranks(S, nb, 1e-9)
+    T = r5.shape[0]
+    assert np.all(r9[r9 >= 0] >= r5[r5 >= 0])
+    near = np.mean([r9[i, i - 1] for i in range(1, T)])
+    far = np.mean([r9[i, j] for i in range(T) for j in range(i) if i - j >= T - 2])
+    assert near > far
+    assert r9.max() < nb
+
+
+# --------------------------------------------------------- MLOE / MMOM -----
+
+def test_mloe_mmom_zero_at_true_parameters():
+    th, locs = _small_problem(40)
+    pred = inputs.jittered_grid(5, 123)
+    mloe, mmom, loe, mom = oracle.mloe_mmom(th, th, locs, pred)
+    assert abs(mloe) < 1e-10 and abs(mmom) < 1e-10
+
+
+def test_mloe_nonnegative_for_misspecified():
+    # E_ta >= E_t since the true-parameter cokriging predictor is the BLUP.
+    th, locs = _small_problem(40)
+    tha = oracle.Theta([1.2, 1.0], 0.12, [0.6, 1.0], 0.3)
+    pred = inputs.jittered_grid(5, 123)
+    mloe, mmom, loe, mom = oracle.mloe_mmom(th, tha, locs, pred)
+    assert np.all(loe >= -1e-12)
