@@ -1,0 +1,228 @@
+/*
+ * geo.h -- C ABI of the GB300 library for the multivariate Matern Gaussian
+ * log-likelihood and cokriging of arxiv 2008.07437, "High Performance
+ * Multivariate Geospatial Statistics on Manycore Systems".
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns an int status (GEO_OK = 0 or a GEO_E* code).
+ *   Nothing throws across the ABI and no kernel traps; the context keeps a
+ *   human-readable message for the last failure (geo_last_error).
+ * - "_dev" pointers are device memory owned by the caller (for example the
+ *   data_ptr() of a torch tensor on the context's device); the library never
+ *   frees them.  "_host" pointers are host memory owned by the caller.
+ * - Locations are n x 2 row-major doubles (x_0, y_0, x_1, y_1, ...): points
+ *   of [0, 1]^2 or of any bounded planar domain, Euclidean distance (d = 2).
+ * - Vectors of observations use Representation I (Sec. 5.2): entry p*l + i is
+ *   variable i at location l ("location-major, variable-minor").
+ * - All device work is enqueued on the given stream (a cudaStream_t passed
+ *   as void*, NULL = legacy default stream).  Functions that return a host
+ *   scalar synchronise that stream before returning.
+ * - Objects returned through out-pointers (geo_ctx, geo_factor) are owned by
+ *   the library and released with geo_destroy / geo_factor_free.
+ */
+#ifndef GEO_H
+#define GEO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+enum {
+    GEO_OK = 0,
+    GEO_EINVAL = 1,      /* bad argument: sizes, theta outside its domain, NULL pointer */
+    GEO_ENOTSPD = 2,     /* Sigma(theta) not positive definite; *info = 1-based failing row */
+    GEO_ENOMEM = 3,      /* the context's HBM budget (or the device) cannot hold the request */
+    GEO_ETIMEOUT = 4,    /* a bounded device-side wait expired; the context stays usable */
+    GEO_ECUDA = 5,       /* a CUDA runtime call failed; see geo_last_error */
+    GEO_EUNSUPPORTED = 6 /* option combination not implemented */
+};
+
+/* ---- factorisation forms (Sec. 5.2 exact, Sec. 5.3 TLR) ----------------- */
+enum {
+    GEO_PREC_FP64 = 0,   /* dense FP64 tiled Cholesky (exact computation) */
+    GEO_PREC_MIXED = 1,  /* FP64 diagonal tiles, FP32 band, FP16/BF16 beyond (per-tile scale) */
+    GEO_PREC_TLR = 2     /* tile low-rank off-diagonal tiles at accuracy tlr_tol */
+};
+
+#define GEO_PMAX 4       /* largest number of variables p */
+
+/*
+ * theta = (sigma^2_11..pp, a, nu_11..pp, beta) of the parsimonious
+ * multivariate Matern model, Eq. 2 (Sec. 4.2).  All arrays are host memory.
+ *   p       number of variables, 1 <= p <= GEO_PMAX
+ *   sigma2  p marginal variances sigma^2_ii > 0
+ *   nu      p marginal smoothness nu_ii > 0 (nu_ij = (nu_ii + nu_jj) / 2)
+ *   beta    p*p row-major symmetric positive definite correlation matrix
+ *           (its diagonal is read as 1); NULL is allowed when p == 1
+ *   a       spatial range a > 0
+ * rho_ij follows Sec. 4.2 with d = 2, reading the square roots as applying to
+ * the marginal Gamma ratios, which gives rho_ii = 1.
+ */
+typedef struct {
+    int p;
+    const double *sigma2;
+    const double *nu;
+    const double *beta;
+    double a;
+} geo_theta;
+
+/* Options of a likelihood evaluation.  geo_opts_default fills the defaults. */
+typedef struct {
+    int nb;             /* tile size of the tiled Cholesky (default 960) */
+    int prec;           /* GEO_PREC_* (default GEO_PREC_FP64) */
+    int band;           /* MIXED: tiles with 0 < |i - j| <= band stay FP32 (default 4) */
+    int lowp;           /* MIXED: 0 = FP16 operands with a per-tile power-of-two scale, 1 = BF16 */
+    int refine_iters;   /* MIXED: FP64 iterative-refinement sweeps on Sigma x = Z (default 2) */
+    double tlr_tol;     /* TLR: absolute accuracy of each compressed tile (default 1e-9) */
+    int tlr_kmax;       /* TLR: maximum tile rank (default 200) */
+    int morton;         /* 1 = reorder locations by Morton (Z-order) key internally (default 1) */
+    int fp64_gemm;      /* FP64 trailing updates: 0 = native FP64 FMA (default) */
+    int reserved[7];
+} geo_opts;
+
+typedef struct geo_ctx geo_ctx;
+typedef struct geo_factor geo_factor;
+
+/* Fill *opts with the defaults listed above. */
+void geo_opts_default(geo_opts *opts);
+
+/*
+ * Create a context on CUDA device `device`.  hbm_budget_bytes caps the device
+ * memory the context allocates for its own workspaces and factors (0 = no cap
+ * beyond the device).  The context owns its workspaces; geo_destroy frees
+ * them and every factor still alive.
+ */
+int geo_create(geo_ctx **ctx, int device, size_t hbm_budget_bytes);
+int geo_destroy(geo_ctx *ctx);
+
+/* Message of the last failed call on this context ("" if none); owned by the context. */
+const char *geo_last_error(const geo_ctx *ctx);
+
+/*
+ * Cross-covariance matrix of Eq. 2 in Representation I (Sec. 5.2, Eq. 4):
+ *   out[(p*r + j) * ld + (p*l + i)] = C_ij(|s1_l - s2_r|; theta)
+ * i.e. column-major (p*n1) x (p*n2) with leading dimension ld >= p*n1.
+ * locs2_dev == NULL means locs2 = locs1 (then Sigma itself, all entries).
+ * h = 0 uses the limit rho_ij sigma_ii sigma_jj (no nugget).  The Bessel
+ * function K_nu is evaluated in FP64 on the device.  No reordering.
+ */
+int geo_covgen(geo_ctx *ctx, const double *locs1_dev, int n1, const double *locs2_dev, int n2,
+               const geo_theta *theta, double *out_dev, long long ld, void *stream);
+
+/*
+ * Gaussian log-likelihood, Eq. 1 (Sec. 1):
+ *   l(theta) = -(N/2) log(2 pi) - 1/2 log|Sigma(theta)| - 1/2 Z' Sigma(theta)^-1 Z,  N = p n,
+ * by covariance generation, tiled Cholesky, triangular solve and
+ * log-determinant, all on the device.
+ *   locs_dev     n x 2 locations (device)
+ *   z_dev        N observations in Representation I (device)
+ *   opts         NULL = defaults
+ *   loglik_host  receives l (host); may be NULL
+ *   keep         if non-NULL, receives a factor (L, L^-1 Z and the reordered
+ *                locations) kept on the device for geo_predict; free with
+ *                geo_factor_free.  NULL = discard.
+ *   info         if non-NULL, receives 0 or, on GEO_ENOTSPD, the 1-based row
+ *                (in the library's internal location order) of the first
+ *                non-positive pivot.
+ * Synchronises `stream`.
+ */
+int geo_loglik(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev, const geo_theta *theta,
+               const geo_opts *opts, double *loglik_host, geo_factor **keep, int *info, void *stream);
+
+/*
+ * Cokriging predictor, Eq. 3 / Eq. 4 (Sec. 4.3): for each of the m new
+ * locations s0, Zhat(s0) = c0' Sigma^-1 Z, c0 the (p n) x p cross-covariance
+ * between Z(s0) and the observed locations.  Every new location misses all p
+ * variables.  Uses the factor kept by geo_loglik (its theta, L and L^-1 Z).
+ *   new_locs_dev  m x 2 (device)
+ *   zhat_dev      p*m outputs in Representation I, in the caller's order of
+ *                 new locations (device)
+ */
+int geo_predict(geo_ctx *ctx, const geo_factor *factor, const double *new_locs_dev, int m, double *zhat_dev,
+                void *stream);
+
+/*
+ * Synthetic draw Z = L e with L L' = Sigma(theta) (Sec. 6.4.1 synthetic data;
+ * the paper does not state its generator): e_dev holds N standard normals
+ * (device), z_dev receives N values in Representation I in the caller's
+ * location order.  Synchronises `stream`.
+ */
+int geo_simulate(geo_ctx *ctx, const double *locs_dev, int n, const double *e_dev, const geo_theta *theta,
+                 const geo_opts *opts, double *z_dev, int *info, void *stream);
+
+/* Summary of a kept factor. */
+typedef struct {
+    int n, p, N, nb, prec;
+    double loglik, logdet, quad;   /* Eq. 1 and its two data-dependent terms */
+    long long device_bytes;        /* device memory the factor holds */
+    double tlr_bytes_ratio;        /* TLR: bytes of the compressed factor / dense bytes; else 1 */
+    int tlr_max_rank, tlr_dense_tiles;
+} geo_factor_stats;
+
+int geo_factor_stats_get(const geo_factor *factor, geo_factor_stats *out);
+
+/*
+ * Copy part of a kept factor to host memory, in the library's internal
+ * (reordered) index space:
+ *   what = 0: the block L[r0:r1, c0:c1] of the Cholesky factor (row-major
+ *             out, (r1-r0)*(c1-c0) doubles; entries above the diagonal are 0)
+ *   what = 1: y = L^-1 Z, entries r0..r1-1
+ *   what = 2: the location permutation, entries r0..r1-1 as doubles
+ *             (internal location k is caller location perm[k])
+ */
+int geo_factor_read(const geo_factor *factor, int what, long long r0, long long r1, long long c0, long long c1,
+                    double *host_out);
+
+void geo_factor_free(geo_factor *factor);
+
+/*
+ * Morton (Z-order) permutation of n locations (Sec. 5.3): keys interleave the
+ * two coordinates quantised to 16 bits over the square bounding box
+ * [xmin, xmin + span]^2 (span = the larger extent), x on the even bits;
+ * locations are sorted by (key, index).  Host memory in and out; perm_host
+ * receives n indices (internal position k holds caller location perm[k]).
+ */
+int geo_morton_order(const double *locs_host, int n, int *perm_host);
+
+/*
+ * Maximum likelihood by the Nelder-Mead simplex method (the paper maximises
+ * Eq. 1 with NLopt, Sec. 5.1; the algorithm is not named).  The state is a
+ * plain host struct owned by the caller: it can be copied, saved and
+ * restored, and geo_mle_step resumes from it.  Coordinates are
+ * x = (log sigma^2_i, log a, log nu_i, beta_ij for i < j); a vertex whose
+ * beta is not positive definite, or whose Sigma is not, scores +inf.
+ */
+#define GEO_MLE_QMAX 16
+typedef struct {
+    int p, q;                                  /* variables, coordinates */
+    int iter, evals;                           /* iterations done, likelihood evaluations */
+    int initialized;                           /* simplex values computed */
+    double step;                               /* initial simplex step */
+    double x[GEO_MLE_QMAX + 1][GEO_MLE_QMAX];  /* vertices, ordered best first once initialized */
+    double f[GEO_MLE_QMAX + 1];                /* -l at each vertex */
+    double last_f;                             /* -l of the last evaluation */
+} geo_mle_state;
+
+/* Start a simplex at theta0 (host) with x0 + step * e_k as the other vertices. */
+int geo_mle_init(geo_mle_state *state, const geo_theta *theta0, double step);
+
+/*
+ * One unit of work: the q + 1 initial evaluations on the first call, one
+ * Nelder-Mead iteration (reflection, expansion, contraction or shrink, with
+ * coefficients 1, 2, 1/2, 1/2; vertices ordered by (value, index)) after.
+ */
+int geo_mle_step(geo_ctx *ctx, geo_mle_state *state, const double *locs_dev, int n, const double *z_dev,
+                 const geo_opts *opts, void *stream);
+
+/* Best vertex as theta: sigma2[p], a, nu[p], beta[p*p] (host; beta may be NULL). */
+int geo_mle_best(const geo_mle_state *state, double *sigma2, double *a, double *nu, double *beta,
+                 double *loglik);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GEO_H */

@@ -1,0 +1,337 @@
+"""GB300 library for the multivariate Matern log-likelihood and cokriging of
+arxiv 2008.07437 ("High Performance Multivariate Geospatial Statistics on
+Manycore Systems").
+
+The computation lives in ``libgeo.so`` (hand-written CUDA for sm_103a behind
+the C ABI of ``include/geo.h``).  This module is the thin Python binding: the
+functions carry the C names (``geo_loglik``, ``geo_predict``, ...) and only
+marshal arguments -- torch tensors for device memory, torch streams for
+ordering.  There is no CPU fallback: if the library is missing or no CUDA
+device is present, every call raises.
+
+``inputs`` (seeded synthetic workloads) does not load the library.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgeo.so")
+
+GEO_OK, GEO_EINVAL, GEO_ENOTSPD, GEO_ENOMEM, GEO_ETIMEOUT, GEO_ECUDA, GEO_EUNSUPPORTED = range(7)
+GEO_PREC_FP64, GEO_PREC_MIXED, GEO_PREC_TLR = 0, 1, 2
+GEO_PMAX = 4
+GEO_MLE_QMAX = 16
+
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+
+
+class geo_theta(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("sigma2", _c_double_p), ("nu", _c_double_p), ("beta", _c_double_p),
+                ("a", ctypes.c_double)]
+
+
+class geo_opts(ctypes.Structure):
+    _fields_ = [("nb", ctypes.c_int), ("prec", ctypes.c_int), ("band", ctypes.c_int), ("lowp", ctypes.c_int),
+                ("refine_iters", ctypes.c_int), ("tlr_tol", ctypes.c_double), ("tlr_kmax", ctypes.c_int),
+                ("morton", ctypes.c_int), ("fp64_gemm", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+
+
+class geo_factor_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("p", ctypes.c_int), ("N", ctypes.c_int), ("nb", ctypes.c_int),
+                ("prec", ctypes.c_int), ("loglik", ctypes.c_double), ("logdet", ctypes.c_double),
+                ("quad", ctypes.c_double), ("device_bytes", ctypes.c_longlong),
+                ("tlr_bytes_ratio", ctypes.c_double), ("tlr_max_rank", ctypes.c_int),
+                ("tlr_dense_tiles", ctypes.c_int)]
+
+
+class geo_mle_state(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("q", ctypes.c_int), ("iter", ctypes.c_int), ("evals", ctypes.c_int),
+                ("initialized", ctypes.c_int), ("step", ctypes.c_double),
+                ("x", (ctypes.c_double * GEO_MLE_QMAX) * (GEO_MLE_QMAX + 1)),
+                ("f", ctypes.c_double * (GEO_MLE_QMAX + 1)), ("last_f", ctypes.c_double)]
+
+
+# every symbol include/geo.h declares, with (restype, argtypes)
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_LL = ctypes.c_longlong
+_D = ctypes.c_double
+SIGNATURES = {
+    "geo_opts_default": (None, [ctypes.POINTER(geo_opts)]),
+    "geo_create": (_I, [ctypes.POINTER(_P), _I, ctypes.c_size_t]),
+    "geo_destroy": (_I, [_P]),
+    "geo_last_error": (ctypes.c_char_p, [_P]),
+    "geo_covgen": (_I, [_P, _P, _I, _P, _I, ctypes.POINTER(geo_theta), _P, _LL, _P]),
+    "geo_loglik": (_I, [_P, _P, _I, _P, ctypes.POINTER(geo_theta), ctypes.POINTER(geo_opts),
+                        ctypes.POINTER(_D), ctypes.POINTER(_P), ctypes.POINTER(_I), _P]),
+    "geo_predict": (_I, [_P, _P, _P, _I, _P, _P]),
+    "geo_simulate": (_I, [_P, _P, _I, _P, ctypes.POINTER(geo_theta), ctypes.POINTER(geo_opts), _P,
+                          ctypes.POINTER(_I), _P]),
+    "geo_factor_stats_get": (_I, [_P, ctypes.POINTER(geo_factor_stats)]),
+    "geo_factor_read": (_I, [_P, _I, _LL, _LL, _LL, _LL, _P]),
+    "geo_factor_free": (None, [_P]),
+    "geo_morton_order": (_I, [_P, _I, _P]),
+    "geo_mle_init": (_I, [ctypes.POINTER(geo_mle_state), ctypes.POINTER(geo_theta), _D]),
+    "geo_mle_step": (_I, [_P, ctypes.POINTER(geo_mle_state), _P, _I, _P, ctypes.POINTER(geo_opts), _P]),
+    "geo_mle_best": (_I, [ctypes.POINTER(geo_mle_state), _P, _P, _P, _P, _P]),
+}
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+class GeoError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("geo error %d: %s" % (code, msg))
+        self.code = code
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libgeo.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError("libgeo.so is not built (%s); run __graft_entry__.build() or "
+                               "python -m paper_2008_07437_gb300.build" % path)
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+# ----------------------------------------------------------------------------
+# argument marshalling
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Theta:
+    """theta = (sigma^2_1..p, a, nu_1..p, beta) of Eq. 2 (Sec. 4.2)."""
+    sigma2: tuple
+    a: float
+    nu: tuple
+    beta: object = None  # p x p matrix, upper-triangle list, or scalar (p = 2)
+
+    def beta_matrix(self) -> np.ndarray:
+        p = len(self.sigma2)
+        b = np.eye(p)
+        if self.beta is None:
+            return b
+        arr = np.asarray(self.beta, dtype=np.float64)
+        if arr.ndim == 0:
+            b[0, 1] = b[1, 0] = float(arr)
+        elif arr.ndim == 1:
+            k = 0
+            for i in range(p):
+                for j in range(i + 1, p):
+                    b[i, j] = b[j, i] = arr[k]
+                    k += 1
+        else:
+            b = arr.copy()
+        return b
+
+    def to_c(self):
+        p = len(self.sigma2)
+        keep = (np.ascontiguousarray(self.sigma2, dtype=np.float64),
+                np.ascontiguousarray(self.nu, dtype=np.float64),
+                np.ascontiguousarray(self.beta_matrix(), dtype=np.float64).reshape(-1))
+        th = geo_theta(p, keep[0].ctypes.data_as(_c_double_p), keep[1].ctypes.data_as(_c_double_p),
+                       keep[2].ctypes.data_as(_c_double_p), float(self.a))
+        return th, keep
+
+    @staticmethod
+    def from_spec(spec) -> "Theta":
+        return Theta(tuple(spec.sigma2), spec.a, tuple(spec.nu), tuple(spec.beta))
+
+
+def opts(**kw) -> geo_opts:
+    o = geo_opts()
+    load_library().geo_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _dev_ptr(t, name, dtype=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA torch tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must be %s" % (name, dtype))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """Owns a geo_ctx (device workspaces, kept factors)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.lib = load_library()
+        h = ctypes.c_void_p()
+        rc = self.lib.geo_create(ctypes.byref(h), int(device), int(hbm_budget_bytes))
+        if rc != GEO_OK:
+            raise GeoError(rc, "geo_create failed on device %d" % device)
+        self.handle = h
+        self.device = device
+
+    def check(self, rc: int):
+        if rc != GEO_OK:
+            raise GeoError(rc, self.lib.geo_last_error(self.handle).decode())
+
+    def close(self):
+        if self.handle:
+            self.lib.geo_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Factor:
+    def __init__(self, ctx: Context, handle):
+        self.ctx, self.handle = ctx, handle
+
+    def free(self):
+        if self.handle:
+            self.ctx.lib.geo_factor_free(self.handle)
+            self.handle = None
+
+
+def geo_create(device: int = 0, hbm_budget_bytes: int = 0) -> Context:
+    return Context(device, hbm_budget_bytes)
+
+
+def geo_covgen(ctx: Context, locs1, theta: Theta, out, locs2=None, ld: int | None = None, stream=None):
+    """Eq. 2 cross-covariance in Representation I, column-major into ``out``."""
+    import torch
+    th, _keep = theta.to_c()
+    n1 = locs1.shape[0]
+    n2 = locs2.shape[0] if locs2 is not None else n1
+    p = len(theta.sigma2)
+    ld = ld if ld is not None else p * n1
+    l2 = _dev_ptr(locs2, "locs2", torch.float64) if locs2 is not None else None
+    ctx.check(ctx.lib.geo_covgen(ctx.handle, _dev_ptr(locs1, "locs1", torch.float64), n1, l2, n2,
+                                 ctypes.byref(th), _dev_ptr(out, "out", torch.float64), ld, _stream(stream)))
+    return out
+
+
+def geo_loglik(ctx: Context, locs, z, theta: Theta, options: geo_opts | None = None, keep: bool = False,
+               stream=None):
+    """Eq. 1 on the device.  Returns (loglik, Factor or None)."""
+    import torch
+    th, _keep = theta.to_c()
+    val = ctypes.c_double()
+    fac = ctypes.c_void_p()
+    info = ctypes.c_int()
+    rc = ctx.lib.geo_loglik(ctx.handle, _dev_ptr(locs, "locs", torch.float64), locs.shape[0],
+                            _dev_ptr(z, "z", torch.float64), ctypes.byref(th),
+                            ctypes.byref(options) if options is not None else None, ctypes.byref(val),
+                            ctypes.byref(fac) if keep else None, ctypes.byref(info), _stream(stream))
+    if rc == GEO_ENOTSPD:
+        err = GeoError(rc, ctx.lib.geo_last_error(ctx.handle).decode())
+        err.info = info.value
+        raise err
+    ctx.check(rc)
+    return val.value, (Factor(ctx, fac) if keep else None)
+
+
+def geo_predict(ctx: Context, factor: Factor, new_locs, zhat, stream=None):
+    """Eq. 3 / Eq. 4 cokriging at ``new_locs`` into ``zhat`` (p*m, Rep. I)."""
+    import torch
+    ctx.check(ctx.lib.geo_predict(ctx.handle, factor.handle, _dev_ptr(new_locs, "new_locs", torch.float64),
+                                  new_locs.shape[0], _dev_ptr(zhat, "zhat", torch.float64), _stream(stream)))
+    return zhat
+
+
+def geo_simulate(ctx: Context, locs, e, theta: Theta, out, options: geo_opts | None = None, stream=None):
+    """Z = L e (L L' = Sigma(theta)) into ``out``."""
+    import torch
+    th, _keep = theta.to_c()
+    info = ctypes.c_int()
+    ctx.check(ctx.lib.geo_simulate(ctx.handle, _dev_ptr(locs, "locs", torch.float64), locs.shape[0],
+                                   _dev_ptr(e, "e", torch.float64), ctypes.byref(th),
+                                   ctypes.byref(options) if options is not None else None,
+                                   _dev_ptr(out, "out", torch.float64), ctypes.byref(info), _stream(stream)))
+    return out
+
+
+def geo_factor_stats_get(factor: Factor) -> geo_factor_stats:
+    st = geo_factor_stats()
+    factor.ctx.check(factor.ctx.lib.geo_factor_stats_get(factor.handle, ctypes.byref(st)))
+    return st
+
+
+def geo_factor_read(factor: Factor, what: int, r0: int, r1: int, c0: int = 0, c1: int = 0) -> np.ndarray:
+    n = (r1 - r0) * (c1 - c0) if what == 0 else (r1 - r0)
+    out = np.zeros(max(n, 1), dtype=np.float64)
+    factor.ctx.check(factor.ctx.lib.geo_factor_read(factor.handle, what, r0, r1, c0, c1,
+                                                    out.ctypes.data_as(ctypes.c_void_p)))
+    out = out[:n]
+    return out.reshape(r1 - r0, c1 - c0) if what == 0 else out
+
+
+def geo_factor_free(factor: Factor):
+    factor.free()
+
+
+def geo_morton_order(locs) -> np.ndarray:
+    """Host Morton permutation (internal position k holds caller location perm[k])."""
+    locs = np.ascontiguousarray(locs, dtype=np.float64)
+    n = locs.shape[0]
+    perm = np.zeros(max(n, 1), dtype=np.int32)
+    rc = load_library().geo_morton_order(locs.ctypes.data_as(ctypes.c_void_p), n, perm.ctypes.data_as(ctypes.c_void_p))
+    if rc != GEO_OK:
+        raise GeoError(rc, "geo_morton_order")
+    return perm[:n].astype(np.int64)
+
+
+def geo_mle_init(theta0: Theta, step: float = 0.1) -> geo_mle_state:
+    st = geo_mle_state()
+    th, _keep = theta0.to_c()
+    rc = load_library().geo_mle_init(ctypes.byref(st), ctypes.byref(th), float(step))
+    if rc != GEO_OK:
+        raise GeoError(rc, "geo_mle_init")
+    return st
+
+
+def geo_mle_step(ctx: Context, state: geo_mle_state, locs, z, options: geo_opts | None = None, stream=None):
+    import torch
+    ctx.check(ctx.lib.geo_mle_step(ctx.handle, ctypes.byref(state), _dev_ptr(locs, "locs", torch.float64),
+                                   locs.shape[0], _dev_ptr(z, "z", torch.float64),
+                                   ctypes.byref(options) if options is not None else None, _stream(stream)))
+    return state
+
+
+def geo_mle_best(state: geo_mle_state):
+    p = state.p
+    s2 = np.zeros(p)
+    nu = np.zeros(p)
+    beta = np.zeros(p * p)
+    a = ctypes.c_double()
+    ll = ctypes.c_double()
+    rc = load_library().geo_mle_best(ctypes.byref(state), s2.ctypes.data_as(ctypes.c_void_p), ctypes.byref(a),
+                                     nu.ctypes.data_as(ctypes.c_void_p), beta.ctypes.data_as(ctypes.c_void_p),
+                                     ctypes.byref(ll))
+    if rc != GEO_OK:
+        raise GeoError(rc, "geo_mle_best")
+    return Theta(tuple(s2), a.value, tuple(nu), beta.reshape(p, p)), ll.value

@@ -1,0 +1,604 @@
+// C ABI of libgeo.so (declared in include/geo.h): argument checking, theta
+// constants, Morton ordering, memory under the context's HBM budget, and the
+// stream-ordered pipelines of geo_loglik / geo_predict / geo_simulate /
+// geo_mle_step.  All arithmetic of the likelihood runs in the CUDA kernels;
+// this file only prepares per-theta constants (p(p+1)/2 triples) and moves
+// scalars.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <numeric>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "geo_internal.cuh"
+
+// ---------------------------------------------------------------------------
+// Context, factor
+// ---------------------------------------------------------------------------
+struct geo_ctx {
+    int device = 0;
+    size_t budget = 0;      // 0 = no cap
+    size_t used = 0;
+    std::string err;
+    DevStatus *st = nullptr;
+    DevResults *res = nullptr;
+    DevStatus *h_st = nullptr;    // pinned
+    DevResults *h_res = nullptr;  // pinned
+    // reusable workspace for the matrix of a discarded evaluation
+    double *ws = nullptr;
+    size_t ws_bytes = 0;
+    std::vector<geo_factor *> factors;
+};
+
+struct geo_factor {
+    geo_ctx *ctx = nullptr;
+    int n = 0, p = 0, N = 0, nb = 0, prec = GEO_PREC_FP64;
+    long long ld = 0;
+    double *A = nullptr;    // L (lower) with y' in row N
+    size_t A_bytes = 0;
+    double *lx = nullptr, *ly = nullptr;   // locations in internal order (SoA)
+    double *w = nullptr;                   // L^-T y (lazy)
+    std::vector<int> perm;                 // internal k -> caller location perm[k]
+    CovParams cp;
+    double loglik = 0, logdet = 0, quad = 0;
+};
+
+namespace {
+
+int fail(geo_ctx *ctx, int code, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int cuda_fail(geo_ctx *ctx, cudaError_t e, const char *where) {
+    return fail(ctx, GEO_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t _e = (call);                                   \
+        if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call);   \
+    } while (0)
+
+int dev_alloc(geo_ctx *ctx, void **ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (bytes == 0) return GEO_OK;
+    if (ctx->budget && ctx->used + bytes > ctx->budget)
+        return fail(ctx, GEO_ENOMEM, "HBM budget exceeded: need " + std::to_string(bytes) + " bytes, " +
+                                         std::to_string(ctx->budget - ctx->used) + " left");
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return fail(ctx, GEO_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    ctx->used += bytes;
+    return GEO_OK;
+}
+
+void dev_free(geo_ctx *ctx, void *ptr, size_t bytes) {
+    if (!ptr) return;
+    cudaFree(ptr);
+    ctx->used -= bytes;
+}
+
+struct SetDevice {
+    int prev = -1;
+    explicit SetDevice(int d) {
+        cudaGetDevice(&prev);
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~SetDevice() {
+        int cur;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+// G1(mu) = (1/Gamma(1-mu) - 1/Gamma(1+mu)) / (2 mu), G2(mu) = (1/Gamma(1-mu) + 1/Gamma(1+mu)) / 2.
+// Near mu = 0 the difference cancels: G1 is even in mu and equals
+// -(a2 + a4 mu^2 + a6 mu^4 + ...), a_k the Taylor coefficients of 1/Gamma(z).
+void temme_gammas(double mu, double *g1, double *g2, double *gp, double *gm, double *fact) {
+    const long double m = mu;
+    const long double rp = 1.0L / tgammal(1.0L + m), rm = 1.0L / tgammal(1.0L - m);
+    *gp = (double)tgammal(1.0L + m);
+    *gm = (double)tgammal(1.0L - m);
+    *g2 = (double)(0.5L * (rm + rp));
+    if (fabsl(m) < 1e-3L) {
+        const double u = mu * mu;
+        // a2 = Euler's constant; a4, a6 of the series of 1/Gamma(z)
+        *g1 = -(0.5772156649015328606 + u * (-0.042002635034095235529 + u * (-0.04219773455554433675)));
+    } else {
+        *g1 = (double)((rm - rp) / (2.0L * m));
+    }
+    const long double pi = 3.141592653589793238462643383279502884L;
+    *fact = (mu == 0.0) ? 1.0 : (double)(m * pi / sinl(m * pi));
+}
+
+}  // namespace
+
+// theta -> per-(i, j) constants of Eq. 2.  rho_ij (Sec. 4.2, d = 2):
+//   rho_ij = beta_ij sqrt(G(nu_i + 1)/G(nu_i)) sqrt(G(nu_j + 1)/G(nu_j)) G(nu_ij)/G(nu_ij + 1).
+int theta_to_params(const geo_theta *th, CovParams *cp, std::string *err) {
+    if (!th) {
+        *err = "theta is NULL";
+        return GEO_EINVAL;
+    }
+    const int p = th->p;
+    if (p < 1 || p > GEO_PMAX) {
+        *err = "theta.p must be in 1.." + std::to_string(GEO_PMAX);
+        return GEO_EINVAL;
+    }
+    if (!th->sigma2 || !th->nu || (p > 1 && !th->beta)) {
+        *err = "theta arrays must not be NULL";
+        return GEO_EINVAL;
+    }
+    if (!(th->a > 0.0) || !isfinite(th->a)) {
+        *err = "theta.a must be > 0";
+        return GEO_EINVAL;
+    }
+    for (int i = 0; i < p; ++i) {
+        if (!(th->sigma2[i] > 0.0) || !isfinite(th->sigma2[i])) {
+            *err = "theta.sigma2 must be > 0";
+            return GEO_EINVAL;
+        }
+        if (!(th->nu[i] > 0.0) || !(th->nu[i] < 50.0)) {
+            *err = "theta.nu must be in (0, 50)";
+            return GEO_EINVAL;
+        }
+    }
+    // beta: symmetric, unit diagonal (implied), positive definite
+    double B[GEO_PMAX][GEO_PMAX];
+    for (int i = 0; i < p; ++i)
+        for (int j = 0; j < p; ++j) {
+            if (i == j) {
+                B[i][j] = 1.0;
+                continue;
+            }
+            const double b = th->beta[i * p + j];
+            if (!isfinite(b) || b != th->beta[j * p + i]) {
+                *err = "theta.beta must be finite and symmetric";
+                return GEO_EINVAL;
+            }
+            B[i][j] = b;
+        }
+    {
+        double L[GEO_PMAX][GEO_PMAX] = {};
+        for (int j = 0; j < p; ++j) {
+            double s = B[j][j];
+            for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+            if (!(s > 0.0)) {
+                *err = "theta.beta is not positive definite";
+                return GEO_EINVAL;
+            }
+            L[j][j] = sqrt(s);
+            for (int i = j + 1; i < p; ++i) {
+                double t = B[i][j];
+                for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+                L[i][j] = t / L[j][j];
+            }
+        }
+    }
+    memset(cp, 0, sizeof(*cp));
+    cp->p = p;
+    cp->inv_a = 1.0 / th->a;
+    for (int i = 0; i < p; ++i) {
+        for (int j = 0; j < p; ++j) {
+            MaternConst &c = cp->m[i * p + j];
+            const double nui = th->nu[i], nuj = th->nu[j];
+            const double nij = 0.5 * (nui + nuj);
+            const long double ri = tgammal((long double)nui + 1.0L) / tgammal((long double)nui);
+            const long double rj = tgammal((long double)nuj + 1.0L) / tgammal((long double)nuj);
+            const long double rho = (long double)B[i][j] * sqrtl(ri) * sqrtl(rj) * tgammal((long double)nij) /
+                                    tgammal((long double)nij + 1.0L);
+            const long double c0 = rho * sqrtl((long double)th->sigma2[i]) * sqrtl((long double)th->sigma2[j]);
+            c.nu = nij;
+            c.c0 = (double)c0;
+            c.pre = (double)(c0 / (powl(2.0L, (long double)nij - 1.0L) * tgammal((long double)nij)));
+            const int nl = (int)floor(nij + 0.5);
+            c.nl = nl;
+            c.mu = nij - nl;
+            temme_gammas(c.mu, &c.g1, &c.g2, &c.gp, &c.gm, &c.fact);
+            c.kind = (nij == 0.5) ? 1 : (nij == 1.5) ? 2 : (nij == 2.5) ? 3 : 0;
+        }
+    }
+    return GEO_OK;
+}
+
+// Morton order: 16-bit quantisation over the square bounding box, x bits on
+// the even positions, sort by (key, index).
+void morton_perm_host(const double *locs, int n, int *perm) {
+    if (n <= 0) return;
+    double xmin = locs[0], xmax = locs[0], ymin = locs[1], ymax = locs[1];
+    for (int k = 1; k < n; ++k) {
+        xmin = std::min(xmin, locs[2 * k]);
+        xmax = std::max(xmax, locs[2 * k]);
+        ymin = std::min(ymin, locs[2 * k + 1]);
+        ymax = std::max(ymax, locs[2 * k + 1]);
+    }
+    const double span = std::max(xmax - xmin, ymax - ymin);
+    auto spread = [](uint32_t v) {
+        uint32_t out = 0;
+        for (int b = 0; b < 16; ++b) out |= ((v >> b) & 1u) << (2 * b);
+        return out;
+    };
+    std::vector<uint32_t> key(n);
+    for (int k = 0; k < n; ++k) {
+        long long qx = 0, qy = 0;
+        if (span > 0.0) {
+            qx = (long long)floor((locs[2 * k] - xmin) / span * 65536.0);
+            qy = (long long)floor((locs[2 * k + 1] - ymin) / span * 65536.0);
+        }
+        qx = std::min(std::max(qx, 0LL), 65535LL);
+        qy = std::min(std::max(qy, 0LL), 65535LL);
+        key[k] = spread((uint32_t)qx) | (spread((uint32_t)qy) << 1);
+    }
+    std::iota(perm, perm + n, 0);
+    std::stable_sort(perm, perm + n, [&](int a, int b) { return key[a] < key[b]; });
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void geo_opts_default(geo_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->nb = 960;
+    o->prec = GEO_PREC_FP64;
+    o->band = 4;
+    o->lowp = 0;
+    o->refine_iters = 2;
+    o->tlr_tol = 1e-9;
+    o->tlr_kmax = 200;
+    o->morton = 1;
+    o->fp64_gemm = 0;
+}
+
+int geo_create(geo_ctx **out, int device, size_t hbm_budget_bytes) {
+    if (!out) return GEO_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return GEO_ECUDA;
+    }
+    if (device < 0 || device >= ndev) return GEO_EINVAL;
+    geo_ctx *ctx = new geo_ctx();
+    ctx->device = device;
+    ctx->budget = hbm_budget_bytes;
+    SetDevice sd(device);
+    if (cudaMalloc(&ctx->st, sizeof(DevStatus)) != cudaSuccess ||
+        cudaMalloc(&ctx->res, sizeof(DevResults)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_st, sizeof(DevStatus)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_res, sizeof(DevResults)) != cudaSuccess) {
+        cudaGetLastError();
+        geo_destroy(ctx);
+        return GEO_ECUDA;
+    }
+    *out = ctx;
+    return GEO_OK;
+}
+
+int geo_destroy(geo_ctx *ctx) {
+    if (!ctx) return GEO_OK;
+    SetDevice sd(ctx->device);
+    cudaDeviceSynchronize();
+    while (!ctx->factors.empty()) geo_factor_free(ctx->factors.back());
+    if (ctx->ws) dev_free(ctx, ctx->ws, ctx->ws_bytes);
+    if (ctx->st) cudaFree(ctx->st);
+    if (ctx->res) cudaFree(ctx->res);
+    if (ctx->h_st) cudaFreeHost(ctx->h_st);
+    if (ctx->h_res) cudaFreeHost(ctx->h_res);
+    delete ctx;
+    return GEO_OK;
+}
+
+const char *geo_last_error(const geo_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int geo_covgen(geo_ctx *ctx, const double *locs1_dev, int n1, const double *locs2_dev, int n2,
+               const geo_theta *theta, double *out_dev, long long ld, void *stream) {
+    if (!ctx) return GEO_EINVAL;
+    CovParams cp;
+    std::string err;
+    int rc = theta_to_params(theta, &cp, &err);
+    if (rc) return fail(ctx, rc, err);
+    if (n1 < 0 || (locs2_dev && n2 < 0)) return fail(ctx, GEO_EINVAL, "negative size");
+    if (!locs2_dev) n2 = n1;
+    if (ld < (long long)cp.p * n1) return fail(ctx, GEO_EINVAL, "ld < p * n1");
+    if ((n1 > 0 && (!locs1_dev || !out_dev))) return fail(ctx, GEO_EINVAL, "NULL pointer");
+    SetDevice sd(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(launch_covgen_rect(cp, locs1_dev, n1, locs2_dev ? locs2_dev : locs1_dev, n2, out_dev, ld, s));
+    return GEO_OK;
+}
+
+// Shared front half of loglik / simulate: order locations, generate Sigma.
+static int prepare_matrix(geo_ctx *ctx, const double *locs_dev, int n, const geo_theta *theta,
+                          const geo_opts *o, int extra_rows, geo_factor *f, cudaStream_t s) {
+    std::string err;
+    int rc = theta_to_params(theta, &f->cp, &err);
+    if (rc) return fail(ctx, rc, err);
+    const int p = theta->p;
+    f->n = n;
+    f->p = p;
+    f->N = p * n;
+    f->nb = o->nb;
+    f->prec = o->prec;
+    f->ld = round_up((long long)f->N + extra_rows, 32);
+    // location order
+    std::vector<double> h_locs((size_t)2 * n);
+    CK(cudaMemcpyAsync(h_locs.data(), locs_dev, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int k = 0; k < 2 * n; ++k)
+        if (!isfinite(h_locs[k])) return fail(ctx, GEO_EINVAL, "non-finite location");
+    f->perm.resize(n);
+    if (o->morton)
+        morton_perm_host(h_locs.data(), n, f->perm.data());
+    else
+        std::iota(f->perm.begin(), f->perm.end(), 0);
+    // device buffers: locations (SoA) + permutation
+    void *p1, *p2;
+    if ((rc = dev_alloc(ctx, &p1, sizeof(double) * 2 * n))) return rc;
+    f->lx = (double *)p1;
+    f->ly = f->lx + n;
+    if ((rc = dev_alloc(ctx, &p2, sizeof(int) * n))) return rc;
+    int *d_perm = (int *)p2;
+    CK(cudaMemcpyAsync(d_perm, f->perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    CK(launch_gather_locs(locs_dev, d_perm, n, f->lx, f->ly, s));
+    // matrix
+    const size_t bytes = sizeof(double) * (size_t)f->ld * (size_t)f->N;
+    if (ctx->ws && ctx->ws_bytes >= bytes) {
+        f->A = ctx->ws;
+        f->A_bytes = ctx->ws_bytes;
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+    } else {
+        if (ctx->ws) {
+            CK(cudaStreamSynchronize(s));
+            dev_free(ctx, ctx->ws, ctx->ws_bytes);
+            ctx->ws = nullptr;
+            ctx->ws_bytes = 0;
+        }
+        void *pa;
+        if ((rc = dev_alloc(ctx, &pa, bytes))) {
+            dev_free(ctx, d_perm, sizeof(int) * n);
+            return rc;
+        }
+        f->A = (double *)pa;
+        f->A_bytes = bytes;
+    }
+    CK(cudaMemsetAsync(ctx->st, 0, sizeof(DevStatus), s));
+    CK(launch_covgen_sym(f->cp, f->lx, f->ly, n, f->A, f->ld, s));
+    // keep d_perm alive until the stream has used it
+    CK(cudaStreamSynchronize(s));
+    dev_free(ctx, d_perm, sizeof(int) * n);
+    return GEO_OK;
+}
+
+static void release_factor_buffers(geo_ctx *ctx, geo_factor *f, bool keep_matrix_as_ws) {
+    if (f->A) {
+        if (keep_matrix_as_ws && !ctx->ws) {
+            ctx->ws = f->A;
+            ctx->ws_bytes = f->A_bytes;
+        } else {
+            dev_free(ctx, f->A, f->A_bytes);
+        }
+        f->A = nullptr;
+    }
+    if (f->lx) dev_free(ctx, f->lx, sizeof(double) * 2 * f->n);
+    if (f->w) dev_free(ctx, f->w, sizeof(double) * f->N);
+    f->lx = f->ly = f->w = nullptr;
+}
+
+int geo_loglik(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev, const geo_theta *theta,
+               const geo_opts *opts, double *loglik_host, geo_factor **keep, int *info, void *stream) {
+    if (!ctx) return GEO_EINVAL;
+    if (keep) *keep = nullptr;
+    if (info) *info = 0;
+    geo_opts o;
+    if (opts)
+        o = *opts;
+    else
+        geo_opts_default(&o);
+    if (n <= 0 || !locs_dev || !z_dev) return fail(ctx, GEO_EINVAL, "n must be > 0 and pointers non-NULL");
+    if (o.nb < 64) return fail(ctx, GEO_EINVAL, "nb must be >= 64");
+    if (o.prec != GEO_PREC_FP64) return fail(ctx, GEO_EUNSUPPORTED, "precision mode not built");
+    SetDevice sd(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    geo_factor *f = new geo_factor();
+    f->ctx = ctx;
+    int rc = prepare_matrix(ctx, locs_dev, n, theta, &o, 1, f, s);
+    if (rc) {
+        release_factor_buffers(ctx, f, false);
+        delete f;
+        return rc;
+    }
+    const int N = f->N;
+    // z' into row N (internal order)
+    void *pp;
+    if ((rc = dev_alloc(ctx, &pp, sizeof(int) * n))) {
+        release_factor_buffers(ctx, f, true);
+        delete f;
+        return rc;
+    }
+    int *d_perm = (int *)pp;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(d_perm, f->perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s)) ||
+        (e = launch_gather_vec(z_dev, d_perm, n, f->p, f->A + N, f->ld, s)) ||
+        (e = chol64_factor(f->A, f->ld, N, N + 1, o.nb, ctx->st, s)) ||
+        (e = launch_loglik_reduce(f->A, f->ld, N, f->A + N, f->ld, ctx->st, ctx->res, s)) ||
+        (e = cudaMemcpyAsync(ctx->h_res, ctx->res, sizeof(DevResults), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s))) {
+        dev_free(ctx, d_perm, sizeof(int) * n);
+        release_factor_buffers(ctx, f, false);
+        delete f;
+        return cuda_fail(ctx, e, "geo_loglik");
+    }
+    dev_free(ctx, d_perm, sizeof(int) * n);
+    if (ctx->h_st->info) {
+        if (info) *info = ctx->h_st->info;
+        if (loglik_host) *loglik_host = nan("");
+        release_factor_buffers(ctx, f, true);
+        delete f;
+        return fail(ctx, GEO_ENOTSPD, "Sigma(theta) is not positive definite (row " +
+                                          std::to_string(ctx->h_st->info) + ")");
+    }
+    f->loglik = ctx->h_res->loglik;
+    f->logdet = ctx->h_res->logdet;
+    f->quad = ctx->h_res->quad;
+    if (loglik_host) *loglik_host = f->loglik;
+    if (keep) {
+        ctx->factors.push_back(f);
+        *keep = f;
+    } else {
+        release_factor_buffers(ctx, f, true);
+        delete f;
+    }
+    return GEO_OK;
+}
+
+int geo_predict(geo_ctx *ctx, const geo_factor *factor, const double *new_locs_dev, int m, double *zhat_dev,
+                void *stream) {
+    if (!ctx || !factor) return GEO_EINVAL;
+    if (m < 0) return fail(ctx, GEO_EINVAL, "m < 0");
+    if (m == 0) return GEO_OK;
+    if (!new_locs_dev || !zhat_dev) return fail(ctx, GEO_EINVAL, "NULL pointer");
+    SetDevice sd(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    geo_factor *f = const_cast<geo_factor *>(factor);
+    if (!f->w) {
+        void *pw;
+        int rc = dev_alloc(ctx, &pw, sizeof(double) * f->N);
+        if (rc) return rc;
+        f->w = (double *)pw;
+        CK(backward_solve(f->A, f->ld, f->N, f->A + f->N, f->ld, f->w, s));
+    }
+    CK(launch_predict(f->cp, new_locs_dev, m, f->lx, f->ly, f->n, f->w, zhat_dev, s));
+    return GEO_OK;
+}
+
+int geo_simulate(geo_ctx *ctx, const double *locs_dev, int n, const double *e_dev, const geo_theta *theta,
+                 const geo_opts *opts, double *z_dev, int *info, void *stream) {
+    if (!ctx) return GEO_EINVAL;
+    if (info) *info = 0;
+    geo_opts o;
+    if (opts)
+        o = *opts;
+    else
+        geo_opts_default(&o);
+    if (n <= 0 || !locs_dev || !e_dev || !z_dev) return fail(ctx, GEO_EINVAL, "bad arguments");
+    SetDevice sd(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    geo_factor f;
+    f.ctx = ctx;
+    int rc = prepare_matrix(ctx, locs_dev, n, theta, &o, 0, &f, s);
+    if (rc) {
+        release_factor_buffers(ctx, &f, false);
+        return rc;
+    }
+    const int N = f.N;
+    void *pz, *pp;
+    if ((rc = dev_alloc(ctx, &pz, sizeof(double) * N))) {
+        release_factor_buffers(ctx, &f, true);
+        return rc;
+    }
+    if ((rc = dev_alloc(ctx, &pp, sizeof(int) * n))) {
+        dev_free(ctx, pz, sizeof(double) * N);
+        release_factor_buffers(ctx, &f, true);
+        return rc;
+    }
+    double *zs = (double *)pz;
+    int *d_perm = (int *)pp;
+    cudaError_t e;
+    if ((e = chol64_factor(f.A, f.ld, N, N, o.nb, ctx->st, s)) ||
+        (e = launch_trmv_lower(f.A, f.ld, N, e_dev, zs, s)) ||
+        (e = cudaMemcpyAsync(d_perm, f.perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s)) ||
+        (e = launch_scatter_vec(zs, 1, d_perm, n, f.p, z_dev, s)) ||
+        (e = cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s))) {
+        rc = cuda_fail(ctx, e, "geo_simulate");
+    }
+    dev_free(ctx, zs, sizeof(double) * N);
+    dev_free(ctx, d_perm, sizeof(int) * n);
+    release_factor_buffers(ctx, &f, true);
+    if (rc) return rc;
+    if (ctx->h_st->info) {
+        if (info) *info = ctx->h_st->info;
+        return fail(ctx, GEO_ENOTSPD, "Sigma(theta) is not positive definite");
+    }
+    return GEO_OK;
+}
+
+int geo_factor_stats_get(const geo_factor *f, geo_factor_stats *out) {
+    if (!f || !out) return GEO_EINVAL;
+    memset(out, 0, sizeof(*out));
+    out->n = f->n;
+    out->p = f->p;
+    out->N = f->N;
+    out->nb = f->nb;
+    out->prec = f->prec;
+    out->loglik = f->loglik;
+    out->logdet = f->logdet;
+    out->quad = f->quad;
+    out->device_bytes = (long long)(f->A_bytes + sizeof(double) * 2 * f->n + (f->w ? sizeof(double) * f->N : 0));
+    out->tlr_bytes_ratio = 1.0;
+    return GEO_OK;
+}
+
+int geo_factor_read(const geo_factor *f, int what, long long r0, long long r1, long long c0, long long c1,
+                    double *host_out) {
+    if (!f || !host_out) return GEO_EINVAL;
+    geo_ctx *ctx = f->ctx;
+    SetDevice sd(ctx->device);
+    if (what == 0) {
+        if (r0 < 0 || c0 < 0 || r1 > f->N || c1 > f->N || r1 < r0 || c1 < c0)
+            return fail(ctx, GEO_EINVAL, "block out of range");
+        const long long nr = r1 - r0, nc = c1 - c0;
+        std::vector<double> col((size_t)std::max(nr, 1LL));
+        for (long long c = c0; c < c1; ++c) {
+            if (nr > 0) CK(cudaMemcpy(col.data(), f->A + c * f->ld + r0, sizeof(double) * nr, cudaMemcpyDeviceToHost));
+            for (long long r = r0; r < r1; ++r) host_out[(r - r0) * nc + (c - c0)] = (r >= c) ? col[r - r0] : 0.0;
+        }
+        return GEO_OK;
+    }
+    if (what == 1) {
+        if (r0 < 0 || r1 > f->N || r1 < r0) return fail(ctx, GEO_EINVAL, "range out of bounds");
+        for (long long k = r0; k < r1; ++k)
+            CK(cudaMemcpy(host_out + (k - r0), f->A + k * f->ld + f->N, sizeof(double), cudaMemcpyDeviceToHost));
+        return GEO_OK;
+    }
+    if (what == 2) {
+        if (r0 < 0 || r1 > f->n || r1 < r0) return fail(ctx, GEO_EINVAL, "range out of bounds");
+        for (long long k = r0; k < r1; ++k) host_out[k - r0] = (double)f->perm[k];
+        return GEO_OK;
+    }
+    return fail(ctx, GEO_EINVAL, "unknown 'what'");
+}
+
+void geo_factor_free(geo_factor *f) {
+    if (!f) return;
+    geo_ctx *ctx = f->ctx;
+    SetDevice sd(ctx->device);
+    cudaDeviceSynchronize();
+    release_factor_buffers(ctx, f, false);
+    auto it = std::find(ctx->factors.begin(), ctx->factors.end(), f);
+    if (it != ctx->factors.end()) ctx->factors.erase(it);
+    delete f;
+}
+
+int geo_morton_order(const double *locs_host, int n, int *perm_host) {
+    if (n < 0 || (n > 0 && (!locs_host || !perm_host))) return GEO_EINVAL;
+    morton_perm_host(locs_host, n, perm_host);
+    return GEO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,69 @@
+// Internal declarations shared by the translation units of libgeo.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "geo.h"
+#include "matern.cuh"
+
+// Status words the kernels write (device memory of the context).
+struct DevStatus {
+    int info;      // 0, or 1-based row of the first non-positive pivot
+    int timeout;   // a bounded wait expired (code of the wait site)
+    int pad[2];
+};
+
+// Device scalars of one likelihood evaluation.
+struct DevResults {
+    double loglik, logdet, quad, pad;
+};
+
+// Matrix view: column-major, A[c * ld + r].
+struct MatView {
+    double *a;
+    long long ld;
+};
+
+// ---- covgen.cu ----------------------------------------------------------
+// Lower triangle of Sigma (order p*n) into A (column-major, ld), from
+// SoA locations; the full p x p block on the location diagonal.
+cudaError_t launch_covgen_sym(const CovParams &cp, const double *lx, const double *ly, int n, double *A,
+                              long long ld, cudaStream_t s);
+// Full rectangular cross-covariance, rows p*n1 (locations 1), cols p*n2.
+cudaError_t launch_covgen_rect(const CovParams &cp, const double *l1, int n1, const double *l2, int n2,
+                               double *out, long long ld, cudaStream_t s);
+// zhat[p*l + i] = sum_{r,j} C_ij(|s0_l - s_r|) w[p*r + j]; s0 interleaved (x,y), s SoA.
+cudaError_t launch_predict(const CovParams &cp, const double *new_locs, int m, const double *lx,
+                           const double *ly, int n, const double *w, double *zhat, cudaStream_t s);
+// AoS (x, y) -> SoA gathered by perm (device ints).
+cudaError_t launch_gather_locs(const double *locs, const int *perm, int n, double *lx, double *ly,
+                               cudaStream_t s);
+// out[k] = in[perm-ordered Rep. I]: out[p*k + i] = in[p*perm[k] + i], strided store (stride for out).
+cudaError_t launch_gather_vec(const double *in, const int *perm, int n, int p, double *out, long long stride,
+                              cudaStream_t s);
+cudaError_t launch_scatter_vec(const double *in, long long stride, const int *perm, int n, int p, double *out,
+                               cudaStream_t s);
+
+// ---- chol64.cu ----------------------------------------------------------
+// In-place lower Cholesky of the leading N x N block of A; rows N..nrows-1
+// are extra right-hand-side rows carried through the factorisation (row N
+// receives (L^-1 z)' when it holds z').  nb = outer tile size.
+cudaError_t chol64_factor(double *A, long long ld, int N, int nrows, int nb, DevStatus *st, cudaStream_t s);
+
+// ---- solve.cu -----------------------------------------------------------
+// logdet = 2 sum log L_kk, quad = sum y_k^2 (y = row N of A), loglik = Eq. 1.
+cudaError_t launch_loglik_reduce(const double *A, long long ld, int N, const double *y, long long ystride,
+                                 const DevStatus *st, DevResults *res, cudaStream_t s);
+// w = L^-T y (y strided), w contiguous.
+cudaError_t backward_solve(const double *A, long long ld, int N, const double *y, long long ystride, double *w,
+                           cudaStream_t s);
+// z = L e (lower-triangular matrix-vector product).
+cudaError_t launch_trmv_lower(const double *A, long long ld, int N, const double *e, double *z, cudaStream_t s);
+
+// ---- host helpers (api.cu) ------------------------------------------------
+int theta_to_params(const geo_theta *th, CovParams *cp, std::string *err);
+void morton_perm_host(const double *locs, int n, int *perm);

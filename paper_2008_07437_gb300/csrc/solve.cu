@@ -1,0 +1,150 @@
+// Triangular solves and the reductions of Eq. 1 (Sec. 1).
+//
+// * log|Sigma| = 2 sum_k log L_kk and Z' Sigma^-1 Z = y'y with y = L^-1 Z
+//   (y comes out of the factorisation as an extra row), reduced in FP64 by
+//   one CTA in a fixed order, so the value does not depend on timing.
+// * w = L^-T y for the cokriging weights of Eq. 3: blocked backward
+//   substitution, 64 x 64 diagonal solves in one CTA, and the update of the
+//   remaining right-hand side by warps that each read one column segment of
+//   L (contiguous in the column-major layout).
+// * z = L e for the synthetic draws.
+// These kernels stream L once: they are HBM-bound.
+#include <math.h>
+
+#include "geo_internal.cuh"
+
+namespace {
+
+constexpr int RED_THREADS = 1024;
+
+__global__ void __launch_bounds__(RED_THREADS) k_loglik_reduce(const double *__restrict__ A, long long ld, int N,
+                                                                const double *__restrict__ y, long long ystride,
+                                                                const DevStatus *st, DevResults *res) {
+    __shared__ double s1[RED_THREADS / 32], s2[RED_THREADS / 32];
+    double ld_acc = 0.0, q_acc = 0.0;
+    for (int k = threadIdx.x; k < N; k += RED_THREADS) {
+        ld_acc += log(A[(long long)k * ld + k]);
+        const double v = y[(long long)k * ystride];
+        q_acc += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ld_acc += __shfl_down_sync(0xffffffffu, ld_acc, o);
+        q_acc += __shfl_down_sync(0xffffffffu, q_acc, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        s1[wid] = ld_acc;
+        s2[wid] = q_acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < RED_THREADS / 32; ++w) {
+            a += s1[w];
+            b += s2[w];
+        }
+        const double logdet = 2.0 * a;
+        if (st->info) {
+            res->loglik = res->logdet = res->quad = nan("");
+        } else {
+            res->logdet = logdet;
+            res->quad = b;
+            res->loglik = -0.5 * (double)N * log(2.0 * 3.141592653589793) - 0.5 * logdet - 0.5 * b;
+        }
+    }
+}
+
+constexpr int BS = 64;   // backward-solve block
+
+// Solve L[j0:j0+jb, j0:j0+jb]' w = r (r = rhs segment, already updated); one CTA.
+__global__ void __launch_bounds__(BS) k_trsv_ut_diag(const double *__restrict__ A, long long ld, int j0, int jb,
+                                                    double *r, double *w) {
+    __shared__ double Ls[BS][BS + 1];   // Ls[c][r] = L[j0 + r, j0 + c]
+    __shared__ double x[BS];
+    for (int c = 0; c < jb; ++c) {
+        const int rr = threadIdx.x;
+        if (rr < jb) Ls[c][rr] = A[(long long)(j0 + c) * ld + j0 + rr];
+    }
+    if (threadIdx.x < jb) x[threadIdx.x] = r[j0 + threadIdx.x];
+    __syncthreads();
+    // L' is upper triangular: w_c = (x_c - sum_{k > c} L[k][c] w_k) / L[c][c], from the bottom
+    if (threadIdx.x == 0) {
+        for (int c = jb - 1; c >= 0; --c) {
+            double t = x[c];
+            for (int k = c + 1; k < jb; ++k) t -= Ls[c][k] * x[k];
+            x[c] = t / Ls[c][c];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < jb) w[j0 + threadIdx.x] = x[threadIdx.x];
+}
+
+// r[c] -= sum_{k < jb} L[j0 + k, c] w[j0 + k] for c < j0: one warp per column.
+__global__ void __launch_bounds__(256) k_gemv_t_update(const double *__restrict__ A, long long ld, int j0, int jb,
+                                                       const double *__restrict__ w, double *r) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= j0) return;
+    const double *col = A + (long long)warp * ld + j0;
+    double t = 0.0;
+    for (int k = lane; k < jb; k += 32) t += col[k] * w[j0 + k];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) r[warp] -= t;
+}
+
+__global__ void k_copy_strided(const double *__restrict__ in, long long stride, int N, double *out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < N) out[k] = in[(long long)k * stride];
+}
+
+// z[i] = sum_{k <= i} L[i, k] e[k]; one thread per row, columns in chunks staged in shared memory.
+__global__ void __launch_bounds__(256) k_trmv_lower(const double *__restrict__ A, long long ld, int N,
+                                                   const double *__restrict__ e, double *z) {
+    __shared__ double es[256];
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    const int imax = min(N - 1, blockIdx.x * 256 + 255);
+    double t = 0.0;
+    for (int k0 = 0; k0 <= imax; k0 += 256) {
+        __syncthreads();
+        es[threadIdx.x] = (k0 + threadIdx.x < N) ? e[k0 + threadIdx.x] : 0.0;
+        __syncthreads();
+        if (i < N) {
+            const int kend = min(256, i - k0 + 1);
+            for (int kk = 0; kk < kend; ++kk) t += A[(long long)(k0 + kk) * ld + i] * es[kk];
+        }
+    }
+    if (i < N) z[i] = t;
+}
+
+}  // namespace
+
+cudaError_t launch_loglik_reduce(const double *A, long long ld, int N, const double *y, long long ystride,
+                                 const DevStatus *st, DevResults *res, cudaStream_t s) {
+    k_loglik_reduce<<<1, RED_THREADS, 0, s>>>(A, ld, N, y, ystride, st, res);
+    return cudaGetLastError();
+}
+
+// w = L^-T y.  r (the running right-hand side) lives in w's buffer: w is
+// overwritten block by block from the bottom, the blocks above still hold
+// the partially updated right-hand side.
+cudaError_t backward_solve(const double *A, long long ld, int N, const double *y, long long ystride, double *w,
+                           cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    k_copy_strided<<<(N + 255) / 256, 256, 0, s>>>(y, ystride, N, w);
+    const int nblk = (N + BS - 1) / BS;
+    for (int b = nblk - 1; b >= 0; --b) {
+        const int j0 = b * BS, jb = min(BS, N - j0);
+        k_trsv_ut_diag<<<1, BS, 0, s>>>(A, ld, j0, jb, w, w);
+        if (j0 > 0) {
+            const int threads = j0 * 32;
+            k_gemv_t_update<<<(threads + 255) / 256, 256, 0, s>>>(A, ld, j0, jb, w, w);
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trmv_lower(const double *A, long long ld, int N, const double *e, double *z, cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    k_trmv_lower<<<(N + 255) / 256, 256, 0, s>>>(A, ld, N, e, z);
+    return cudaGetLastError();
+}
