@@ -222,6 +222,38 @@ int geo_mle_step(geo_ctx *ctx, geo_mle_state *state, const double *locs_dev, int
 int geo_mle_best(const geo_mle_state *state, double *sigma2, double *a, double *nu, double *beta,
                  double *loglik);
 
+/*
+ * Device-time profile per kernel class, measured with CUDA events recorded
+ * on the stream each kernel is launched on (no paper counterpart: the
+ * paper's timing is wall-clock per phase, Sec. 6.1 / Sec. 6.3).
+ *   geo_profile_enable(ctx, 1) clears the counters and starts recording events
+ *   around every launch; 0 stops recording (launch counting never stops).
+ *   geo_profile_read synchronises the device, resolves the recorded events
+ *   and fills out[0 .. GEO_K_COUNT-1]; flops / bytes are the algorithmic
+ *   work of the launches (lower-triangle flops for the Cholesky updates).
+ */
+enum {
+    GEO_K_COVGEN = 0,   /* Eq. 2 matrix generation */
+    GEO_K_POTRF = 1,    /* diagonal-block Cholesky */
+    GEO_K_TRSM = 2,     /* panel triangular solves */
+    GEO_K_GEMM = 3,     /* trailing / panel updates (SYRK + GEMM) */
+    GEO_K_REDUCE = 4,   /* log-determinant and quadratic form */
+    GEO_K_SOLVE = 5,    /* backward substitution L' w = y */
+    GEO_K_PREDICT = 6,  /* fused cross-covariance + GEMV of Eq. 3 */
+    GEO_K_AUX = 7,      /* gathers, scatters, conversions */
+    GEO_K_COUNT = 8
+};
+typedef struct {
+    long long launches;
+    double ms;        /* summed device time of the launches that were timed */
+    double flops;     /* algorithmic floating-point operations */
+    double bytes;     /* algorithmic HBM bytes */
+    long long timed;  /* launches with events */
+} geo_kstat;
+
+int geo_profile_enable(geo_ctx *ctx, int enable);
+int geo_profile_read(geo_ctx *ctx, geo_kstat *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,6 +57,15 @@ class geo_mle_state(ctypes.Structure):
                 ("f", ctypes.c_double * (GEO_MLE_QMAX + 1)), ("last_f", ctypes.c_double)]
 
 
+GEO_K_NAMES = ["covgen", "potrf", "trsm", "gemm", "reduce", "solve", "predict", "aux"]
+GEO_K_COUNT = len(GEO_K_NAMES)
+
+
+class geo_kstat(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("ms", ctypes.c_double), ("flops", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("timed", ctypes.c_longlong)]
+
+
 # every symbol include/geo.h declares, with (restype, argtypes)
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -80,6 +89,8 @@ SIGNATURES = {
     "geo_mle_init": (_I, [ctypes.POINTER(geo_mle_state), ctypes.POINTER(geo_theta), _D]),
     "geo_mle_step": (_I, [_P, ctypes.POINTER(geo_mle_state), _P, _I, _P, ctypes.POINTER(geo_opts), _P]),
     "geo_mle_best": (_I, [ctypes.POINTER(geo_mle_state), _P, _P, _P, _P, _P]),
+    "geo_profile_enable": (_I, [_P, _I]),
+    "geo_profile_read": (_I, [_P, ctypes.POINTER(geo_kstat)]),
 }
 
 _lib = None
@@ -335,3 +346,17 @@ def geo_mle_best(state: geo_mle_state):
     if rc != GEO_OK:
         raise GeoError(rc, "geo_mle_best")
     return Theta(tuple(s2), a.value, tuple(nu), beta.reshape(p, p)), ll.value
+
+
+def geo_profile_enable(ctx: Context, enable: bool = True):
+    """Clear the per-kernel-class counters and (stop) recording CUDA events around launches."""
+    ctx.check(ctx.lib.geo_profile_enable(ctx.handle, 1 if enable else 0))
+
+
+def geo_profile_read(ctx: Context) -> dict:
+    """{class: {launches, ms, flops, bytes, timed}} for every kernel class."""
+    arr = (geo_kstat * GEO_K_COUNT)()
+    ctx.check(ctx.lib.geo_profile_read(ctx.handle, arr))
+    return {GEO_K_NAMES[k]: dict(launches=arr[k].launches, ms=arr[k].ms, flops=arr[k].flops,
+                                 bytes=arr[k].bytes, timed=arr[k].timed) for k in range(GEO_K_COUNT)}
+

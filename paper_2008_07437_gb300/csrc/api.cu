@@ -32,6 +32,7 @@ struct geo_ctx {
     double *ws = nullptr;
     size_t ws_bytes = 0;
     std::vector<geo_factor *> factors;
+    Profiler prof;
 };
 
 struct geo_factor {
@@ -45,6 +46,61 @@ struct geo_factor {
     std::vector<int> perm;                 // internal k -> caller location perm[k]
     CovParams cp;
     double loglik = 0, logdet = 0, quad = 0;
+};
+
+thread_local Profiler *t_prof = nullptr;
+
+cudaEvent_t Profiler::take() {
+    if (pool_used == pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        pool.push_back(e);
+    }
+    return pool[pool_used++];
+}
+
+void Profiler::resolve() {
+    for (const Rec &r : recs) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+            ms[r.cls] += t;
+            timed[r.cls] += 1;
+        }
+    }
+    recs.clear();
+    pool_used = 0;
+}
+
+void Profiler::clear() {
+    recs.clear();
+    pool_used = 0;
+    for (int k = 0; k < GEO_K_COUNT; ++k) launches[k] = timed[k] = 0, flops[k] = bytes[k] = ms[k] = 0.0;
+}
+
+KScope::KScope(int cls_, cudaStream_t s_, double fl, double by) : p(t_prof), cls(cls_), s(s_) {
+    if (!p) return;
+    p->launches[cls] += 1;
+    p->flops[cls] += fl;
+    p->bytes[cls] += by;
+    if (p->enabled) {
+        a = p->take();
+        if (a) cudaEventRecord(a, s);
+    }
+}
+
+KScope::~KScope() {
+    if (!p || !a) return;
+    cudaEvent_t b = p->take();
+    if (!b) return;
+    cudaEventRecord(b, s);
+    p->recs.push_back({cls, a, b});
+}
+
+// Points t_prof at a context's profiler for the duration of an API call.
+struct ProfBind {
+    Profiler *prev;
+    explicit ProfBind(Profiler *p) : prev(t_prof) { t_prof = p; }
+    ~ProfBind() { t_prof = prev; }
 };
 
 namespace {
@@ -292,6 +348,7 @@ int geo_destroy(geo_ctx *ctx) {
     SetDevice sd(ctx->device);
     cudaDeviceSynchronize();
     while (!ctx->factors.empty()) geo_factor_free(ctx->factors.back());
+    for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
     if (ctx->ws) dev_free(ctx, ctx->ws, ctx->ws_bytes);
     if (ctx->st) cudaFree(ctx->st);
     if (ctx->res) cudaFree(ctx->res);
@@ -306,6 +363,7 @@ const char *geo_last_error(const geo_ctx *ctx) { return ctx ? ctx->err.c_str() :
 int geo_covgen(geo_ctx *ctx, const double *locs1_dev, int n1, const double *locs2_dev, int n2,
                const geo_theta *theta, double *out_dev, long long ld, void *stream) {
     if (!ctx) return GEO_EINVAL;
+    ProfBind pb(&ctx->prof);
     CovParams cp;
     std::string err;
     int rc = theta_to_params(theta, &cp, &err);
@@ -401,6 +459,7 @@ static void release_factor_buffers(geo_ctx *ctx, geo_factor *f, bool keep_matrix
 int geo_loglik(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev, const geo_theta *theta,
                const geo_opts *opts, double *loglik_host, geo_factor **keep, int *info, void *stream) {
     if (!ctx) return GEO_EINVAL;
+    ProfBind pb(&ctx->prof);
     if (keep) *keep = nullptr;
     if (info) *info = 0;
     geo_opts o;
@@ -469,6 +528,7 @@ int geo_loglik(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev,
 int geo_predict(geo_ctx *ctx, const geo_factor *factor, const double *new_locs_dev, int m, double *zhat_dev,
                 void *stream) {
     if (!ctx || !factor) return GEO_EINVAL;
+    ProfBind pb(&ctx->prof);
     if (m < 0) return fail(ctx, GEO_EINVAL, "m < 0");
     if (m == 0) return GEO_OK;
     if (!new_locs_dev || !zhat_dev) return fail(ctx, GEO_EINVAL, "NULL pointer");
@@ -489,6 +549,7 @@ int geo_predict(geo_ctx *ctx, const geo_factor *factor, const double *new_locs_d
 int geo_simulate(geo_ctx *ctx, const double *locs_dev, int n, const double *e_dev, const geo_theta *theta,
                  const geo_opts *opts, double *z_dev, int *info, void *stream) {
     if (!ctx) return GEO_EINVAL;
+    ProfBind pb(&ctx->prof);
     if (info) *info = 0;
     geo_opts o;
     if (opts)
@@ -589,10 +650,36 @@ void geo_factor_free(geo_factor *f) {
     geo_ctx *ctx = f->ctx;
     SetDevice sd(ctx->device);
     cudaDeviceSynchronize();
-    release_factor_buffers(ctx, f, false);
+    release_factor_buffers(ctx, f, true);   // the matrix buffer becomes the context's workspace
     auto it = std::find(ctx->factors.begin(), ctx->factors.end(), f);
     if (it != ctx->factors.end()) ctx->factors.erase(it);
     delete f;
+}
+
+int geo_profile_enable(geo_ctx *ctx, int enable) {
+    if (!ctx) return GEO_EINVAL;
+    SetDevice sd(ctx->device);
+    if (enable) {
+        cudaDeviceSynchronize();
+        ctx->prof.clear();
+    }
+    ctx->prof.enabled = enable != 0;
+    return GEO_OK;
+}
+
+int geo_profile_read(geo_ctx *ctx, geo_kstat *out) {
+    if (!ctx || !out) return GEO_EINVAL;
+    SetDevice sd(ctx->device);
+    CK(cudaDeviceSynchronize());
+    ctx->prof.resolve();
+    for (int k = 0; k < GEO_K_COUNT; ++k) {
+        out[k].launches = ctx->prof.launches[k];
+        out[k].ms = ctx->prof.ms[k];
+        out[k].flops = ctx->prof.flops[k];
+        out[k].bytes = ctx->prof.bytes[k];
+        out[k].timed = ctx->prof.timed[k];
+    }
+    return GEO_OK;
 }
 
 int geo_morton_order(const double *locs_host, int n, int *perm_host) {

@@ -170,6 +170,10 @@ cudaError_t gemm_update(double *A, long long ld, int rC, int cC, int m, int n, i
                         cudaStream_t s) {
     if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
     dim3 grid((m + GT - 1) / GT, (n + GT - 1) / GT);
+    // algorithmic work: the lower-triangle entries of C (rC == cC here), 2k flops each
+    const double nn = n, mm = m;
+    const double entries = (rC == cC) ? (nn * mm - nn * (nn - 1.0) / 2.0) : nn * mm;
+    KScope ks(GEO_K_GEMM, s, 2.0 * k * entries, 8.0 * (2.0 * entries + (mm + nn) * k));
     k_dgemm_update<<<grid, 256, 0, s>>>(A, ld, rC, cC, m, n, kA, k, st);
     return cudaGetLastError();
 }
@@ -186,10 +190,14 @@ cudaError_t chol64_factor(double *A, long long ld, int N, int nrows, int nb, Dev
         const int jb = min(nb, N - j0);
         for (int c0 = j0; c0 < j0 + jb; c0 += IB) {
             const int cb = min(IB, j0 + jb - c0);
-            k_potrf_diag<<<1, 256, 0, s>>>(A, ld, c0, cb, st);
+            {
+                KScope ks(GEO_K_POTRF, s, (double)cb * cb * cb / 3.0, 16.0 * cb * cb);
+                k_potrf_diag<<<1, 256, 0, s>>>(A, ld, c0, cb, st);
+            }
             const int rows0 = c0 + cb;
             if (rows0 < nrows) {
                 const int nr = nrows - rows0;
+                KScope ks(GEO_K_TRSM, s, (double)nr * cb * cb, 16.0 * nr * cb);
                 k_trsm_rlt<<<(nr + TRSM_ROWS - 1) / TRSM_ROWS, 256, trsm_smem, s>>>(A, ld, c0, cb, rows0, nrows, st);
             }
             if ((e = cudaGetLastError()) != cudaSuccess) return e;

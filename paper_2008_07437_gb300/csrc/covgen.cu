@@ -134,6 +134,8 @@ cudaError_t launch_covgen_sym(const CovParams &cp, const double *lx, const doubl
                               long long ld, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     dim3 grid((n + TR - 1) / TR, (n + TL - 1) / TL);
+    const double N = (double)cp.p * n;
+    KScope ks(GEO_K_COVGEN, s, 0.0, 8.0 * N * (N + cp.p) / 2.0);   // bytes: lower triangle written once
     k_covgen_sym<<<grid, TL * TR, 0, s>>>(cp, lx, ly, n, A, ld);
     return cudaGetLastError();
 }
@@ -142,6 +144,7 @@ cudaError_t launch_covgen_rect(const CovParams &cp, const double *l1, int n1, co
                                double *out, long long ld, cudaStream_t s) {
     if (n1 <= 0 || n2 <= 0) return cudaSuccess;
     dim3 grid((n2 + TR - 1) / TR, (n1 + TL - 1) / TL);
+    KScope ks(GEO_K_COVGEN, s, 0.0, 8.0 * cp.p * (double)n1 * cp.p * (double)n2);
     k_covgen_rect<<<grid, TL * TR, 0, s>>>(cp, l1, n1, l2, n2, out, ld);
     return cudaGetLastError();
 }
@@ -149,6 +152,7 @@ cudaError_t launch_covgen_rect(const CovParams &cp, const double *l1, int n1, co
 cudaError_t launch_predict(const CovParams &cp, const double *new_locs, int m, const double *lx,
                            const double *ly, int n, const double *w, double *zhat, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
+    KScope ks(GEO_K_PREDICT, s, 2.0 * cp.p * (double)m * cp.p * (double)n, 16.0 * n + 24.0 * m);
     k_predict<<<m, PRED_THREADS, 0, s>>>(cp, new_locs, lx, ly, n, w, zhat);
     return cudaGetLastError();
 }
@@ -156,6 +160,7 @@ cudaError_t launch_predict(const CovParams &cp, const double *new_locs, int m, c
 cudaError_t launch_gather_locs(const double *locs, const int *perm, int n, double *lx, double *ly,
                                cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
+    KScope ks(GEO_K_AUX, s);
     k_gather_locs<<<(n + 255) / 256, 256, 0, s>>>(locs, perm, n, lx, ly);
     return cudaGetLastError();
 }
@@ -164,6 +169,7 @@ cudaError_t launch_gather_vec(const double *in, const int *perm, int n, int p, d
                               cudaStream_t s) {
     const long long t = (long long)n * p;
     if (t <= 0) return cudaSuccess;
+    KScope ks(GEO_K_AUX, s);
     k_gather_vec<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(in, perm, n, p, out, stride);
     return cudaGetLastError();
 }
@@ -172,6 +178,7 @@ cudaError_t launch_scatter_vec(const double *in, long long stride, const int *pe
                                cudaStream_t s) {
     const long long t = (long long)n * p;
     if (t <= 0) return cudaSuccess;
+    KScope ks(GEO_K_AUX, s);
     k_scatter_vec<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(in, stride, perm, n, p, out);
     return cudaGetLastError();
 }

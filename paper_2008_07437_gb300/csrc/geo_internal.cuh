@@ -28,6 +28,39 @@ struct MatView {
     long long ld;
 };
 
+// ---- per-launch profiling (api.cu) ---------------------------------------
+// The API entry points point t_prof at their context's profiler; every
+// launch site opens a KScope, which counts the launch and, when recording is
+// on, brackets it with CUDA events on the launching stream.
+struct Profiler {
+    bool enabled = false;
+    long long launches[GEO_K_COUNT] = {};
+    long long timed[GEO_K_COUNT] = {};
+    double flops[GEO_K_COUNT] = {};
+    double bytes[GEO_K_COUNT] = {};
+    double ms[GEO_K_COUNT] = {};
+    struct Rec {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    size_t pool_used = 0;
+    cudaEvent_t take();
+    void resolve();
+    void clear();
+};
+extern thread_local Profiler *t_prof;
+
+struct KScope {
+    Profiler *p;
+    int cls;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    KScope(int cls_, cudaStream_t s_, double flops = 0.0, double bytes = 0.0);
+    ~KScope();
+};
+
 // ---- covgen.cu ----------------------------------------------------------
 // Lower triangle of Sigma (order p*n) into A (column-major, ld), from
 // SoA locations; the full p x p block on the location diagonal.
@@ -53,6 +86,7 @@ cudaError_t launch_scatter_vec(const double *in, long long stride, const int *pe
 // are extra right-hand-side rows carried through the factorisation (row N
 // receives (L^-1 z)' when it holds z').  nb = outer tile size.
 cudaError_t chol64_factor(double *A, long long ld, int N, int nrows, int nb, DevStatus *st, cudaStream_t s);
+
 
 // ---- solve.cu -----------------------------------------------------------
 // logdet = 2 sum log L_kk, quad = sum y_k^2 (y = row N of A), loglik = Eq. 1.

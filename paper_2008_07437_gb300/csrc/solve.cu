@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(256) k_trmv_lower(const double *__restrict__ A
 
 cudaError_t launch_loglik_reduce(const double *A, long long ld, int N, const double *y, long long ystride,
                                  const DevStatus *st, DevResults *res, cudaStream_t s) {
+    KScope ks(GEO_K_REDUCE, s, 3.0 * N, 16.0 * N);
     k_loglik_reduce<<<1, RED_THREADS, 0, s>>>(A, ld, N, y, ystride, st, res);
     return cudaGetLastError();
 }
@@ -130,13 +131,20 @@ cudaError_t launch_loglik_reduce(const double *A, long long ld, int N, const dou
 cudaError_t backward_solve(const double *A, long long ld, int N, const double *y, long long ystride, double *w,
                            cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
-    k_copy_strided<<<(N + 255) / 256, 256, 0, s>>>(y, ystride, N, w);
+    {
+        KScope ks(GEO_K_AUX, s);
+        k_copy_strided<<<(N + 255) / 256, 256, 0, s>>>(y, ystride, N, w);
+    }
     const int nblk = (N + BS - 1) / BS;
     for (int b = nblk - 1; b >= 0; --b) {
         const int j0 = b * BS, jb = min(BS, N - j0);
-        k_trsv_ut_diag<<<1, BS, 0, s>>>(A, ld, j0, jb, w, w);
+        {
+            KScope ks(GEO_K_SOLVE, s, (double)jb * jb, 8.0 * jb * jb / 2.0);
+            k_trsv_ut_diag<<<1, BS, 0, s>>>(A, ld, j0, jb, w, w);
+        }
         if (j0 > 0) {
             const int threads = j0 * 32;
+            KScope ks(GEO_K_SOLVE, s, 2.0 * j0 * jb, 8.0 * (double)j0 * jb);
             k_gemv_t_update<<<(threads + 255) / 256, 256, 0, s>>>(A, ld, j0, jb, w, w);
         }
     }
@@ -145,6 +153,7 @@ cudaError_t backward_solve(const double *A, long long ld, int N, const double *y
 
 cudaError_t launch_trmv_lower(const double *A, long long ld, int N, const double *e, double *z, cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
+    KScope ks(GEO_K_AUX, s, (double)N * N, 4.0 * (double)N * N);
     k_trmv_lower<<<(N + 255) / 256, 256, 0, s>>>(A, ld, N, e, z);
     return cudaGetLastError();
 }

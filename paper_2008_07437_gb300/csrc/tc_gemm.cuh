@@ -1,0 +1,262 @@
+// Tensor-core (tcgen05) update of far-from-diagonal tiles for the
+// mixed-precision Cholesky:  C[I, J] -= inv_s_I inv_s_J * (A_I B_J')  with
+// A_I, B_J FP16 (per-row-block power-of-two scale s), FP32 accumulation in
+// tensor memory, FP64 C.
+//
+// Per CTA: one 128 x 128 output tile, K in 64-wide blocks.
+//   warp 0 (one lane): TMA producer, 4-stage ring of (A 128x64, B 128x64)
+//                      FP16 tiles in 128-byte-swizzled shared memory;
+//   warp 1: allocates 128 TMEM columns; one lane issues tcgen05.mma
+//           (M = 128, N = 128, K = 16, kind::f16, FP32 accumulate) and
+//           commits each stage back to the producer;
+//   warps 2-5: epilogue, tcgen05.ld of the accumulator (warp w reads TMEM
+//           lanes 32 (w % 4) .. + 31 = tile rows), scale, FP64 read-modify-write
+//           of C with stores contiguous across each warp.
+// Every wait on an mbarrier is bounded by a clock budget; on expiry the
+// thread records an error code in the status word and the CTA drains, frees
+// its TMEM and returns.
+#pragma once
+
+#include <cuda.h>
+#include <stdint.h>
+
+#include "geo_internal.cuh"
+
+namespace tc {
+
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
+constexpr int TILE_A_BYTES = BM * BK * 2;
+constexpr int TILE_B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = TILE_A_BYTES + TILE_B_BYTES;
+constexpr int THREADS = 192;
+constexpr int TMEM_COLS = 128;
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024;   // + alignment slack
+constexpr long long WAIT_CYCLES = 4000000000LL;                        // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the completion of phase `parity`; false on timeout (code recorded).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *timeout_word, int code) {
+    if (mbar_test(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_test(bar, parity)) return true;
+        if (clock64() - t0 > WAIT_CYCLES) {
+            atomicCAS(timeout_word, 0, code);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap *map, uint64_t *bar, void *dst, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (SBO), start address in 16-byte units, descriptor
+// version 1, layout type 2 = SWIZZLE_128B.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+    d |= (uint64_t)1 << 46;                 // descriptor version
+    d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = F16 (or BF16), both K-major, N = 128, M = 128.
+__host__ __device__ constexpr uint32_t instr_desc(int bf16) {
+    return (1u << 4) | ((uint32_t)bf16 << 7) | ((uint32_t)bf16 << 10) | ((uint32_t)(BN >> 3) << 17) |
+           ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Which 128 x 128 output tiles a launch computes: the grid spans the
+// 128-tiles (ti, tj) of rows [r0, r0 + m) x cols [c0, c0 + n); a tile runs
+// when its nb-tile distance |I - J| (I = global row / nb) lies in [dlo, dhi].
+struct TcArgs {
+    double *C;
+    long long ldc;
+    int r0, c0, m, n;      // output region (global indices)
+    int prow0;             // global row of panel row 0 (A / B operand row = global - prow0)
+    int K;                 // panel width (multiple of 64)
+    int nb, dlo, dhi;      // class filter
+    const double *inv_scale;   // per 128-row block of the panel
+    DevStatus *st;
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+    k_tc_update(const __grid_constant__ CUtensorMap map, const TcArgs args, const uint32_t idesc) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], acc_bar;
+    __shared__ uint32_t tmem_slot;
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int gr = args.r0 + blockIdx.x * BM;   // global row of the tile
+    const int gc = args.c0 + blockIdx.y * BN;   // global col of the tile
+    // class filter (uniform across the CTA; decided before any barrier or TMEM use)
+    {
+        const int I = gr / args.nb, J = gc / args.nb;
+        const int I2 = (gr + BM - 1) / args.nb, J2 = (gc + BN - 1) / args.nb;
+        const int dmin = I - J2, dmax = I2 - J;
+        if (dmin < args.dlo || dmax > args.dhi || args.st->info) return;
+    }
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int nk = args.K / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&acc_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    int *tword = &args.st->timeout;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            const int arow = gr - args.prow0, brow = gc - args.prow0;
+            int issued = 0, consumed_ok = 1;
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % STAGES;
+                if (kb >= STAGES) {
+                    if (!mbar_wait(&empty_bar[s], ((kb / STAGES) & 1) ^ 1, tword, 1)) {
+                        consumed_ok = 0;
+                        break;
+                    }
+                }
+                uint8_t *sa = smem + (size_t)s * STAGE_BYTES;
+                uint8_t *sb = sa + TILE_A_BYTES;
+                mbar_arrive_expect_tx(&full_bar[s], STAGE_BYTES);
+                tma_load_2d(&map, &full_bar[s], sa, kb * BK, arow);
+                tma_load_2d(&map, &full_bar[s], sb, kb * BK, brow);
+                ++issued;
+            }
+            if (!consumed_ok) {
+                // drain: wait (bounded) for every copy this thread issued to land
+                for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+                    mbar_wait(&full_bar[kb % STAGES], (kb / STAGES) & 1, tword, 2);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            bool ok = true;
+            for (int kb = 0; kb < nk && ok; ++kb) {
+                const int s = kb % STAGES;
+                if (!mbar_wait(&full_bar[s], (kb / STAGES) & 1, tword, 3)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sa = smem_u32(smem + (size_t)s * STAGE_BYTES);
+                const uint32_t sb = sa + TILE_A_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk) {
+                    mma_f16(tmem, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32), idesc, (kb | kk) != 0);
+                }
+                mma_commit(&empty_bar[s]);
+            }
+            if (ok) mma_commit(&acc_bar);
+        }
+        __syncwarp();
+    } else {
+        // epilogue: warps 2..5, TMEM lane quarter q = warp % 4
+        const int q = warp % 4;
+        const int row = q * 32 + lane;
+        bool ok = mbar_wait(&acc_bar, 0, tword, 4);
+        // all lanes of the warp must take part in tcgen05.ld: agree on ok
+        ok = __all_sync(0xffffffffu, ok);
+        if (ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int grow = gr + row;
+            const double si = args.inv_scale[(gr - args.prow0) / BM];
+            const double sj = args.inv_scale[(gc - args.prow0) / BN];
+            const double sc = si * sj;
+            for (int c = 0; c < BN / 32; ++c) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 32), v);
+                if (grow < args.r0 + args.m) {
+#pragma unroll 4
+                    for (int j = 0; j < 32; ++j) {
+                        const int gcol = gc + c * 32 + j;
+                        if (gcol < args.c0 + args.n) {
+                            double *p = args.C + (long long)gcol * args.ldc + grow;
+                            *p -= sc * (double)v[j];
+                        }
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+}  // namespace tc
