@@ -38,7 +38,8 @@ enum {
     GEO_ENOMEM = 3,      /* the context's HBM budget (or the device) cannot hold the request */
     GEO_ETIMEOUT = 4,    /* a bounded device-side wait expired; the context stays usable */
     GEO_ECUDA = 5,       /* a CUDA runtime call failed; see geo_last_error */
-    GEO_EUNSUPPORTED = 6 /* option combination not implemented */
+    GEO_EUNSUPPORTED = 6, /* option combination not implemented */
+    GEO_ESCRATCH = 7      /* geo_loglik_noalloc: p*n exceeds GEO_NOALLOC_MAX_N */
 };
 
 /* ---- factorisation forms (Sec. 5.2 exact, Sec. 5.3 TLR) ----------------- */
@@ -253,6 +254,44 @@ typedef struct {
 
 int geo_profile_enable(geo_ctx *ctx, int enable);
 int geo_profile_read(geo_ctx *ctx, geo_kstat *out);
+
+/*
+ * geo_loglik_noalloc -- the log-likelihood of geo_loglik for small problems,
+ * for callers that cannot allocate device memory.  The paper has no
+ * counterpart; this is a deployment variant.
+ *
+ * Some callers cannot call cudaMalloc: a host application or framework that
+ * reserved the GPU's memory for its own allocator up front (a cudaMalloc from
+ * this library would then fail or fragment that pool), or a latency-critical
+ * loop that cannot afford cudaMalloc / cudaFree, which may synchronise the
+ * device and may fail at unpredictable times.  This entry point allocates
+ * nothing and needs no context: every intermediate (the covariance matrix and
+ * its factor, the reordered locations, the status words) lives in one
+ * fixed-size array in device global memory owned by the library, about
+ * GEO_NOALLOC_SCRATCH_DOUBLES * 8 bytes (34 MB), which every GPU that loads the
+ * library holds until the process exits.
+ *
+ *   locs_dev  n x 2 locations (device, caller-owned); used in the caller's order
+ *   z_dev     N = p*n observations in Representation I (device)
+ *   theta     host struct as for geo_loglik
+ *   nb        tile size (>= 64)
+ *   out_dev   3 doubles (device, caller-owned): l(theta), log|Sigma|, Z' Sigma^-1 Z;
+ *             l is NaN when Sigma is not positive definite
+ *   info_dev  NULL or one int (device): 0, or the 1-based failing row
+ * The work is only enqueued on `stream`: synchronise it before reading the
+ * outputs.  Returns GEO_ESCRATCH when p*n > GEO_NOALLOC_MAX_N (the scratch is
+ * too small), GEO_EINVAL for other bad arguments, GEO_ECUDA if a launch or the
+ * scratch set-up fails.  The first call on each device looks up the device
+ * address of the scratch array (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  All calls share
+ * the one array, which keeps the previous call's contents (the status words are
+ * cleared at the start of each call): calls that overlap on the GPU race, so
+ * serialise them (one stream, one thread).
+ */
+#define GEO_NOALLOC_MAX_N 2048
+#define GEO_NOALLOC_SCRATCH_DOUBLES 4263938LL
+int geo_loglik_noalloc(const double *locs_dev, int n, const double *z_dev, const geo_theta *theta, int nb,
+                       double *out_dev, int *info_dev, void *stream);
 
 #ifdef __cplusplus
 }

@@ -23,7 +23,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgeo.so")
 
-GEO_OK, GEO_EINVAL, GEO_ENOTSPD, GEO_ENOMEM, GEO_ETIMEOUT, GEO_ECUDA, GEO_EUNSUPPORTED = range(7)
+GEO_OK, GEO_EINVAL, GEO_ENOTSPD, GEO_ENOMEM, GEO_ETIMEOUT, GEO_ECUDA, GEO_EUNSUPPORTED, GEO_ESCRATCH = range(8)
+GEO_NOALLOC_MAX_N = 2048
 GEO_PREC_FP64, GEO_PREC_MIXED, GEO_PREC_TLR = 0, 1, 2
 GEO_PMAX = 4
 GEO_MLE_QMAX = 16
@@ -91,6 +92,7 @@ SIGNATURES = {
     "geo_mle_best": (_I, [ctypes.POINTER(geo_mle_state), _P, _P, _P, _P, _P]),
     "geo_profile_enable": (_I, [_P, _I]),
     "geo_profile_read": (_I, [_P, ctypes.POINTER(geo_kstat)]),
+    "geo_loglik_noalloc": (_I, [_P, _I, _P, ctypes.POINTER(geo_theta), _I, _P, _P, _P]),
 }
 
 _lib = None
@@ -360,3 +362,14 @@ def geo_profile_read(ctx: Context) -> dict:
     return {GEO_K_NAMES[k]: dict(launches=arr[k].launches, ms=arr[k].ms, flops=arr[k].flops,
                                  bytes=arr[k].bytes, timed=arr[k].timed) for k in range(GEO_K_COUNT)}
 
+
+def geo_loglik_noalloc(locs, z, theta: Theta, out, info=None, nb: int = 960, stream=None) -> int:
+    """Eq. 1 without any device allocation (fixed library-owned scratch, p*n <= GEO_NOALLOC_MAX_N).
+    ``out`` (3 doubles) and ``info`` (1 int32, optional) are device tensors written asynchronously on
+    the stream; returns the status code (GEO_OK, GEO_ESCRATCH, ...) without raising."""
+    import torch
+    th, _keep = theta.to_c()
+    return load_library().geo_loglik_noalloc(
+        _dev_ptr(locs, "locs", torch.float64), locs.shape[0], _dev_ptr(z, "z", torch.float64), ctypes.byref(th),
+        int(nb), _dev_ptr(out, "out", torch.float64),
+        _dev_ptr(info, "info", torch.int32) if info is not None else None, _stream(stream))
