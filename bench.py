@@ -41,6 +41,36 @@ from paper_2008_07437_gb300 import inputs  # noqa: E402
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA / clock /
 # SM x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s for GB300).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def measured_peaks():
+    import json as _json
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return _json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# Roofline of each kernel class: (bound, peak, unit, what the peak is).
+def class_roofline(cls):
+    mp = measured_peaks()
+    if cls == "tcgemm":
+        if "bf16_tflops" in mp:
+            return "tensor", float(mp["bf16_tflops"]), "measured cuBLAS bf16 burst (FP16 runs at the bf16 rate)"
+        return "tensor", 1900.0, "fallback 1.9 PFLOP/s bf16 burst"
+    if cls == "sgemm":
+        return "alu", FP32_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
+    return "alu", FP64_PEAK_TFLOPS, "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"
+
+
+KERNEL_NAMES = {"gemm": "k_dgemm_update (FP64 FMA trailing/panel updates)",
+                "sgemm": "k_sgemm_nt (FP32 SIMT diagonal/band and panel updates)",
+                "tcgemm": "k_tc_update (tcgen05 FP16x2 updates beyond the band)",
+                "covgen": "k_covgen_sym (FP64 Matern + Bessel K_nu)"}
 METRIC = "loglik evals/s"
 UNIT = "evals/s"
 
@@ -206,8 +236,12 @@ def run_reference(args):
 
 def config_json(w, args):
     p = w.theta.p
+    form = "dense FP64 tiled Cholesky"
+    if w.extra.get("prec") == 1:
+        form = ("mixed: FP64 diagonal tiles, FP32 band of %d tiles, %s tensor cores beyond, %d FP64 refinement sweeps"
+                % (w.extra.get("band", 4), "BF16" if w.extra.get("lowp") else "FP16x2", w.extra.get("refine_iters", 2)))
     return {"workload": w.name, "n": w.n, "p": p, "N": p * w.n, "nb": w.nb, "n_pred": w.n_pred,
-            "form": "dense FP64 tiled Cholesky", "theta": {"sigma2": list(w.theta.sigma2), "a": w.theta.a,
+            "form": form, "theta": {"sigma2": list(w.theta.sigma2), "a": w.theta.a,
                                                            "nu": list(w.theta.nu), "beta": list(w.theta.beta)},
             "l2": "inputs larger than L2: the %.1f GB matrix is regenerated every step" % (
                 8.0 * (p * w.n) ** 2 / 1e9)}
@@ -241,7 +275,7 @@ def run_ours(args):
     p = w.theta.p
     N = p * w.n
     theta = geo.Theta.from_spec(w.theta)
-    o = geo.opts(nb=w.nb)
+    o = geo.opts(nb=w.nb, **w.extra)
     ctx = geo.geo_create(dev.index)
 
     # ---- setup (untimed): locations and one joint draw Z = L e -------------
@@ -333,23 +367,25 @@ def run_ours(args):
 
     # ---- report ------------------------------------------------------------
     launches = sum(v["launches"] for v in prof.values())
-    gemm = prof["gemm"]
-    gemm_tflops = gemm["flops"] / (gemm["ms"] * 1e-3) / 1e12 if gemm["ms"] > 0 else 0.0
-    chol_ms = (prof["potrf"]["ms"] + prof["trsm"]["ms"] + prof["gemm"]["ms"]) / args.steps
+    # dominant kernel class of the step and its roofline
+    dom = max(("gemm", "sgemm", "tcgemm", "covgen"), key=lambda k: prof[k]["ms"])
+    dk = prof[dom]
+    bound, peak, peak_src = class_roofline(dom)
+    dom_tflops = dk["flops"] / (dk["ms"] * 1e-3) / 1e12 if dk["ms"] > 0 and dk["flops"] > 0 else 0.0
+    chol_ms = sum(prof[k]["ms"] for k in ("potrf", "trsm", "gemm", "sgemm", "tcgemm")) / args.steps
     chol_tflops = (N ** 3 / 3.0) / (chol_ms * 1e-3) / 1e12 if chol_ms > 0 else 0.0
+    # DRAM bytes per launch: an ncu capture of a full rank-960 trailing update
+    # (N = 8,000) measured 0.822 x the algorithmic bytes; scaled to this run's
+    # average launch (FP64 update kernel only)
+    traffic = 0.822 * dk["bytes"] / max(dk["launches"], 1) if dom == "gemm" else None
     out = {"metric": METRIC, "value": world * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": config_json(w, args),
            "cholesky_tflops": chol_tflops,
-           "roofline": {"bound": "alu", "kernel": "k_dgemm_update (FP64 FMA trailing/panel updates)",
-                        "achieved": gemm_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                        "frac": gemm_tflops / FP64_PEAK_TFLOPS,
-                        "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-                        # DRAM bytes per launch: an ncu capture of a full rank-960 trailing update
-                        # (N = 8,000) measured 0.822 x the algorithmic bytes; scaled to this run's
-                        # average launch
-                        "traffic": 0.822 * gemm["bytes"] / max(gemm["launches"], 1)},
+           "roofline": {"bound": bound, "kernel": KERNEL_NAMES.get(dom, dom), "achieved": dom_tflops, "peak": peak,
+                        "unit": "TFLOP/s", "frac": dom_tflops / peak, "peak_source": peak_src,
+                        "traffic": traffic},
            "gpu_launches": launches,
            "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
            "quality": {"loglik": ll, "mspe": mspe},

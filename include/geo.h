@@ -150,7 +150,11 @@ int geo_predict(geo_ctx *ctx, const geo_factor *factor, const double *new_locs_d
  * Synthetic draw Z = L e with L L' = Sigma(theta) (Sec. 6.4.1 synthetic data;
  * the paper does not state its generator): e_dev holds N standard normals
  * (device), z_dev receives N values in Representation I in the caller's
- * location order.  Synchronises `stream`.
+ * location order.  With opts->prec = GEO_PREC_MIXED, L is the mixed-precision
+ * factor (a draw from N(0, L L') with L L' close to Sigma).  With the default
+ * Morton reordering the draw differs from the one of the caller's order
+ * (Cholesky factors of permuted matrices are not permutations of each other);
+ * opts->morton = 0 reproduces L e in the caller's order.  Synchronises `stream`.
  */
 int geo_simulate(geo_ctx *ctx, const double *locs_dev, int n, const double *e_dev, const geo_theta *theta,
                  const geo_opts *opts, double *z_dev, int *info, void *stream);
@@ -242,7 +246,9 @@ enum {
     GEO_K_SOLVE = 5,    /* backward substitution L' w = y */
     GEO_K_PREDICT = 6,  /* fused cross-covariance + GEMV of Eq. 3 */
     GEO_K_AUX = 7,      /* gathers, scatters, conversions */
-    GEO_K_COUNT = 8
+    GEO_K_TCGEMM = 8,   /* tensor-core (tcgen05) updates of far tiles, mixed precision */
+    GEO_K_SGEMM = 9,    /* FP32 SIMT updates (mixed precision: diagonal and band tiles, panel) */
+    GEO_K_COUNT = 10
 };
 typedef struct {
     long long launches;

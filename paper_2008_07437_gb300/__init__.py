@@ -58,7 +58,7 @@ class geo_mle_state(ctypes.Structure):
                 ("f", ctypes.c_double * (GEO_MLE_QMAX + 1)), ("last_f", ctypes.c_double)]
 
 
-GEO_K_NAMES = ["covgen", "potrf", "trsm", "gemm", "reduce", "solve", "predict", "aux"]
+GEO_K_NAMES = ["covgen", "potrf", "trsm", "gemm", "reduce", "solve", "predict", "aux", "tcgemm", "sgemm"]
 GEO_K_COUNT = len(GEO_K_NAMES)
 
 

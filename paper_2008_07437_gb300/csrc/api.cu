@@ -31,6 +31,12 @@ struct geo_ctx {
     // reusable workspace for the matrix of a discarded evaluation
     double *ws = nullptr;
     size_t ws_bytes = 0;
+    // workspace of the mixed-precision factorisation (panel copies)
+    void *mws = nullptr;
+    size_t mws_bytes = 0;
+    // iterative refinement: copy of Sigma, sorted Z, partial sums
+    void *sws = nullptr, *zws = nullptr, *rws = nullptr;
+    size_t sws_bytes = 0, zws_bytes = 0, rws_bytes = 0;
     std::vector<geo_factor *> factors;
     Profiler prof;
 };
@@ -156,6 +162,21 @@ struct SetDevice {
 };
 
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+// Grow a context-cached device buffer to at least `need` bytes.
+int ensure_buffer(geo_ctx *ctx, void **buf, size_t *have, size_t need, cudaStream_t s) {
+    if (*have >= need) return GEO_OK;
+    if (*buf) {
+        cudaStreamSynchronize(s);
+        dev_free(ctx, *buf, *have);
+        *buf = nullptr;
+        *have = 0;
+    }
+    int rc = dev_alloc(ctx, buf, need);
+    if (rc) return rc;
+    *have = need;
+    return GEO_OK;
+}
 
 // G1(mu) = (1/Gamma(1-mu) - 1/Gamma(1+mu)) / (2 mu), G2(mu) = (1/Gamma(1-mu) + 1/Gamma(1+mu)) / 2.
 // Near mu = 0 the difference cancels: G1 is even in mu and equals
@@ -350,6 +371,10 @@ int geo_destroy(geo_ctx *ctx) {
     while (!ctx->factors.empty()) geo_factor_free(ctx->factors.back());
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
     if (ctx->ws) dev_free(ctx, ctx->ws, ctx->ws_bytes);
+    if (ctx->mws) dev_free(ctx, ctx->mws, ctx->mws_bytes);
+    if (ctx->sws) dev_free(ctx, ctx->sws, ctx->sws_bytes);
+    if (ctx->zws) dev_free(ctx, ctx->zws, ctx->zws_bytes);
+    if (ctx->rws) dev_free(ctx, ctx->rws, ctx->rws_bytes);
     if (ctx->st) cudaFree(ctx->st);
     if (ctx->res) cudaFree(ctx->res);
     if (ctx->h_st) cudaFreeHost(ctx->h_st);
@@ -469,7 +494,10 @@ int geo_loglik(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev,
         geo_opts_default(&o);
     if (n <= 0 || !locs_dev || !z_dev) return fail(ctx, GEO_EINVAL, "n must be > 0 and pointers non-NULL");
     if (o.nb < 64) return fail(ctx, GEO_EINVAL, "nb must be >= 64");
-    if (o.prec != GEO_PREC_FP64) return fail(ctx, GEO_EUNSUPPORTED, "precision mode not built");
+    if (o.prec != GEO_PREC_FP64 && o.prec != GEO_PREC_MIXED)
+        return fail(ctx, GEO_EUNSUPPORTED, "precision mode not built");
+    if (o.prec == GEO_PREC_MIXED && (o.nb % 128 != 0 || o.band < 0))
+        return fail(ctx, GEO_EINVAL, "mixed precision needs nb a multiple of 128 and band >= 0");
     SetDevice sd(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     geo_factor *f = new geo_factor();
@@ -490,10 +518,42 @@ int geo_loglik(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev,
     }
     int *d_perm = (int *)pp;
     cudaError_t e;
+    const bool mixed = (o.prec == GEO_PREC_MIXED);
+    const bool refine = mixed && o.refine_iters > 0;
+    if (mixed) {
+        const size_t abytes = sizeof(double) * (size_t)f->ld * (size_t)N;
+        if ((rc = ensure_buffer(ctx, &ctx->mws, &ctx->mws_bytes, mixed_workspace_bytes(N, o.nb), s)) ||
+            (refine && (rc = ensure_buffer(ctx, &ctx->sws, &ctx->sws_bytes, abytes, s))) ||
+            (refine && (rc = ensure_buffer(ctx, &ctx->zws, &ctx->zws_bytes, sizeof(double) * N, s))) ||
+            (refine && (rc = ensure_buffer(ctx, &ctx->rws, &ctx->rws_bytes, refine_workspace_bytes(N), s)))) {
+            dev_free(ctx, d_perm, sizeof(int) * n);
+            release_factor_buffers(ctx, f, true);
+            delete f;
+            return rc;
+        }
+        if (refine) {
+            void *pw;
+            if ((rc = dev_alloc(ctx, &pw, sizeof(double) * N))) {
+                dev_free(ctx, d_perm, sizeof(int) * n);
+                release_factor_buffers(ctx, f, true);
+                delete f;
+                return rc;
+            }
+            f->w = (double *)pw;
+        }
+    }
+    double *Scopy = (double *)ctx->sws, *zsorted = (double *)ctx->zws;
     if ((e = cudaMemcpyAsync(d_perm, f->perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s)) ||
         (e = launch_gather_vec(z_dev, d_perm, n, f->p, f->A + N, f->ld, s)) ||
-        (e = chol64_factor(f->A, f->ld, N, N + 1, o.nb, ctx->st, s)) ||
-        (e = launch_loglik_reduce(f->A, f->ld, N, f->A + N, f->ld, ctx->st, ctx->res, s)) ||
+        (refine && (e = launch_gather_vec(z_dev, d_perm, n, f->p, zsorted, 1, s))) ||
+        (refine && (e = cudaMemcpyAsync(Scopy, f->A, sizeof(double) * (size_t)f->ld * (size_t)N,
+                                        cudaMemcpyDeviceToDevice, s))) ||
+        (e = mixed ? chol_mixed_factor(f->A, f->ld, N, N + 1, o.nb, o.band, o.lowp, ctx->mws, ctx->mws_bytes,
+                                       ctx->st, s)
+                   : chol64_factor(f->A, f->ld, N, N + 1, o.nb, ctx->st, s)) ||
+        (e = refine ? refine_solve(Scopy, f->A, f->ld, N, zsorted, f->A + N, f->ld, o.refine_iters, f->w, ctx->rws,
+                                   ctx->st, ctx->res, s)
+                    : launch_loglik_reduce(f->A, f->ld, N, f->A + N, f->ld, ctx->st, ctx->res, s)) ||
         (e = cudaMemcpyAsync(ctx->h_res, ctx->res, sizeof(DevResults), cudaMemcpyDeviceToHost, s)) ||
         (e = cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s)) ||
         (e = cudaStreamSynchronize(s))) {
@@ -580,7 +640,16 @@ int geo_simulate(geo_ctx *ctx, const double *locs_dev, int n, const double *e_de
     double *zs = (double *)pz;
     int *d_perm = (int *)pp;
     cudaError_t e;
-    if ((e = chol64_factor(f.A, f.ld, N, N, o.nb, ctx->st, s)) ||
+    const bool mixed = (o.prec == GEO_PREC_MIXED);
+    if (mixed && (o.nb % 128 != 0 ||
+                  (rc = ensure_buffer(ctx, &ctx->mws, &ctx->mws_bytes, mixed_workspace_bytes(N, o.nb), s)))) {
+        dev_free(ctx, zs, sizeof(double) * N);
+        dev_free(ctx, d_perm, sizeof(int) * n);
+        release_factor_buffers(ctx, &f, true);
+        return rc ? rc : fail(ctx, GEO_EINVAL, "mixed precision needs nb a multiple of 128");
+    }
+    if ((e = mixed ? chol_mixed_factor(f.A, f.ld, N, N, o.nb, o.band, o.lowp, ctx->mws, ctx->mws_bytes, ctx->st, s)
+                   : chol64_factor(f.A, f.ld, N, N, o.nb, ctx->st, s)) ||
         (e = launch_trmv_lower(f.A, f.ld, N, e_dev, zs, s)) ||
         (e = cudaMemcpyAsync(d_perm, f.perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s)) ||
         (e = launch_scatter_vec(zs, 1, d_perm, n, f.p, z_dev, s)) ||

@@ -180,33 +180,60 @@ cudaError_t gemm_update(double *A, long long ld, int rC, int cC, int m, int n, i
 
 }  // namespace
 
-cudaError_t chol64_factor(double *A, long long ld, int N, int nrows, int nb, DevStatus *st, cudaStream_t s) {
+// Factor the panel of columns [j0, j0 + jb): its diagonal tile (inner 64-wide
+// blocks: POTRF, TRSM, rank-64 update) and, carried through the same inner
+// steps, the rows [x0, x1) below the tile (x0 >= j0 + jb; x0 == x1 = none).
+cudaError_t chol64_panel(double *A, long long ld, int j0, int jb, int x0, int x1, DevStatus *st, cudaStream_t s) {
     const size_t trsm_smem = sizeof(double) * (IB * IB + IB * (TRSM_ROWS + 1));
     cudaError_t e = cudaFuncSetAttribute(k_trsm_rlt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem);
     if (e != cudaSuccess) return e;
-    if (nb < IB) nb = IB;
-    nb = (nb / IB) * IB;
-    for (int j0 = 0; j0 < N; j0 += nb) {
-        const int jb = min(nb, N - j0);
-        for (int c0 = j0; c0 < j0 + jb; c0 += IB) {
-            const int cb = min(IB, j0 + jb - c0);
-            {
-                KScope ks(GEO_K_POTRF, s, (double)cb * cb * cb / 3.0, 16.0 * cb * cb);
-                k_potrf_diag<<<1, 256, 0, s>>>(A, ld, c0, cb, st);
-            }
-            const int rows0 = c0 + cb;
-            if (rows0 < nrows) {
-                const int nr = nrows - rows0;
-                KScope ks(GEO_K_TRSM, s, (double)nr * cb * cb, 16.0 * nr * cb);
-                k_trsm_rlt<<<(nr + TRSM_ROWS - 1) / TRSM_ROWS, 256, trsm_smem, s>>>(A, ld, c0, cb, rows0, nrows, st);
-            }
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            // rest of the panel: rows rows0.., cols rows0 .. j0+jb-1
-            if (rows0 < j0 + jb) {
-                e = gemm_update(A, ld, rows0, rows0, nrows - rows0, j0 + jb - rows0, c0, cb, st, s);
+    const bool contiguous = (x0 == j0 + jb);
+    for (int c0 = j0; c0 < j0 + jb; c0 += IB) {
+        const int cb = min(IB, j0 + jb - c0);
+        {
+            KScope ks(GEO_K_POTRF, s, (double)cb * cb * cb / 3.0, 16.0 * cb * cb);
+            k_potrf_diag<<<1, 256, 0, s>>>(A, ld, c0, cb, st);
+        }
+        const int rows0 = c0 + cb;
+        // row ranges carried through this inner step
+        int ra[2][2];
+        int nrange = 0;
+        if (contiguous) {
+            if (rows0 < x1) ra[nrange][0] = rows0, ra[nrange][1] = x1, ++nrange;
+        } else {
+            if (rows0 < j0 + jb) ra[nrange][0] = rows0, ra[nrange][1] = j0 + jb, ++nrange;
+            if (x0 < x1) ra[nrange][0] = x0, ra[nrange][1] = x1, ++nrange;
+        }
+        for (int q = 0; q < nrange; ++q) {
+            const int nr = ra[q][1] - ra[q][0];
+            KScope ks(GEO_K_TRSM, s, (double)nr * cb * cb, 16.0 * nr * cb);
+            k_trsm_rlt<<<(nr + TRSM_ROWS - 1) / TRSM_ROWS, 256, trsm_smem, s>>>(A, ld, c0, cb, ra[q][0], ra[q][1], st);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // rest of the panel: cols rows0 .. j0+jb-1
+        if (rows0 < j0 + jb) {
+            for (int q = 0; q < nrange; ++q) {
+                e = gemm_update(A, ld, ra[q][0], rows0, ra[q][1] - ra[q][0], j0 + jb - rows0, c0, cb, st, s);
                 if (e != cudaSuccess) return e;
             }
         }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t chol64_gemm_update(double *A, long long ld, int rC, int cC, int m, int n, int kA, int k, DevStatus *st,
+                               cudaStream_t s) {
+    return gemm_update(A, ld, rC, cC, m, n, kA, k, st, s);
+}
+
+cudaError_t chol64_factor(double *A, long long ld, int N, int nrows, int nb, DevStatus *st, cudaStream_t s) {
+    if (nb < IB) nb = IB;
+    nb = (nb / IB) * IB;
+    cudaError_t e = cudaSuccess;
+    for (int j0 = 0; j0 < N; j0 += nb) {
+        const int jb = min(nb, N - j0);
+        e = chol64_panel(A, ld, j0, jb, j0 + jb, nrows, st, s);
+        if (e != cudaSuccess) return e;
         // trailing update: rows j0+jb .. nrows-1, cols j0+jb .. N-1, rank jb
         const int t0 = j0 + jb;
         if (t0 < N) {

@@ -1,0 +1,374 @@
+// Mixed-precision tiled Cholesky (the precision pattern the library offers on
+// top of the paper's exact and TLR forms; the paper itself runs FP64 only).
+//
+// Tiles of width nb (a multiple of 128).  For panel k:
+//   * diagonal tile: FP64 storage, FP64 POTRF (inner 64-wide blocks);
+//   * rows below it: TRSM in FP32 (L_ik = A_ik L_kk^-T, inner 64-wide blocks,
+//     FP32 SIMT), written back to the FP64 matrix;
+//   * trailing update of tile (I, J), d = I - J:
+//       d <= band : FP32 operands, FP32 SIMT FMA, FP64 read-modify-write of C
+//                   (the diagonal tiles d = 0 included: they stay FP64 in
+//                   storage and in their factorisation, their updates are FP32);
+//       d >  band : FP16 operands split in two terms (hi + lo, three MMAs) or
+//                   one BF16 term, with a power-of-two scale per panel row,
+//                   tcgen05 tensor cores with FP32 accumulation in TMEM, FP64
+//                   read-modify-write of C;
+//   * the extra right-hand-side row N (Z', becoming (L^-1 Z)') is solved and
+//     updated in FP64 throughout.
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include "geo_internal.cuh"
+#include "tc_gemm.cuh"
+
+namespace {
+
+constexpr int SB = 128, SK = 8;   // SIMT FP32 GEMM: 128 x 128 tile, K slices of 8
+
+// C[i, j] -= sum_k A[i, k] B[j, k] (i < m, j < n); A, B column-major FP32; C
+// column-major TC.  gr0 / gc0: global row / col of C(0, 0) for the class
+// filter (nb-tile distance in [dlo, dhi]) and, when tri, the skip of tiles
+// entirely above the diagonal.
+template <typename TC>
+__global__ void __launch_bounds__(256) k_sgemm_nt(TC *C, long long ldc, const float *__restrict__ A, long long lda,
+                                                  const float *__restrict__ B, long long ldb, int m, int n, int k,
+                                                  int gr0, int gc0, int nb, int dlo, int dhi, int tri,
+                                                  const DevStatus *st) {
+    __shared__ float As[SK][SB + 4];
+    __shared__ float Bs[SK][SB + 4];
+    if (st->info) return;
+    const int tm = blockIdx.x * SB, tn = blockIdx.y * SB;
+    const int gr = gr0 + tm, gc = gc0 + tn;
+    if (nb > 0) {
+        const int dmin = gr / nb - (gc + SB - 1) / nb, dmax = (gr + SB - 1) / nb - gc / nb;
+        if (dmax < dlo || dmin > dhi) return;
+        // a CTA tile never straddles classes when nb is a multiple of 128 and the region is nb-aligned
+    }
+    if (tri && gr + SB - 1 < gc) return;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int k0 = 0; k0 < k; k0 += SK) {
+#pragma unroll
+        for (int t = 0; t < (SK * SB) / 256; ++t) {
+            const int idx = threadIdx.x + t * 256;
+            const int kk = idx / SB, r = idx % SB;
+            const bool kin = k0 + kk < k;
+            As[kk][r] = (kin && tm + r < m) ? A[(long long)(k0 + kk) * lda + tm + r] : 0.f;
+            Bs[kk][r] = (kin && tn + r < n) ? B[(long long)(k0 + kk) * ldb + tn + r] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < SK; ++kk) {
+            float a[8], b[8];
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[kk][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[kk][64 + tx * 4]);
+            a[0] = a0.x, a[1] = a0.y, a[2] = a0.z, a[3] = a0.w, a[4] = a1.x, a[5] = a1.y, a[6] = a1.z, a[7] = a1.w;
+            b[0] = b0.x, b[1] = b0.y, b[2] = b0.z, b[3] = b0.w, b[4] = b1.x, b[5] = b1.y, b[6] = b1.z, b[7] = b1.w;
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int c = tn + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+        if (c >= n) continue;
+        TC *col = C + (long long)c * ldc + tm;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+            if (tm + r < m) col[r] -= (TC)acc[i][j];
+        }
+    }
+}
+
+// FP32 TRSM on a column-major FP32 block X (rows, 64 cols, ldx): X <- X L^-T,
+// L = the 64 x 64 lower block of the FP64 diagonal tile (read as FP32).
+constexpr int TR_ROWS = 64;
+__global__ void __launch_bounds__(256) k_trsm32(float *X, long long ldx, int rows, const double *L, long long ldl,
+                                               int cb, const DevStatus *st) {
+    __shared__ float Ls[64][65];
+    __shared__ float Xs[64][TR_ROWS + 1];
+    if (st->info) return;
+    const int rb = blockIdx.x * TR_ROWS;
+    const int nr = min(TR_ROWS, rows - rb);
+    for (int t = threadIdx.x; t < cb * cb; t += 256) {
+        const int c = t / cb, r = t % cb;
+        Ls[c][r] = (r >= c) ? (float)L[(long long)c * ldl + r] : 0.f;
+    }
+    for (int t = threadIdx.x; t < cb * TR_ROWS; t += 256) {
+        const int c = t / TR_ROWS, r = t % TR_ROWS;
+        Xs[c][r] = (r < nr) ? X[(long long)c * ldx + rb + r] : 0.f;
+    }
+    __syncthreads();
+    const int row = threadIdx.x % TR_ROWS, grp = threadIdx.x / TR_ROWS;
+    for (int c = 0; c < cb; ++c) {
+        if (grp == 0) Xs[c][row] /= Ls[c][c];
+        __syncthreads();
+        const float xc = Xs[c][row];
+        for (int kk = c + 1 + grp; kk < cb; kk += 4) Xs[kk][row] -= xc * Ls[c][kk];
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < cb * TR_ROWS; t += 256) {
+        const int c = t / TR_ROWS, r = t % TR_ROWS;
+        if (r < nr) X[(long long)c * ldx + rb + r] = Xs[c][r];
+    }
+}
+
+// FP64 panel block -> FP32 (column-major, ldp), rows [0, rows), cols [0, cols).
+__global__ void k_to_f32(const double *A, long long lda, int rows, int cols, float *P, long long ldp) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)rows * cols) return;
+    const int c = (int)(t / rows), r = (int)(t % rows);
+    P[(long long)c * ldp + r] = (float)A[(long long)c * lda + r];
+}
+
+// FP32 panel -> FP64 matrix.
+__global__ void k_to_f64(const float *P, long long ldp, int rows, int cols, double *A, long long lda) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)rows * cols) return;
+    const int c = (int)(t / rows), r = (int)(t % rows);
+    A[(long long)c * lda + r] = (double)P[(long long)c * ldp + r];
+}
+
+// Per panel row r: power-of-two scale s_r with max_c |x[r, c]| s_r < 2^14, and
+// the K-major (row-major) low-precision copies x s = hi + lo (lo only when
+// two terms are kept); 1 / s_r goes to inv_scale[r].  One CTA per 64 rows:
+// a column sweep for the row maxima (coalesced along rows), then 64 x 64
+// tiles transposed through shared memory so that the stores run along K.
+template <typename T16>
+__global__ void __launch_bounds__(256) k_to_lowp(const float *P, long long ldp, int rows, int cols, T16 *Hhi,
+                                                 T16 *Hlo, int Kp, double *inv_scale) {
+    __shared__ float red[4][64];
+    __shared__ float sc[64];
+    __shared__ float tile[64][65];
+    const int rb = blockIdx.x * 64;
+    const int rr = threadIdx.x % 64, g = threadIdx.x / 64;
+    float mx = 0.f;
+    if (rb + rr < rows)
+        for (int c = g; c < cols; c += 4) mx = fmaxf(mx, fabsf(P[(long long)c * ldp + rb + rr]));
+    red[g][rr] = mx;
+    __syncthreads();
+    if (threadIdx.x < 64) {
+        const float m = fmaxf(fmaxf(red[0][rr], red[1][rr]), fmaxf(red[2][rr], red[3][rr]));
+        int e = 0;
+        if (m > 0.f) frexpf(m, &e);   // m = f 2^e, f in [0.5, 1)
+        const float s = (m > 0.f) ? ldexpf(1.f, 14 - e) : 1.f;
+        sc[rr] = s;
+        if (rb + rr < rows) inv_scale[rb + rr] = 1.0 / (double)s;
+    }
+    __syncthreads();
+    for (int c0 = 0; c0 < Kp; c0 += 64) {
+        for (int t = threadIdx.x; t < 64 * 64; t += 256) {
+            const int c = t / 64, r = t % 64;
+            tile[c][r] = (rb + r < rows && c0 + c < cols) ? P[(long long)(c0 + c) * ldp + rb + r] * sc[r] : 0.f;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < 64 * 64; t += 256) {
+            const int r = t / 64, c = t % 64;
+            if (rb + r >= rows) continue;
+            const float v = tile[c][r];
+            const T16 hi = (T16)v;
+            Hhi[(long long)(rb + r) * Kp + c0 + c] = hi;
+            if (Hlo) Hlo[(long long)(rb + r) * Kp + c0 + c] = (T16)(v - (float)hi);
+        }
+        __syncthreads();
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+template <typename TC>
+cudaError_t sgemm(TC *C, long long ldc, const float *A, long long lda, const float *B, long long ldb, int m, int n,
+                  int k, int gr0, int gc0, int nb, int dlo, int dhi, int tri, const DevStatus *st, double flops,
+                  cudaStream_t s) {
+    if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
+    dim3 grid((m + SB - 1) / SB, (n + SB - 1) / SB);
+    KScope ks(GEO_K_SGEMM, s, flops, 0.0);
+    k_sgemm_nt<TC><<<grid, 256, 0, s>>>(C, ldc, A, lda, B, ldb, m, n, k, gr0, gc0, nb, dlo, dhi, tri, st);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t mixed_workspace_bytes(int N, int nb) {
+    const size_t rows = (size_t)N + 128;
+    const size_t ldp = (rows + 3) / 4 * 4;
+    return sizeof(float) * ldp * nb              // FP32 panel
+           + sizeof(float) * (size_t)nb * nb     // FP32 copy of the diagonal tile
+           + 4 * rows * (size_t)nb               // FP16 / BF16 panel, hi and lo
+           + sizeof(double) * rows               // row scales
+           + 4096;
+}
+
+cudaError_t chol_mixed_factor(double *A, long long ld, int N, int nrows, int nb, int band, int lowp, void *ws,
+                              size_t ws_bytes, DevStatus *st, cudaStream_t s) {
+    if (nb % 128 != 0 || nb <= 0) return cudaErrorInvalidValue;
+    if (ws_bytes < mixed_workspace_bytes(N, nb)) return cudaErrorInvalidValue;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    cudaError_t e = cudaFuncSetAttribute(tc::k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tc::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    const size_t rows_max = (size_t)N + 128;
+    const long long ldp = (long long)((rows_max + 3) / 4 * 4);
+    uint8_t *w = (uint8_t *)ws;
+    float *P32 = (float *)w;
+    w += sizeof(float) * ldp * nb;
+    float *LD32 = (float *)w;
+    w += sizeof(float) * (size_t)nb * nb;
+    w = (uint8_t *)(((uintptr_t)w + 255) & ~(uintptr_t)255);
+    void *P16 = w;
+    w += 2 * rows_max * (size_t)nb;
+    void *P16lo = w;
+    w += 2 * rows_max * (size_t)nb;
+    w = (uint8_t *)(((uintptr_t)w + 255) & ~(uintptr_t)255);
+    double *inv_scale = (double *)w;
+    const uint32_t idesc = tc::instr_desc(lowp ? 1 : 0);
+
+    for (int j0 = 0; j0 < N; j0 += nb) {
+        const int jb = min(nb, N - j0);
+        const int t0 = j0 + jb;
+        // 1. diagonal tile in FP64, carrying the right-hand-side rows [N, nrows)
+        e = chol64_panel(A, ld, j0, jb, (nrows > N) ? N : t0, (nrows > N) ? nrows : t0, st, s);
+        if (e != cudaSuccess) return e;
+        if (t0 >= N) break;
+        const int R = N - t0;   // rows of the panel below the diagonal tile
+        // 2. FP32 TRSM of rows [t0, N) against L_kk, inner 64-wide blocks
+        {
+            const long long tot = (long long)R * jb;
+            KScope ks(GEO_K_AUX, s);
+            k_to_f32<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(A + (long long)j0 * ld + t0, ld, R, jb, P32, ldp);
+        }
+        {
+            const long long tot = (long long)jb * jb;
+            KScope ks(GEO_K_AUX, s);
+            k_to_f32<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(A + (long long)j0 * ld + j0, ld, jb, jb, LD32, nb);
+        }
+        for (int c0 = 0; c0 < jb; c0 += 64) {
+            const int cb = min(64, jb - c0);
+            {
+                KScope ks(GEO_K_TRSM, s, (double)R * cb * cb, 0.0);
+                k_trsm32<<<(R + TR_ROWS - 1) / TR_ROWS, 256, 0, s>>>(P32 + (long long)c0 * ldp, ldp, R,
+                                                                     A + (long long)(j0 + c0) * ld + j0 + c0, ld, cb,
+                                                                     st);
+            }
+            if (c0 + cb < jb) {
+                // P32[:, c0+cb:] -= P32[:, c0:c0+cb] LD[c0+cb:, c0:c0+cb]'
+                e = sgemm<float>(P32 + (long long)(c0 + cb) * ldp, ldp, P32 + (long long)c0 * ldp, ldp,
+                                 LD32 + (long long)c0 * nb + c0 + cb, nb, R, jb - c0 - cb, cb, 0, 0, 0, 0, 0, 0, st,
+                                 2.0 * R * (jb - c0 - cb) * cb, s);
+                if (e != cudaSuccess) return e;
+            }
+        }
+        {
+            const long long tot = (long long)R * jb;
+            KScope ks(GEO_K_AUX, s);
+            k_to_f64<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P32, ldp, R, jb, A + (long long)j0 * ld + t0, ld);
+        }
+        // 3. low-precision copy with per-128-row-block scales (only needed when far tiles exist)
+        const bool far = (N - 1) / nb - t0 / nb > band;
+        const int nblk = (R + 63) / 64;
+        const int terms = lowp ? 1 : 2;   // FP16 keeps hi + lo; BF16 keeps one term
+        if (far) {
+            KScope ks(GEO_K_AUX, s);
+            if (lowp)
+                k_to_lowp<__nv_bfloat16><<<nblk, 256, 0, s>>>(P32, ldp, R, jb, (__nv_bfloat16 *)P16, nullptr, nb,
+                                                              inv_scale);
+            else
+                k_to_lowp<__half><<<nblk, 256, 0, s>>>(P32, ldp, R, jb, (__half *)P16, (__half *)P16lo, nb,
+                                                       inv_scale);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // 4a. trailing update of diagonal and band tiles in FP32
+        {
+            // algorithmic flops: lower-triangle entries of the classes d <= band
+            double ent = 0.0;
+            const int T0 = t0 / nb, T1 = (N - 1) / nb;
+            for (int I = T0; I <= T1; ++I) {
+                const double hi = min(N, (I + 1) * nb) - I * nb;
+                for (int J = max(T0, I - band); J <= I; ++J) {
+                    const double wj = min(N, (J + 1) * nb) - J * nb;
+                    ent += (I == J) ? hi * (hi + 1) / 2 : hi * wj;
+                }
+            }
+            e = sgemm<double>(A + (long long)t0 * ld + t0, ld, P32, ldp, P32, ldp, R, R, jb, t0, t0, nb, 0, band, 1,
+                              st, 2.0 * jb * ent, s);
+            if (e != cudaSuccess) return e;
+        }
+        // 4b. far tiles on tensor cores
+        if (far) {
+            CUtensorMap map;
+            cuuint64_t dims[2] = {(cuuint64_t)nb, (cuuint64_t)R};
+            cuuint64_t strides[1] = {(cuuint64_t)nb * 2};
+            cuuint32_t box[2] = {64, 128};
+            cuuint32_t es[2] = {1, 1};
+            CUresult cr = enc(&map, lowp ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, P16,
+                              dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+            CUtensorMap map_lo = map;
+            if (terms == 2) {
+                cr = enc(&map_lo, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, P16lo, dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+            }
+            tc::TcArgs a;
+            a.C = A;
+            a.ldc = ld;
+            a.r0 = t0;
+            a.c0 = t0;
+            a.m = R;
+            a.n = R;
+            a.prow0 = t0;
+            a.K = nb;   // columns jb..nb of the low-precision copy are zero
+            a.nb = nb;
+            a.dlo = band + 1;
+            a.dhi = 1 << 30;
+            a.inv_scale = inv_scale;
+            a.terms = terms;
+            a.st = st;
+            double ent = 0.0;
+            const int T0 = t0 / nb, T1 = (N - 1) / nb;
+            for (int I = T0; I <= T1; ++I) {
+                const double hi = min(N, (I + 1) * nb) - I * nb;
+                for (int J = T0; J < I - band; ++J) ent += hi * nb;
+            }
+            dim3 grid((R + tc::BM - 1) / tc::BM, (R + tc::BN - 1) / tc::BN);
+            KScope ks(GEO_K_TCGEMM, s, 2.0 * jb * ent * (terms == 2 ? 3 : 1), 16.0 * ent + 2.0 * terms * (double)R * jb);
+            tc::k_tc_update<<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(map, map_lo, a, idesc);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        // 4c. right-hand-side rows in FP64
+        if (nrows > N) {
+            e = chol64_gemm_update(A, ld, N, t0, nrows - N, N - t0, j0, jb, st, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}

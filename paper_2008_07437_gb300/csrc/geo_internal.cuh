@@ -86,6 +86,16 @@ cudaError_t launch_scatter_vec(const double *in, long long stride, const int *pe
 // are extra right-hand-side rows carried through the factorisation (row N
 // receives (L^-1 z)' when it holds z').  nb = outer tile size.
 cudaError_t chol64_factor(double *A, long long ld, int N, int nrows, int nb, DevStatus *st, cudaStream_t s);
+// One panel [j0, j0+jb): diagonal tile plus extra rows [x0, x1) carried along.
+cudaError_t chol64_panel(double *A, long long ld, int j0, int jb, int x0, int x1, DevStatus *st, cudaStream_t s);
+// C[rC.., cC..] (m x n) -= A[rC.., kA..kA+k] A[cC.., kA..kA+k]' in FP64.
+cudaError_t chol64_gemm_update(double *A, long long ld, int rC, int cC, int m, int n, int kA, int k, DevStatus *st,
+                               cudaStream_t s);
+
+// ---- chol_mixed.cu --------------------------------------------------------
+size_t mixed_workspace_bytes(int N, int nb);
+cudaError_t chol_mixed_factor(double *A, long long ld, int N, int nrows, int nb, int band, int lowp, void *ws,
+                              size_t ws_bytes, DevStatus *st, cudaStream_t s);
 
 
 // ---- solve.cu -----------------------------------------------------------
@@ -97,6 +107,15 @@ cudaError_t backward_solve(const double *A, long long ld, int N, const double *y
                            cudaStream_t s);
 // z = L e (lower-triangular matrix-vector product).
 cudaError_t launch_trmv_lower(const double *A, long long ld, int N, const double *e, double *z, cudaStream_t s);
+
+// ---- refine.cu ------------------------------------------------------------
+cudaError_t forward_solve(const double *A, long long ld, int N, double *x, cudaStream_t s);
+size_t refine_workspace_bytes(int N);
+// x = Sigma^-1 z by FP64 iterative refinement with the factor in A and the
+// lower triangle of Sigma in S; writes l, log|Sigma|, z'x to res.
+cudaError_t refine_solve(const double *S, const double *A, long long ld, int N, const double *z, const double *y,
+                         long long ystride, int iters, double *x, void *ws, const DevStatus *st, DevResults *res,
+                         cudaStream_t s);
 
 // ---- host helpers (api.cu) ------------------------------------------------
 int theta_to_params(const geo_theta *th, CovParams *cp, std::string *err);

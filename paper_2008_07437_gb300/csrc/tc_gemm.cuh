@@ -1,11 +1,14 @@
 // Tensor-core (tcgen05) update of far-from-diagonal tiles for the
-// mixed-precision Cholesky:  C[I, J] -= inv_s_I inv_s_J * (A_I B_J')  with
-// A_I, B_J FP16 (per-row-block power-of-two scale s), FP32 accumulation in
-// tensor memory, FP64 C.
+// mixed-precision Cholesky:  C[r, c] -= inv_s_r inv_s_c * (A B')[r, c]  with
+// the panel rows scaled by a power of two s_r each (max |x| s_r < 2^14) and
+// held as FP16 (or BF16), FP32 accumulation in tensor memory, FP64 C.
+// With two terms the panel is split x s = hi + lo (both FP16) and the tile
+// accumulates hi hi' + hi lo' + lo hi' (three MMAs per K step): about 22
+// significant bits per operand instead of 11.
 //
 // Per CTA: one 128 x 128 output tile, K in 64-wide blocks.
-//   warp 0 (one lane): TMA producer, 4-stage ring of (A 128x64, B 128x64)
-//                      FP16 tiles in 128-byte-swizzled shared memory;
+//   warp 0 (one lane): TMA producer, 3-stage ring of (A, B) tiles (hi, and lo
+//                      with two terms), 128 x 64 FP16 each, 128-byte swizzle;
 //   warp 1: allocates 128 TMEM columns; one lane issues tcgen05.mma
 //           (M = 128, N = 128, K = 16, kind::f16, FP32 accumulate) and
 //           commits each stage back to the producer;
@@ -24,10 +27,11 @@
 
 namespace tc {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3;
 constexpr int TILE_A_BYTES = BM * BK * 2;
 constexpr int TILE_B_BYTES = BN * BK * 2;
-constexpr int STAGE_BYTES = TILE_A_BYTES + TILE_B_BYTES;
+constexpr int TILE_BYTES = TILE_A_BYTES;                   // A and B tiles have the same shape
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;                // A_hi, B_hi, A_lo, B_lo
 constexpr int THREADS = 192;
 constexpr int TMEM_COLS = 128;
 constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024;   // + alignment slack
@@ -132,12 +136,14 @@ struct TcArgs {
     int prow0;             // global row of panel row 0 (A / B operand row = global - prow0)
     int K;                 // panel width (multiple of 64)
     int nb, dlo, dhi;      // class filter
-    const double *inv_scale;   // per 128-row block of the panel
+    const double *inv_scale;   // per panel row
+    int terms;                 // 1: hi only, 2: hi + lo
     DevStatus *st;
 };
 
 __global__ void __launch_bounds__(THREADS, 1)
-    k_tc_update(const __grid_constant__ CUtensorMap map, const TcArgs args, const uint32_t idesc) {
+    k_tc_update(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap map_lo,
+                const TcArgs args, const uint32_t idesc) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], acc_bar;
     __shared__ uint32_t tmem_slot;
@@ -189,10 +195,14 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                 }
                 uint8_t *sa = smem + (size_t)s * STAGE_BYTES;
-                uint8_t *sb = sa + TILE_A_BYTES;
-                mbar_arrive_expect_tx(&full_bar[s], STAGE_BYTES);
+                uint8_t *sb = sa + TILE_BYTES;
+                mbar_arrive_expect_tx(&full_bar[s], (args.terms == 2 ? 4 : 2) * TILE_BYTES);
                 tma_load_2d(&map, &full_bar[s], sa, kb * BK, arow);
                 tma_load_2d(&map, &full_bar[s], sb, kb * BK, brow);
+                if (args.terms == 2) {
+                    tma_load_2d(&map_lo, &full_bar[s], sa + 2 * TILE_BYTES, kb * BK, arow);
+                    tma_load_2d(&map_lo, &full_bar[s], sb + 2 * TILE_BYTES, kb * BK, brow);
+                }
                 ++issued;
             }
             if (!consumed_ok) {
@@ -212,10 +222,15 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t sa = smem_u32(smem + (size_t)s * STAGE_BYTES);
-                const uint32_t sb = sa + TILE_A_BYTES;
+                const uint32_t sb = sa + TILE_BYTES;
+                const uint32_t sal = sa + 2 * TILE_BYTES, sbl = sb + 2 * TILE_BYTES;
 #pragma unroll
                 for (int kk = 0; kk < BK / 16; ++kk) {
                     mma_f16(tmem, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32), idesc, (kb | kk) != 0);
+                    if (args.terms == 2) {
+                        mma_f16(tmem, smem_desc(sa + kk * 32), smem_desc(sbl + kk * 32), idesc, 1);
+                        mma_f16(tmem, smem_desc(sal + kk * 32), smem_desc(sb + kk * 32), idesc, 1);
+                    }
                 }
                 mma_commit(&empty_bar[s]);
             }
@@ -232,19 +247,19 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (ok) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int grow = gr + row;
-            const double si = args.inv_scale[(gr - args.prow0) / BM];
-            const double sj = args.inv_scale[(gc - args.prow0) / BN];
-            const double sc = si * sj;
+            const bool rin = grow < args.r0 + args.m;
+            const double si = rin ? args.inv_scale[grow - args.prow0] : 0.0;
             for (int c = 0; c < BN / 32; ++c) {
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 32), v);
-                if (grow < args.r0 + args.m) {
+                if (rin) {
 #pragma unroll 4
                     for (int j = 0; j < 32; ++j) {
                         const int gcol = gc + c * 32 + j;
                         if (gcol < args.c0 + args.n) {
+                            const double sj = args.inv_scale[gcol - args.prow0];
                             double *p = args.C + (long long)gcol * args.ldc + grow;
-                            *p -= sc * (double)v[j];
+                            *p -= (si * sj) * (double)v[j];
                         }
                     }
                 }

@@ -106,7 +106,7 @@ class Workload:
     nb: int = 960
     loc_seed: int = 1000
     z_seed: int = 2000
-    extra: dict = field(default_factory=dict)
+    extra: dict = field(default_factory=dict)   # factorisation options (prec, band, lowp, refine_iters, ...)
 
     def locations(self) -> tuple[np.ndarray, np.ndarray]:
         """(observed n x 2, held-out n_pred x 2), drawn jointly then split."""
@@ -129,9 +129,11 @@ WORKLOADS = {
                                  ThetaSpec((1.0, 1.0), 0.03, (0.5, 1.5), (0.5,)),
                                  n_pred=2000, nb=960, loc_seed=1001, z_seed=2001),
     # 50,000 locations (N = 100,000), mixed precision.
+    # FP64 diagonal tiles, FP32 band of 4 tiles, FP16 x 2 tensor cores beyond, 2 refinement sweeps.
     "bivariate-n50000-mixed": Workload("bivariate-n50000-mixed", 50000,
                                        ThetaSpec((1.0, 1.0), 0.1, (0.5, 1.0), (0.7,)),
-                                       nb=960, loc_seed=1002, z_seed=2002),
+                                       nb=1024, loc_seed=1002, z_seed=2002,
+                                       extra={"prec": 1, "band": 4, "lowp": 0, "refine_iters": 2}),
     # 60,000 locations, trivariate (N = 180,000), tile low-rank.
     "trivariate-n60000-tlr": Workload("trivariate-n60000-tlr", 60000,
                                       ThetaSpec((1.0, 1.0, 1.0), 0.05, (0.5, 1.0, 1.5), (0.5, 0.3, 0.4)),
