@@ -178,6 +178,11 @@ int geo_factor_stats_get(const geo_factor *factor, geo_factor_stats *out);
  *   what = 1: y = L^-1 Z, entries r0..r1-1
  *   what = 2: the location permutation, entries r0..r1-1 as doubles
  *             (internal location k is caller location perm[k])
+ * Tile-low-rank factors (tiles of nb rows; tile (i, j), i > j, is U V'):
+ *   what = 3: ranks of tiles (i, c0) for i = r0 .. r1-1 (-1 where i <= c0)
+ *   what = 4: U of tile (r0, c0), rows of tile r0 x rank, column-major
+ *   what = 5: V of tile (r0, c0), rows of tile c0 x rank, column-major
+ *   what = 6: diagonal tile r0 of L, column-major (zeros above the diagonal)
  */
 int geo_factor_read(const geo_factor *factor, int what, long long r0, long long r1, long long c0, long long c1,
                     double *host_out);
@@ -248,7 +253,8 @@ enum {
     GEO_K_AUX = 7,      /* gathers, scatters, conversions */
     GEO_K_TCGEMM = 8,   /* tensor-core (tcgen05) updates of far tiles, mixed precision */
     GEO_K_SGEMM = 9,    /* FP32 SIMT updates (mixed precision: diagonal and band tiles, panel) */
-    GEO_K_COUNT = 10
+    GEO_K_TLR = 10,     /* TLR compression: Householder QR and Jacobi SVD of sketched tiles */
+    GEO_K_COUNT = 11
 };
 typedef struct {
     long long launches;

@@ -58,7 +58,7 @@ class geo_mle_state(ctypes.Structure):
                 ("f", ctypes.c_double * (GEO_MLE_QMAX + 1)), ("last_f", ctypes.c_double)]
 
 
-GEO_K_NAMES = ["covgen", "potrf", "trsm", "gemm", "reduce", "solve", "predict", "aux", "tcgemm", "sgemm"]
+GEO_K_NAMES = ["covgen", "potrf", "trsm", "gemm", "reduce", "solve", "predict", "aux", "tcgemm", "sgemm", "tlr"]
 GEO_K_COUNT = len(GEO_K_NAMES)
 
 
@@ -295,6 +295,7 @@ def geo_factor_stats_get(factor: Factor) -> geo_factor_stats:
 
 
 def geo_factor_read(factor: Factor, what: int, r0: int, r1: int, c0: int = 0, c1: int = 0) -> np.ndarray:
+    """Modes 0 (block of L), 1 (y = L^-1 Z), 2 (permutation), 3 (TLR ranks); see geo_tlr_tile for 4-6."""
     n = (r1 - r0) * (c1 - c0) if what == 0 else (r1 - r0)
     out = np.zeros(max(n, 1), dtype=np.float64)
     factor.ctx.check(factor.ctx.lib.geo_factor_read(factor.handle, what, r0, r1, c0, c1,
@@ -373,3 +374,33 @@ def geo_loglik_noalloc(locs, z, theta: Theta, out, info=None, nb: int = 960, str
         _dev_ptr(locs, "locs", torch.float64), locs.shape[0], _dev_ptr(z, "z", torch.float64), ctypes.byref(th),
         int(nb), _dev_ptr(out, "out", torch.float64),
         _dev_ptr(info, "info", torch.int32) if info is not None else None, _stream(stream))
+
+
+def geo_tlr_tile(factor: Factor, i: int, j: int, which: str = "U") -> np.ndarray:
+    """A tile of a TLR factor: "U" / "V" of the off-diagonal tile (i, j), i > j
+    (columns = rank), or "D" for the diagonal tile i of L."""
+    st = geo_factor_stats_get(factor)
+    nb, N = st.nb, st.N
+    mt = lambda t: min(nb, N - t * nb)
+    if which == "D":
+        m = mt(i)
+        out = np.zeros(m * m)
+        factor.ctx.check(factor.ctx.lib.geo_factor_read(factor.handle, 6, i, i + 1, 0, 0,
+                                                        out.ctypes.data_as(ctypes.c_void_p)))
+        return out.reshape(m, m, order="F")
+    r = int(geo_factor_read(factor, 3, i, i + 1, j, j + 1)[0])
+    m = mt(i) if which == "U" else mt(j)
+    out = np.zeros(max(m * r, 1))
+    factor.ctx.check(factor.ctx.lib.geo_factor_read(factor.handle, 4 if which == "U" else 5, i, i + 1, j, j + 1,
+                                                    out.ctypes.data_as(ctypes.c_void_p)))
+    return out[:m * r].reshape(m, r, order="F")
+
+
+def geo_tlr_ranks(factor: Factor) -> np.ndarray:
+    """T x T matrix of off-diagonal tile ranks (-1 on and above the diagonal)."""
+    st = geo_factor_stats_get(factor)
+    T = (st.N + st.nb - 1) // st.nb
+    R = -np.ones((T, T), dtype=np.int64)
+    for j in range(T):
+        R[:, j] = geo_factor_read(factor, 3, 0, T, j, j + 1).astype(np.int64)
+    return R

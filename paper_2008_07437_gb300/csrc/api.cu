@@ -37,6 +37,9 @@ struct geo_ctx {
     // iterative refinement: copy of Sigma, sorted Z, partial sums
     void *sws = nullptr, *zws = nullptr, *rws = nullptr;
     size_t sws_bytes = 0, zws_bytes = 0, rws_bytes = 0;
+    // TLR workspace (device) and descriptor staging (pinned host)
+    void *tws = nullptr, *tarena = nullptr;
+    size_t tws_bytes = 0, tarena_bytes = 0;
     std::vector<geo_factor *> factors;
     Profiler prof;
 };
@@ -52,6 +55,10 @@ struct geo_factor {
     std::vector<int> perm;                 // internal k -> caller location perm[k]
     CovParams cp;
     double loglik = 0, logdet = 0, quad = 0;
+    // tile-low-rank form
+    TlrFactor *tlr = nullptr;
+    size_t tlr_bytes = 0;
+    double *ybuf = nullptr;                // L^-1 Z (TLR form)
 };
 
 thread_local Profiler *t_prof = nullptr;
@@ -375,6 +382,8 @@ int geo_destroy(geo_ctx *ctx) {
     if (ctx->sws) dev_free(ctx, ctx->sws, ctx->sws_bytes);
     if (ctx->zws) dev_free(ctx, ctx->zws, ctx->zws_bytes);
     if (ctx->rws) dev_free(ctx, ctx->rws, ctx->rws_bytes);
+    if (ctx->tws) dev_free(ctx, ctx->tws, ctx->tws_bytes);
+    if (ctx->tarena) cudaFreeHost(ctx->tarena);
     if (ctx->st) cudaFree(ctx->st);
     if (ctx->res) cudaFree(ctx->res);
     if (ctx->h_st) cudaFreeHost(ctx->h_st);
@@ -405,7 +414,7 @@ int geo_covgen(geo_ctx *ctx, const double *locs1_dev, int n1, const double *locs
 
 // Shared front half of loglik / simulate: order locations, generate Sigma.
 static int prepare_matrix(geo_ctx *ctx, const double *locs_dev, int n, const geo_theta *theta,
-                          const geo_opts *o, int extra_rows, geo_factor *f, cudaStream_t s) {
+                          const geo_opts *o, int extra_rows, geo_factor *f, cudaStream_t s, bool with_matrix = true) {
     std::string err;
     int rc = theta_to_params(theta, &f->cp, &err);
     if (rc) return fail(ctx, rc, err);
@@ -436,6 +445,12 @@ static int prepare_matrix(geo_ctx *ctx, const double *locs_dev, int n, const geo
     int *d_perm = (int *)p2;
     CK(cudaMemcpyAsync(d_perm, f->perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
     CK(launch_gather_locs(locs_dev, d_perm, n, f->lx, f->ly, s));
+    if (!with_matrix) {
+        CK(cudaMemsetAsync(ctx->st, 0, sizeof(DevStatus), s));
+        CK(cudaStreamSynchronize(s));
+        dev_free(ctx, d_perm, sizeof(int) * n);
+        return GEO_OK;
+    }
     // matrix
     const size_t bytes = sizeof(double) * (size_t)f->ld * (size_t)f->N;
     if (ctx->ws && ctx->ws_bytes >= bytes) {
@@ -479,6 +494,113 @@ static void release_factor_buffers(geo_ctx *ctx, geo_factor *f, bool keep_matrix
     if (f->lx) dev_free(ctx, f->lx, sizeof(double) * 2 * f->n);
     if (f->w) dev_free(ctx, f->w, sizeof(double) * f->N);
     f->lx = f->ly = f->w = nullptr;
+    if (f->ybuf) dev_free(ctx, f->ybuf, sizeof(double) * f->N);
+    f->ybuf = nullptr;
+    if (f->tlr) {
+        if (f->tlr->D) dev_free(ctx, f->tlr->D, f->tlr_bytes);
+        for (auto &sg : f->tlr->segs) dev_free(ctx, sg.first, sizeof(double) * sg.second);
+        delete f->tlr;
+        f->tlr = nullptr;
+    }
+}
+
+// Tile-low-rank evaluation of Eq. 1 (Sec. 5.3).
+static int loglik_tlr(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev, const geo_theta *theta,
+                      const geo_opts &o, double *loglik_host, geo_factor **keep, int *info, cudaStream_t s) {
+    geo_factor *f = new geo_factor();
+    f->ctx = ctx;
+    int rc = prepare_matrix(ctx, locs_dev, n, theta, &o, 0, f, s, false);
+    auto bail = [&](int code) {
+        release_factor_buffers(ctx, f, false);
+        delete f;
+        return code;
+    };
+    if (rc) return bail(rc);
+    const int N = f->N, p = f->p, nb = o.nb;
+    if (nb % p != 0) return bail(fail(ctx, GEO_EINVAL, "TLR needs nb to be a multiple of p"));
+    if (!(o.tlr_tol > 0.0) || o.tlr_kmax < 1) return bail(fail(ctx, GEO_EINVAL, "TLR needs tol > 0 and kmax >= 1"));
+    TlrFactor *F = new TlrFactor();
+    f->tlr = F;
+    F->N = N;
+    F->nb = nb;
+    F->T = (N + nb - 1) / nb;
+    F->kmax = std::min(o.tlr_kmax, nb);
+    F->tol = o.tlr_tol;
+    const size_t fbytes = tlr_factor_bytes(N, nb, F->kmax);
+    void *pf;
+    if ((rc = dev_alloc(ctx, &pf, fbytes))) return bail(rc);
+    f->tlr_bytes = fbytes;
+    F->D = (double *)pf;
+    // U / V segments: a quarter of the dense lower tiles at a time, at least the request
+    const size_t seg_default = std::max((size_t)1 << 24, (size_t)F->T * (F->T - 1) / 8 * nb * nb / 2);
+    F->grow = [ctx, F, seg_default](size_t need) -> double * {
+        void *p = nullptr;
+        const size_t n = std::max(need, seg_default);
+        if (dev_alloc(ctx, &p, sizeof(double) * n) != GEO_OK) {
+            // retry with exactly the request
+            if (n == need || dev_alloc(ctx, &p, sizeof(double) * need) != GEO_OK) return nullptr;
+            F->segs.push_back({(double *)p, need});
+            return (double *)p;
+        }
+        F->segs.push_back({(double *)p, n});
+        return (double *)p;
+    };
+    const size_t wbytes = std::max(tlr_workspace_bytes(N, nb, F->kmax), tlr_solve_workspace_bytes(N, nb, F->kmax));
+    if ((rc = ensure_buffer(ctx, &ctx->tws, &ctx->tws_bytes, wbytes, s))) return bail(rc);
+    const size_t abytes = TLR_ARENA_BYTES + sizeof(double) * (size_t)F->T * (F->kmax + 16) + 4096;
+    if (ctx->tarena_bytes < abytes) {
+        if (ctx->tarena) {
+            cudaStreamSynchronize(s);
+            cudaFreeHost(ctx->tarena);
+            ctx->tarena = nullptr;
+            ctx->tarena_bytes = 0;
+        }
+        if (cudaMallocHost(&ctx->tarena, abytes) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(ctx, GEO_ENOMEM, "pinned staging buffer"));
+        }
+        ctx->tarena_bytes = abytes;
+    }
+    void *py, *pp;
+    if ((rc = dev_alloc(ctx, &py, sizeof(double) * N))) return bail(rc);
+    f->ybuf = (double *)py;
+    if ((rc = dev_alloc(ctx, &pp, sizeof(int) * n))) return bail(rc);
+    int *d_perm = (int *)pp;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(d_perm, f->perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s)) ||
+        (e = launch_gather_vec(z_dev, d_perm, n, p, f->ybuf, 1, s)) ||
+        (e = tlr_factor(*F, f->cp, f->lx, f->ly, ctx->tws, ctx->tws_bytes, ctx->tarena, ctx->st, ctx->h_st, s))) {
+        cudaStreamSynchronize(s);
+        dev_free(ctx, d_perm, sizeof(int) * n);
+        if (e == cudaErrorMemoryAllocation)
+            return bail(fail(ctx, GEO_ENOMEM, "TLR: the tiles' ranks exceed the factor's pool (raise tlr_kmax or tlr_tol)"));
+        return bail(cuda_fail(ctx, e, "TLR factorisation"));
+    }
+    CK(cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    dev_free(ctx, d_perm, sizeof(int) * n);
+    if (ctx->h_st->info) {
+        if (info) *info = ctx->h_st->info;
+        if (loglik_host) *loglik_host = nan("");
+        return bail(fail(ctx, GEO_ENOTSPD, "Sigma(theta) is not positive definite (TLR diagonal tile)"));
+    }
+    if ((e = tlr_solve(*F, f->ybuf, false, ctx->tws, ctx->tarena, s)) ||
+        (e = tlr_reduce(*F, f->ybuf, ctx->st, ctx->res, s)) ||
+        (e = cudaMemcpyAsync(ctx->h_res, ctx->res, sizeof(DevResults), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s)))
+        return bail(cuda_fail(ctx, e, "TLR solve"));
+    f->loglik = ctx->h_res->loglik;
+    f->logdet = ctx->h_res->logdet;
+    f->quad = ctx->h_res->quad;
+    if (loglik_host) *loglik_host = f->loglik;
+    if (keep) {
+        ctx->factors.push_back(f);
+        *keep = f;
+    } else {
+        release_factor_buffers(ctx, f, false);
+        delete f;
+    }
+    return GEO_OK;
 }
 
 int geo_loglik(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev, const geo_theta *theta,
@@ -494,12 +616,13 @@ int geo_loglik(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev,
         geo_opts_default(&o);
     if (n <= 0 || !locs_dev || !z_dev) return fail(ctx, GEO_EINVAL, "n must be > 0 and pointers non-NULL");
     if (o.nb < 64) return fail(ctx, GEO_EINVAL, "nb must be >= 64");
-    if (o.prec != GEO_PREC_FP64 && o.prec != GEO_PREC_MIXED)
+    if (o.prec != GEO_PREC_FP64 && o.prec != GEO_PREC_MIXED && o.prec != GEO_PREC_TLR)
         return fail(ctx, GEO_EUNSUPPORTED, "precision mode not built");
     if (o.prec == GEO_PREC_MIXED && (o.nb % 128 != 0 || o.band < 0))
         return fail(ctx, GEO_EINVAL, "mixed precision needs nb a multiple of 128 and band >= 0");
     SetDevice sd(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
+    if (o.prec == GEO_PREC_TLR) return loglik_tlr(ctx, locs_dev, n, z_dev, theta, o, loglik_host, keep, info, s);
     geo_factor *f = new geo_factor();
     f->ctx = ctx;
     int rc = prepare_matrix(ctx, locs_dev, n, theta, &o, 1, f, s);
@@ -600,7 +723,12 @@ int geo_predict(geo_ctx *ctx, const geo_factor *factor, const double *new_locs_d
         int rc = dev_alloc(ctx, &pw, sizeof(double) * f->N);
         if (rc) return rc;
         f->w = (double *)pw;
-        CK(backward_solve(f->A, f->ld, f->N, f->A + f->N, f->ld, f->w, s));
+        if (f->tlr) {
+            CK(cudaMemcpyAsync(f->w, f->ybuf, sizeof(double) * f->N, cudaMemcpyDeviceToDevice, s));
+            CK(tlr_solve(*f->tlr, f->w, true, ctx->tws, ctx->tarena, s));
+        } else {
+            CK(backward_solve(f->A, f->ld, f->N, f->A + f->N, f->ld, f->w, s));
+        }
     }
     CK(launch_predict(f->cp, new_locs_dev, m, f->lx, f->ly, f->n, f->w, zhat_dev, s));
     return GEO_OK;
@@ -681,6 +809,16 @@ int geo_factor_stats_get(const geo_factor *f, geo_factor_stats *out) {
     out->quad = f->quad;
     out->device_bytes = (long long)(f->A_bytes + sizeof(double) * 2 * f->n + (f->w ? sizeof(double) * f->N : 0));
     out->tlr_bytes_ratio = 1.0;
+    if (f->tlr) {
+        const TlrFactor &F = *f->tlr;
+        double used = (double)F.T * F.nb * F.nb;
+        for (int r : F.rank) used += 2.0 * F.nb * r;
+        const double dense = (double)F.T * (F.T + 1) / 2.0 * F.nb * F.nb;
+        out->tlr_bytes_ratio = used / dense;
+        out->tlr_max_rank = F.max_rank;
+        out->tlr_dense_tiles = F.capped;
+        out->device_bytes = (long long)(8.0 * used + sizeof(double) * (2.0 * f->n + f->N));
+    }
     return GEO_OK;
 }
 
@@ -709,6 +847,35 @@ int geo_factor_read(const geo_factor *f, int what, long long r0, long long r1, l
     if (what == 2) {
         if (r0 < 0 || r1 > f->n || r1 < r0) return fail(ctx, GEO_EINVAL, "range out of bounds");
         for (long long k = r0; k < r1; ++k) host_out[k - r0] = (double)f->perm[k];
+        return GEO_OK;
+    }
+    if (what >= 3 && what <= 6) {
+        if (!f->tlr) return fail(ctx, GEO_EINVAL, "not a TLR factor");
+        const TlrFactor &F = *f->tlr;
+        auto mt = [&](long long t) { return (long long)std::min(F.nb, F.N - (int)t * F.nb); };
+        if (what == 3) {   // ranks of tiles (r0, c0 = j) for rows r0 .. r1-1
+            for (long long i = r0; i < r1; ++i)
+                host_out[i - r0] = (i > c0 && i < F.T && c0 >= 0) ? (double)F.rank[(size_t)i * (i - 1) / 2 + c0] : -1.0;
+            return GEO_OK;
+        }
+        if (what == 6) {   // diagonal tile r0 of L (mt x mt, column-major)
+            if (r0 < 0 || r0 >= F.T) return fail(ctx, GEO_EINVAL, "tile out of range");
+            const long long m = mt(r0);
+            std::vector<double> buf((size_t)F.nb * m);
+            CK(cudaMemcpy(buf.data(), F.D + (size_t)r0 * F.nb * F.nb, sizeof(double) * F.nb * m, cudaMemcpyDeviceToHost));
+            for (long long c = 0; c < m; ++c)
+                for (long long r = 0; r < m; ++r) host_out[c * m + r] = (r >= c) ? buf[(size_t)c * F.nb + r] : 0.0;
+            return GEO_OK;
+        }
+        // U (what 4, mt(r0) x rank) or V (what 5, mt(c0) x rank) of tile (r0, c0), column-major
+        if (!(r0 > c0 && c0 >= 0 && r0 < F.T)) return fail(ctx, GEO_EINVAL, "tile out of range");
+        const size_t sl = (size_t)r0 * (r0 - 1) / 2 + c0;
+        const long long k = F.rank[sl], m = (what == 4) ? mt(r0) : mt(c0);
+        const double *src = (what == 4) ? F.Uof(sl) : F.Vof(sl);
+        std::vector<double> buf((size_t)F.nb * std::max(k, 1LL));
+        if (k) CK(cudaMemcpy(buf.data(), src, sizeof(double) * F.nb * k, cudaMemcpyDeviceToHost));
+        for (long long c = 0; c < k; ++c)
+            for (long long r = 0; r < m; ++r) host_out[c * m + r] = buf[(size_t)c * F.nb + r];
         return GEO_OK;
     }
     return fail(ctx, GEO_EINVAL, "unknown 'what'");

@@ -1,0 +1,287 @@
+// Batched FP64 building blocks of the tile-low-rank factorisation (Sec. 5.3):
+// variable-size GEMMs, Householder QR of tall-skinny blocks, one-sided Jacobi
+// SVD of small square blocks, and the Gaussian test matrices of the
+// randomized range finder.  Every problem of a batch is independent; each
+// kernel maps one problem (or one 64 x 64 tile of it) to one CTA.
+#include <math.h>
+
+#include "geo_internal.cuh"
+
+namespace {
+
+// ---- batched GEMM: C = alpha op(A) op(B) + beta C (column-major) ----------
+constexpr int BT = 64, BKK = 16;
+
+__global__ void __launch_bounds__(256) k_bgemm(const GemmDesc *__restrict__ d, int count) {
+    __shared__ double As[BKK][BT + 2];
+    __shared__ double Bs[BKK][BT + 2];
+    const int pi = blockIdx.y;
+    if (pi >= count) return;
+    const GemmDesc g = d[pi];
+    const int tiles_m = (g.m + BT - 1) / BT;
+    const int tiles_n = (g.n + BT - 1) / BT;
+    if ((int)blockIdx.x >= tiles_m * tiles_n) return;
+    const int tm = (blockIdx.x % tiles_m) * BT, tn = (blockIdx.x / tiles_m) * BT;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int k0 = 0; k0 < g.k; k0 += BKK) {
+        for (int t = threadIdx.x; t < BKK * BT; t += 256) {
+            const int kk = t / BT, r = t % BT;
+            const int kg = k0 + kk;
+            double a = 0.0, b = 0.0;
+            if (kg < g.k && tm + r < g.m)
+                a = g.ta ? g.A[(long long)(tm + r) * g.lda + kg] : g.A[(long long)kg * g.lda + tm + r];
+            if (kg < g.k && tn + r < g.n)
+                b = g.tb ? g.B[(long long)kg * g.ldb + tn + r] : g.B[(long long)(tn + r) * g.ldb + kg];
+            As[kk][r] = a;
+            Bs[kk][r] = b;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BKK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c = tn + tx + 16 * j;
+        if (c >= g.n) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = tm + ty + 16 * i;
+            if (r >= g.m) continue;
+            double *p = g.C + (long long)c * g.ldc + r;
+            *p = g.alpha * acc[i][j] + (g.beta == 0.0 ? 0.0 : g.beta * *p);
+        }
+    }
+}
+
+// ---- Householder QR of an m x r block (m >= r), in place -------------------
+// Column c: v = x - alpha e1 with alpha = -sign(x_0) |x|, stored below the
+// diagonal (v_0 kept in tau-scaled form), R on and above the diagonal; then
+// the thin Q (m x r) is formed in Qout by applying the reflectors backwards
+// to [I; 0].  One CTA (8 warps) per block; warp w updates columns w, w+8, ...
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return __shfl_sync(0xffffffffu, v, 0);
+}
+
+__global__ void __launch_bounds__(256) k_house_qr(const QrDesc *__restrict__ d, int count) {
+    const int pi = blockIdx.x;
+    if (pi >= count) return;
+    const QrDesc q = d[pi];
+    double *Y = q.Y;
+    const long long ld = q.ldy;
+    const int m = q.m, r = q.r;
+    double *tau = q.tau;   // r entries
+    __shared__ double red[8];
+    __shared__ double s_alpha, s_tau, s_v0;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int c = 0; c < r; ++c) {
+        double *x = Y + (long long)c * ld;
+        // norm of x[c:m]
+        double s = 0.0;
+        for (int i = c + threadIdx.x; i < m; i += 256) s += x[i] * x[i];
+        s = warp_sum(s);
+        if (lane == 0) red[warp] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < 8; ++w) t += red[w];
+            const double nrm = sqrt(t);
+            const double x0 = x[c];
+            double alpha = (x0 >= 0.0) ? -nrm : nrm;
+            double v0 = x0 - alpha;
+            double taue;
+            if (nrm == 0.0) {
+                alpha = 0.0;
+                v0 = 1.0;
+                taue = 0.0;
+            } else {
+                // H = I - tau v v' with v = (v0, x[c+1:]), tau = 2 / (v'v), v'v = 2 nrm (nrm - x0 sign...)
+                const double vtv = v0 * v0 + (t - x0 * x0);
+                taue = (vtv > 0.0) ? 2.0 / vtv : 0.0;
+            }
+            s_alpha = alpha;
+            s_tau = taue;
+            s_v0 = v0;
+        }
+        __syncthreads();
+        const double v0 = s_v0, tauc = s_tau;
+        // apply to columns c+1 .. r-1: y -= tau (v'y) v
+        for (int j = c + 1 + warp; j < r; j += 8) {
+            double *y = Y + (long long)j * ld;
+            double dot = (lane == 0) ? v0 * y[c] : 0.0;
+            for (int i = c + 1 + lane; i < m; i += 32) dot += x[i] * y[i];
+            dot = warp_sum(dot) * tauc;
+            if (lane == 0) y[c] -= dot * v0;
+            for (int i = c + 1 + lane; i < m; i += 32) y[i] -= dot * x[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            x[c] = s_alpha;   // R diagonal
+            tau[c] = s_tau;
+            q.v0[c] = s_v0;
+        }
+        __syncthreads();
+    }
+    // thin Q: start from [I; 0] and apply H_c for c = r-1 .. 0
+    double *Q = q.Q;
+    const long long ldq = q.ldq;
+    for (int j = warp; j < r; j += 8)
+        for (int i = lane; i < m; i += 32) Q[(long long)j * ldq + i] = (i == j) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int c = r - 1; c >= 0; --c) {
+        const double *x = Y + (long long)c * ld;
+        const double v0 = q.v0[c], tauc = tau[c];
+        for (int j = c + warp; j < r; j += 8) {
+            double *y = Q + (long long)j * ldq;
+            double dot = (lane == 0) ? v0 * y[c] : 0.0;
+            for (int i = c + 1 + lane; i < m; i += 32) dot += x[i] * y[i];
+            dot = warp_sum(dot) * tauc;
+            if (lane == 0) y[c] -= dot * v0;
+            for (int i = c + 1 + lane; i < m; i += 32) y[i] -= dot * x[i];
+        }
+        __syncthreads();
+    }
+}
+
+// ---- one-sided Jacobi SVD of an r x r block M (Hestenes) --------------------
+// Rotates column pairs of M (and accumulates V) until every pair is
+// orthogonal to relative 1e-15 or the sweep budget is spent; on exit the
+// column norms of M are the singular values (unsorted), M = U S V' with
+// U = M_col / norm.  Pairs are processed in round-robin order, r/2 disjoint
+// pairs per round, one warp per pair.
+__global__ void __launch_bounds__(256) k_jacobi_svd(const SvdDesc *__restrict__ d, int count, int max_sweeps) {
+    const int pi = blockIdx.x;
+    if (pi >= count) return;
+    const SvdDesc s = d[pi];
+    const int r = s.r;
+    double *M = s.M, *V = s.V;
+    const long long ld = s.ld;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int j = warp; j < r; j += 8)
+        for (int i = lane; i < r; i += 32) V[(long long)j * ld + i] = (i == j) ? 1.0 : 0.0;
+    __shared__ int rotated;
+    const int rr = r + (r & 1);   // round-robin over an even count (index r = dummy)
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        if (threadIdx.x == 0) rotated = 0;
+        __syncthreads();
+        for (int round = 0; round < rr - 1; ++round) {
+            for (int pr = warp; pr < rr / 2; pr += 8) {
+                // pairing of the circle method: position 0 fixed, others rotate
+                int a = (pr == 0) ? 0 : 1 + (pr - 1 + round) % (rr - 1);
+                int b = 1 + (rr - 2 - pr + round) % (rr - 1);
+                if (a >= r || b >= r || a == b) continue;
+                if (a > b) {
+                    const int t = a;
+                    a = b;
+                    b = t;
+                }
+                double *ma = M + (long long)a * ld, *mb = M + (long long)b * ld;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = lane; i < r; i += 32) {
+                    const double x = ma[i], y = mb[i];
+                    al += x * x;
+                    be += y * y;
+                    ga += x * y;
+                }
+                al = warp_sum(al);
+                be = warp_sum(be);
+                ga = warp_sum(ga);
+                // both columns far below the truncation threshold: they are dropped anyway,
+                // and any combination of them stays below sqrt(r) * skip
+                if (al < s.skip * s.skip && be < s.skip * s.skip) continue;
+                if (fabs(ga) <= 1e-15 * sqrt(al * be) || ga == 0.0) continue;
+                const double zeta = (be - al) / (2.0 * ga);
+                const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+                for (int i = lane; i < r; i += 32) {
+                    const double x = ma[i], y = mb[i];
+                    ma[i] = cs * x - sn * y;
+                    mb[i] = sn * x + cs * y;
+                }
+                double *va = V + (long long)a * ld, *vb = V + (long long)b * ld;
+                for (int i = lane; i < r; i += 32) {
+                    const double x = va[i], y = vb[i];
+                    va[i] = cs * x - sn * y;
+                    vb[i] = sn * x + cs * y;
+                }
+                if (lane == 0) rotated = 1;
+            }
+            __syncthreads();
+        }
+        if (!rotated) break;
+        __syncthreads();
+    }
+    // singular values = column norms
+    for (int j = warp; j < r; j += 8) {
+        double t = 0.0;
+        for (int i = lane; i < r; i += 32) t += M[(long long)j * ld + i] * M[(long long)j * ld + i];
+        t = warp_sum(t);
+        if (lane == 0) s.sigma[j] = sqrt(t);
+    }
+}
+
+// ---- Gaussian test matrices: counter-based SplitMix64 -> Box-Muller ---------
+__device__ __forceinline__ unsigned long long splitmix(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_gaussian(double *O, long long n, unsigned long long seed) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (n + 1) / 2) return;
+    const unsigned long long h1 = splitmix(seed ^ (2ull * t)), h2 = splitmix(seed ^ (2ull * t + 1));
+    const double u1 = 1.0 - (double)(h1 >> 11) * (1.0 / 9007199254740992.0);
+    const double u2 = (double)(h2 >> 11) * (1.0 / 9007199254740992.0);
+    const double rad = sqrt(-2.0 * log(u1));
+    O[2 * t] = rad * cos(6.283185307179586 * u2);
+    if (2 * t + 1 < n) O[2 * t + 1] = rad * sin(6.283185307179586 * u2);
+}
+
+}  // namespace
+
+cudaError_t launch_bgemm(const GemmDesc *d_desc, int count, int max_tiles, cudaStream_t s, double flops) {
+    if (count <= 0 || max_tiles <= 0) return cudaSuccess;
+    KScope ks(GEO_K_GEMM, s, flops, 0.0);
+    k_bgemm<<<dim3(max_tiles, count), 256, 0, s>>>(d_desc, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_house_qr(const QrDesc *d_desc, int count, cudaStream_t s, double flops) {
+    if (count <= 0) return cudaSuccess;
+    KScope ks(GEO_K_TLR, s, flops, 0.0);
+    k_house_qr<<<count, 256, 0, s>>>(d_desc, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi_svd(const SvdDesc *d_desc, int count, int max_sweeps, cudaStream_t s, double flops) {
+    if (count <= 0) return cudaSuccess;
+    KScope ks(GEO_K_TLR, s, flops, 0.0);
+    k_jacobi_svd<<<count, 256, 0, s>>>(d_desc, count, max_sweeps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gaussian(double *O, long long n, unsigned long long seed, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    KScope ks(GEO_K_AUX, s);
+    const long long pairs = (n + 1) / 2;
+    k_gaussian<<<(unsigned)((pairs + 255) / 256), 256, 0, s>>>(O, n, seed);
+    return cudaGetLastError();
+}

@@ -183,14 +183,17 @@ cudaError_t gemm_update(double *A, long long ld, int rC, int cC, int m, int n, i
 // Factor the panel of columns [j0, j0 + jb): its diagonal tile (inner 64-wide
 // blocks: POTRF, TRSM, rank-64 update) and, carried through the same inner
 // steps, the rows [x0, x1) below the tile (x0 >= j0 + jb; x0 == x1 = none).
-cudaError_t chol64_panel(double *A, long long ld, int j0, int jb, int x0, int x1, DevStatus *st, cudaStream_t s) {
+// With factor_diag false the diagonal tile must already hold L and only the
+// rows [x0, x1) are solved against it (X <- X L^-T).
+cudaError_t chol64_panel(double *A, long long ld, int j0, int jb, int x0, int x1, DevStatus *st, cudaStream_t s,
+                         bool factor_diag) {
     const size_t trsm_smem = sizeof(double) * (IB * IB + IB * (TRSM_ROWS + 1));
     cudaError_t e = cudaFuncSetAttribute(k_trsm_rlt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem);
     if (e != cudaSuccess) return e;
-    const bool contiguous = (x0 == j0 + jb);
+    const bool contiguous = factor_diag && (x0 == j0 + jb);
     for (int c0 = j0; c0 < j0 + jb; c0 += IB) {
         const int cb = min(IB, j0 + jb - c0);
-        {
+        if (factor_diag) {
             KScope ks(GEO_K_POTRF, s, (double)cb * cb * cb / 3.0, 16.0 * cb * cb);
             k_potrf_diag<<<1, 256, 0, s>>>(A, ld, c0, cb, st);
         }
@@ -198,7 +201,9 @@ cudaError_t chol64_panel(double *A, long long ld, int j0, int jb, int x0, int x1
         // row ranges carried through this inner step
         int ra[2][2];
         int nrange = 0;
-        if (contiguous) {
+        if (!factor_diag) {
+            if (x0 < x1) ra[nrange][0] = x0, ra[nrange][1] = x1, ++nrange;
+        } else if (contiguous) {
             if (rows0 < x1) ra[nrange][0] = rows0, ra[nrange][1] = x1, ++nrange;
         } else {
             if (rows0 < j0 + jb) ra[nrange][0] = rows0, ra[nrange][1] = j0 + jb, ++nrange;

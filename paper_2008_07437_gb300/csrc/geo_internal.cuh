@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "geo.h"
@@ -87,7 +89,8 @@ cudaError_t launch_scatter_vec(const double *in, long long stride, const int *pe
 // receives (L^-1 z)' when it holds z').  nb = outer tile size.
 cudaError_t chol64_factor(double *A, long long ld, int N, int nrows, int nb, DevStatus *st, cudaStream_t s);
 // One panel [j0, j0+jb): diagonal tile plus extra rows [x0, x1) carried along.
-cudaError_t chol64_panel(double *A, long long ld, int j0, int jb, int x0, int x1, DevStatus *st, cudaStream_t s);
+cudaError_t chol64_panel(double *A, long long ld, int j0, int jb, int x0, int x1, DevStatus *st, cudaStream_t s,
+                         bool factor_diag = true);
 // C[rC.., cC..] (m x n) -= A[rC.., kA..kA+k] A[cC.., kA..kA+k]' in FP64.
 cudaError_t chol64_gemm_update(double *A, long long ld, int rC, int cC, int m, int n, int kA, int k, DevStatus *st,
                                cudaStream_t s);
@@ -116,6 +119,98 @@ size_t refine_workspace_bytes(int N);
 cudaError_t refine_solve(const double *S, const double *A, long long ld, int N, const double *z, const double *y,
                          long long ystride, int iters, double *x, void *ws, const DevStatus *st, DevResults *res,
                          cudaStream_t s);
+
+// ---- batched.cu -----------------------------------------------------------
+struct GemmDesc {           // C = alpha op(A) op(B) + beta C, column-major
+    int m, n, k, ta, tb;
+    const double *A;
+    long long lda;
+    const double *B;
+    long long ldb;
+    double *C;
+    long long ldc;
+    double alpha, beta;
+};
+struct QrDesc {             // in-place Householder QR of Y (m x r), thin Q out
+    int m, r;
+    double *Y;
+    long long ldy;
+    double *Q;
+    long long ldq;
+    double *tau, *v0;       // r entries each
+};
+struct SvdDesc {            // one-sided Jacobi SVD of M (r x r): M <- M V, V, sigma
+    int r;
+    double *M, *V;
+    long long ld;
+    double *sigma;
+    double skip;            // pairs of columns both below this norm are left alone (0 = none)
+};
+cudaError_t launch_bgemm(const GemmDesc *d_desc, int count, int max_tiles, cudaStream_t s, double flops);
+cudaError_t launch_house_qr(const QrDesc *d_desc, int count, cudaStream_t s, double flops);
+cudaError_t launch_jacobi_svd(const SvdDesc *d_desc, int count, int max_sweeps, cudaStream_t s, double flops);
+cudaError_t launch_gaussian(double *O, long long n, unsigned long long seed, cudaStream_t s);
+
+// ---- tlr.cu ---------------------------------------------------------------
+constexpr int TLR_KCHUNK = 2048;            // stacked rank per update chunk
+constexpr int TLR_MAXK_PER_CHUNK = 16;      // column tiles per update chunk
+constexpr size_t TLR_ARENA_BYTES = 16u << 20;
+struct TlrFactor {
+    int N = 0, nb = 0, T = 0, kmax = 0;
+    double tol = 0.0;
+    double *D = nullptr;                    // T diagonal tiles nb x nb (ld nb), lower = L_tt
+    // U and V of every off-diagonal tile live in pool segments (nb x rank each, ld nb);
+    // a new segment is requested through grow() when the current one is full
+    std::vector<std::pair<double *, size_t>> segs;   // (pointer, capacity in doubles)
+    size_t seg_used = 0;                              // doubles used in the last segment
+    std::function<double *(size_t)> grow;             // returns a segment of >= n doubles or nullptr
+    std::vector<int> rank;                  // per slot(i, j) = i (i - 1) / 2 + j
+    std::vector<double *> uptr, vptr;       // per slot
+    std::vector<char> dense;                // per slot: stored dense (U = L_ij, V = I; rank = tile width)
+    int capped = 0, max_rank = 0;           // capped = tiles stored dense (rank above kmax)
+    double *Uof(size_t sl) const { return uptr[sl]; }
+    double *Vof(size_t sl) const { return vptr[sl]; }
+    double *take(size_t n) {
+        if (segs.empty() || seg_used + n > segs.back().second) {
+            double *p = grow ? grow(n) : nullptr;
+            if (!p) return nullptr;
+            seg_used = 0;
+        }
+        double *p = segs.back().first + seg_used;
+        seg_used += (n + 31) / 32 * 32;
+        return p;
+    }
+};
+struct TlrR2Desc {
+    int r;
+    const double *B;
+    long long ldb;
+    double *M;
+    long long ldm;
+};
+struct TlrSelDesc {
+    int r, k;
+    const double *M, *Vj;
+    double *Msel, *Vsel;
+    long long ld;
+    const int *sel;
+};
+struct TlrTrsmDesc {
+    const double *L;
+    long long ldl;
+    double *X;
+    long long ldx;
+    int ncols;
+};
+size_t tlr_factor_bytes(int N, int nb, int kmax);
+size_t tlr_workspace_bytes(int N, int nb, int kmax);
+size_t tlr_solve_workspace_bytes(int N, int nb, int kmax);
+cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, const double *ly, void *ws,
+                       size_t ws_bytes, void *arena_host, DevStatus *st, DevStatus *h_st, cudaStream_t s);
+cudaError_t tlr_solve(const TlrFactor &F, double *x, bool transpose, void *ws, void *arena_host, cudaStream_t s);
+cudaError_t tlr_reduce(const TlrFactor &F, const double *y, const DevStatus *st, DevResults *res, cudaStream_t s);
+cudaError_t backward_solve(const double *A, long long ld, int N, const double *y, long long ystride, double *w,
+                           cudaStream_t s);
 
 // ---- host helpers (api.cu) ------------------------------------------------
 int theta_to_params(const geo_theta *th, CovParams *cp, std::string *err);
