@@ -73,13 +73,15 @@ __global__ void __launch_bounds__(256) k_bgemm(const GemmDesc *__restrict__ d, i
 // Column c: v = x - alpha e1 with alpha = -sign(x_0) |x|, stored below the
 // diagonal (v_0 kept in tau-scaled form), R on and above the diagonal; then
 // the thin Q (m x r) is formed in Qout by applying the reflectors backwards
-// to [I; 0].  One CTA (8 warps) per block; warp w updates columns w, w+8, ...
+// to [I; 0].  One CTA (32 warps) per block; warp w updates columns w, w+32, ...
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return __shfl_sync(0xffffffffu, v, 0);
 }
 
-__global__ void __launch_bounds__(256) k_house_qr(const QrDesc *__restrict__ d, int count) {
+constexpr int LA_THREADS = 1024, LA_WARPS = LA_THREADS / 32;
+
+__global__ void __launch_bounds__(LA_THREADS) k_house_qr(const QrDesc *__restrict__ d, int count) {
     const int pi = blockIdx.x;
     if (pi >= count) return;
     const QrDesc q = d[pi];
@@ -87,20 +89,20 @@ __global__ void __launch_bounds__(256) k_house_qr(const QrDesc *__restrict__ d, 
     const long long ld = q.ldy;
     const int m = q.m, r = q.r;
     double *tau = q.tau;   // r entries
-    __shared__ double red[8];
+    __shared__ double red[LA_WARPS];
     __shared__ double s_alpha, s_tau, s_v0;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     for (int c = 0; c < r; ++c) {
         double *x = Y + (long long)c * ld;
         // norm of x[c:m]
         double s = 0.0;
-        for (int i = c + threadIdx.x; i < m; i += 256) s += x[i] * x[i];
+        for (int i = c + threadIdx.x; i < m; i += LA_THREADS) s += x[i] * x[i];
         s = warp_sum(s);
         if (lane == 0) red[warp] = s;
         __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0.0;
-            for (int w = 0; w < 8; ++w) t += red[w];
+            for (int w = 0; w < LA_WARPS; ++w) t += red[w];
             const double nrm = sqrt(t);
             const double x0 = x[c];
             double alpha = (x0 >= 0.0) ? -nrm : nrm;
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(256) k_house_qr(const QrDesc *__restrict__ d, 
         __syncthreads();
         const double v0 = s_v0, tauc = s_tau;
         // apply to columns c+1 .. r-1: y -= tau (v'y) v
-        for (int j = c + 1 + warp; j < r; j += 8) {
+        for (int j = c + 1 + warp; j < r; j += LA_WARPS) {
             double *y = Y + (long long)j * ld;
             double dot = (lane == 0) ? v0 * y[c] : 0.0;
             for (int i = c + 1 + lane; i < m; i += 32) dot += x[i] * y[i];
@@ -141,13 +143,13 @@ __global__ void __launch_bounds__(256) k_house_qr(const QrDesc *__restrict__ d, 
     // thin Q: start from [I; 0] and apply H_c for c = r-1 .. 0
     double *Q = q.Q;
     const long long ldq = q.ldq;
-    for (int j = warp; j < r; j += 8)
+    for (int j = warp; j < r; j += LA_WARPS)
         for (int i = lane; i < m; i += 32) Q[(long long)j * ldq + i] = (i == j) ? 1.0 : 0.0;
     __syncthreads();
     for (int c = r - 1; c >= 0; --c) {
         const double *x = Y + (long long)c * ld;
         const double v0 = q.v0[c], tauc = tau[c];
-        for (int j = c + warp; j < r; j += 8) {
+        for (int j = c + warp; j < r; j += LA_WARPS) {
             double *y = Q + (long long)j * ldq;
             double dot = (lane == 0) ? v0 * y[c] : 0.0;
             for (int i = c + 1 + lane; i < m; i += 32) dot += x[i] * y[i];
@@ -161,11 +163,12 @@ __global__ void __launch_bounds__(256) k_house_qr(const QrDesc *__restrict__ d, 
 
 // ---- one-sided Jacobi SVD of an r x r block M (Hestenes) --------------------
 // Rotates column pairs of M (and accumulates V) until every pair is
-// orthogonal to relative 1e-15 or the sweep budget is spent; on exit the
+// orthogonal to relative 1e-13 or the sweep budget is spent (pairs whose
+// columns both have norms below `skip` are not rotated); on exit the
 // column norms of M are the singular values (unsorted), M = U S V' with
 // U = M_col / norm.  Pairs are processed in round-robin order, r/2 disjoint
 // pairs per round, one warp per pair.
-__global__ void __launch_bounds__(256) k_jacobi_svd(const SvdDesc *__restrict__ d, int count, int max_sweeps) {
+__global__ void __launch_bounds__(LA_THREADS) k_jacobi_svd(const SvdDesc *__restrict__ d, int count, int max_sweeps) {
     const int pi = blockIdx.x;
     if (pi >= count) return;
     const SvdDesc s = d[pi];
@@ -173,7 +176,7 @@ __global__ void __launch_bounds__(256) k_jacobi_svd(const SvdDesc *__restrict__ 
     double *M = s.M, *V = s.V;
     const long long ld = s.ld;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    for (int j = warp; j < r; j += 8)
+    for (int j = warp; j < r; j += LA_WARPS)
         for (int i = lane; i < r; i += 32) V[(long long)j * ld + i] = (i == j) ? 1.0 : 0.0;
     __shared__ int rotated;
     const int rr = r + (r & 1);   // round-robin over an even count (index r = dummy)
@@ -181,7 +184,7 @@ __global__ void __launch_bounds__(256) k_jacobi_svd(const SvdDesc *__restrict__ 
         if (threadIdx.x == 0) rotated = 0;
         __syncthreads();
         for (int round = 0; round < rr - 1; ++round) {
-            for (int pr = warp; pr < rr / 2; pr += 8) {
+            for (int pr = warp; pr < rr / 2; pr += LA_WARPS) {
                 // pairing of the circle method: position 0 fixed, others rotate
                 int a = (pr == 0) ? 0 : 1 + (pr - 1 + round) % (rr - 1);
                 int b = 1 + (rr - 2 - pr + round) % (rr - 1);
@@ -205,7 +208,7 @@ __global__ void __launch_bounds__(256) k_jacobi_svd(const SvdDesc *__restrict__ 
                 // both columns far below the truncation threshold: they are dropped anyway,
                 // and any combination of them stays below sqrt(r) * skip
                 if (al < s.skip * s.skip && be < s.skip * s.skip) continue;
-                if (fabs(ga) <= 1e-15 * sqrt(al * be) || ga == 0.0) continue;
+                if (fabs(ga) <= 1e-13 * sqrt(al * be) || ga == 0.0) continue;
                 const double zeta = (be - al) / (2.0 * ga);
                 const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                 const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
@@ -228,7 +231,7 @@ __global__ void __launch_bounds__(256) k_jacobi_svd(const SvdDesc *__restrict__ 
         __syncthreads();
     }
     // singular values = column norms
-    for (int j = warp; j < r; j += 8) {
+    for (int j = warp; j < r; j += LA_WARPS) {
         double t = 0.0;
         for (int i = lane; i < r; i += 32) t += M[(long long)j * ld + i] * M[(long long)j * ld + i];
         t = warp_sum(t);
@@ -267,14 +270,14 @@ cudaError_t launch_bgemm(const GemmDesc *d_desc, int count, int max_tiles, cudaS
 cudaError_t launch_house_qr(const QrDesc *d_desc, int count, cudaStream_t s, double flops) {
     if (count <= 0) return cudaSuccess;
     KScope ks(GEO_K_TLR, s, flops, 0.0);
-    k_house_qr<<<count, 256, 0, s>>>(d_desc, count);
+    k_house_qr<<<count, LA_THREADS, 0, s>>>(d_desc, count);
     return cudaGetLastError();
 }
 
 cudaError_t launch_jacobi_svd(const SvdDesc *d_desc, int count, int max_sweeps, cudaStream_t s, double flops) {
     if (count <= 0) return cudaSuccess;
     KScope ks(GEO_K_TLR, s, flops, 0.0);
-    k_jacobi_svd<<<count, 256, 0, s>>>(d_desc, count, max_sweeps);
+    k_jacobi_svd<<<count, LA_THREADS, 0, s>>>(d_desc, count, max_sweeps);
     return cudaGetLastError();
 }
 
