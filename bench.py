@@ -95,7 +95,7 @@ def workload(args):
     w = inputs.WORKLOADS[args.workload]
     if args.n:
         w = inputs.Workload(w.name + "-n%d" % args.n, args.n, w.theta, n_pred=w.n_pred, nb=w.nb,
-                            loc_seed=w.loc_seed, z_seed=w.z_seed)
+                            loc_seed=w.loc_seed, z_seed=w.z_seed, extra=dict(w.extra))
     if args.n_pred >= 0:
         w.n_pred = args.n_pred
     if args.nb:
