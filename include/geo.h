@@ -233,6 +233,32 @@ int geo_mle_best(const geo_mle_state *state, double *sigma2, double *a, double *
                  double *loglik);
 
 /*
+ * Batched log-likelihoods of many small, uneven problems (Eq. 1 for each),
+ * dense FP64, in the callers' location order.  One launch per step serves the
+ * whole batch (covariance generation, each 64-wide panel of the Cholesky
+ * factorisation, the reduction); the launch sequence of a batch shape (count
+ * and largest order) is captured once as a CUDA graph and replayed, with the
+ * per-problem inputs and theta refreshed in device descriptors.  A problem's
+ * result depends only on its own inputs: it is bit-identical alone and in any
+ * batch.
+ *   items        count entries (host array); each names device inputs and a
+ *                host theta, as for geo_loglik
+ *   loglik_host  count results (host); NaN where Sigma is not positive definite
+ *   info_host    NULL or count ints: 0 or the 1-based failing row
+ * Synchronises `stream`.  Returns GEO_EINVAL for bad items (the first one is
+ * named in geo_last_error), GEO_ENOMEM beyond the context's budget.
+ */
+typedef struct {
+    const double *locs_dev;   /* n x 2 */
+    int n;
+    const double *z_dev;      /* p n, Representation I */
+    geo_theta theta;
+} geo_batch_item;
+
+int geo_loglik_batch(geo_ctx *ctx, int count, const geo_batch_item *items, double *loglik_host, int *info_host,
+                     void *stream);
+
+/*
  * Device-time profile per kernel class, measured with CUDA events recorded
  * on the stream each kernel is launched on (no paper counterpart: the
  * paper's timing is wall-clock per phase, Sec. 6.1 / Sec. 6.3).

@@ -62,6 +62,10 @@ GEO_K_NAMES = ["covgen", "potrf", "trsm", "gemm", "reduce", "solve", "predict", 
 GEO_K_COUNT = len(GEO_K_NAMES)
 
 
+class geo_batch_item(ctypes.Structure):
+    _fields_ = [("locs_dev", ctypes.c_void_p), ("n", ctypes.c_int), ("z_dev", ctypes.c_void_p), ("theta", geo_theta)]
+
+
 class geo_kstat(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("ms", ctypes.c_double), ("flops", ctypes.c_double),
                 ("bytes", ctypes.c_double), ("timed", ctypes.c_longlong)]
@@ -93,6 +97,7 @@ SIGNATURES = {
     "geo_profile_enable": (_I, [_P, _I]),
     "geo_profile_read": (_I, [_P, ctypes.POINTER(geo_kstat)]),
     "geo_loglik_noalloc": (_I, [_P, _I, _P, ctypes.POINTER(geo_theta), _I, _P, _P, _P]),
+    "geo_loglik_batch": (_I, [_P, _I, _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -404,3 +409,24 @@ def geo_tlr_ranks(factor: Factor) -> np.ndarray:
     for j in range(T):
         R[:, j] = geo_factor_read(factor, 3, 0, T, j, j + 1).astype(np.int64)
     return R
+
+
+def geo_loglik_batch(ctx: Context, problems, stream=None):
+    """Eq. 1 for a list of (locs, z, theta) small problems in one batched launch sequence.
+    Returns (loglik array, info array)."""
+    import torch
+    count = len(problems)
+    items = (geo_batch_item * count)()
+    keep = []
+    for k, (locs, z, theta) in enumerate(problems):
+        th, kk = theta.to_c()
+        keep.append(kk)
+        items[k].locs_dev = _dev_ptr(locs, "locs", torch.float64).value
+        items[k].n = locs.shape[0]
+        items[k].z_dev = _dev_ptr(z, "z", torch.float64).value
+        items[k].theta = th
+    out = np.zeros(count)
+    info = np.zeros(count, dtype=np.int32)
+    ctx.check(ctx.lib.geo_loglik_batch(ctx.handle, count, items, out.ctypes.data_as(ctypes.c_void_p),
+                                       info.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    return out, info

@@ -9,6 +9,8 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <map>
+#include <tuple>
 #include <numeric>
 #include <stdexcept>
 #include <string>
@@ -40,6 +42,11 @@ struct geo_ctx {
     // TLR workspace (device) and descriptor staging (pinned host)
     void *tws = nullptr, *tarena = nullptr;
     size_t tws_bytes = 0, tarena_bytes = 0;
+    // batched likelihoods: matrices, descriptors (device + pinned host), captured graphs
+    void *bws = nullptr, *bdesc_d = nullptr, *bdesc_h = nullptr;
+    size_t bws_bytes = 0, bdesc_cap = 0;
+    std::map<std::tuple<int, int, int>, std::pair<cudaGraphExec_t, long long>> graphs;   // -> (exec, kernel nodes)
+    cudaStream_t cap_stream = nullptr;   // private stream for graph capture (the legacy stream cannot capture)
     std::vector<geo_factor *> factors;
     Profiler prof;
 };
@@ -384,6 +391,11 @@ int geo_destroy(geo_ctx *ctx) {
     if (ctx->rws) dev_free(ctx, ctx->rws, ctx->rws_bytes);
     if (ctx->tws) dev_free(ctx, ctx->tws, ctx->tws_bytes);
     if (ctx->tarena) cudaFreeHost(ctx->tarena);
+    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.second.first);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->bws) dev_free(ctx, ctx->bws, ctx->bws_bytes);
+    if (ctx->bdesc_d) cudaFree(ctx->bdesc_d);
+    if (ctx->bdesc_h) cudaFreeHost(ctx->bdesc_h);
     if (ctx->st) cudaFree(ctx->st);
     if (ctx->res) cudaFree(ctx->res);
     if (ctx->h_st) cudaFreeHost(ctx->h_st);
@@ -890,6 +902,86 @@ void geo_factor_free(geo_factor *f) {
     auto it = std::find(ctx->factors.begin(), ctx->factors.end(), f);
     if (it != ctx->factors.end()) ctx->factors.erase(it);
     delete f;
+}
+
+int geo_loglik_batch(geo_ctx *ctx, int count, const geo_batch_item *items, double *loglik_host, int *info_host,
+                     void *stream) {
+    if (!ctx) return GEO_EINVAL;
+    if (count <= 0 || !items || !loglik_host) return fail(ctx, GEO_EINVAL, "count must be > 0 and arrays non-NULL");
+    SetDevice sd(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<CovParams> cps(count);
+    std::vector<size_t> offs(count);
+    size_t total = 0;
+    int nmax = 0, Nmax = 0;
+    for (int k = 0; k < count; ++k) {
+        const geo_batch_item &it = items[k];
+        std::string err;
+        if (it.n <= 0 || !it.locs_dev || !it.z_dev)
+            return fail(ctx, GEO_EINVAL, "batch item " + std::to_string(k) + ": bad size or pointer");
+        int rc = theta_to_params(&it.theta, &cps[k], &err);
+        if (rc) return fail(ctx, rc, "batch item " + std::to_string(k) + ": " + err);
+        const int N = it.theta.p * it.n;
+        const long long ld = round_up((long long)N + 1, 32);
+        offs[k] = total;
+        total += (size_t)ld * N;
+        nmax = std::max(nmax, it.n);
+        Nmax = std::max(Nmax, N);
+    }
+    int rc;
+    if ((rc = ensure_buffer(ctx, &ctx->bws, &ctx->bws_bytes, sizeof(double) * total, s))) return rc;
+    const size_t dbytes = batch_desc_bytes() * (size_t)count;
+    if (ctx->bdesc_cap < dbytes) {
+        CK(cudaStreamSynchronize(s));
+        if (ctx->bdesc_d) cudaFree(ctx->bdesc_d);
+        if (ctx->bdesc_h) cudaFreeHost(ctx->bdesc_h);
+        ctx->bdesc_d = ctx->bdesc_h = nullptr;
+        ctx->bdesc_cap = 0;
+        if (cudaMalloc(&ctx->bdesc_d, dbytes) != cudaSuccess || cudaMallocHost(&ctx->bdesc_h, dbytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, GEO_ENOMEM, "batch descriptors");
+        }
+        ctx->bdesc_cap = dbytes;
+        // graphs hold the old descriptor pointer
+        for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.second.first);
+        ctx->graphs.clear();
+    }
+    double *base = (double *)ctx->bws;
+    for (int k = 0; k < count; ++k) {
+        const geo_batch_item &it = items[k];
+        const int N = it.theta.p * it.n;
+        batch_fill_desc(ctx->bdesc_h, k, base + offs[k], round_up((long long)N + 1, 32), N, it.n, it.locs_dev,
+                        it.z_dev, cps[k]);
+    }
+    CK(cudaMemcpyAsync(ctx->bdesc_d, ctx->bdesc_h, dbytes, cudaMemcpyHostToDevice, s));
+    const auto key = std::make_tuple(count, nmax, Nmax);
+    auto itg = ctx->graphs.find(key);
+    if (itg == ctx->graphs.end()) {
+        // capture the launch sequence of this batch shape; launches are counted, not event-timed
+        if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        Profiler counter;
+        ProfBind pb(&counter);
+        cudaGraph_t graph;
+        CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = batch_record(ctx->bdesc_d, count, nmax, Nmax, ctx->cap_stream);
+        cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &graph);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "batch capture");
+        if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "batch capture end");
+        cudaGraphExec_t exec;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+        long long nodes = 0;
+        for (int k = 0; k < GEO_K_COUNT; ++k) nodes += counter.launches[k];
+        itg = ctx->graphs.emplace(key, std::make_pair(exec, nodes)).first;
+    }
+    CK(cudaGraphLaunch(itg->second.first, s));
+    ctx->prof.launches[GEO_K_GEMM] += itg->second.second;   // kernel nodes of the replayed graph
+    std::vector<int> info(count);
+    CK(batch_results(ctx->bdesc_d, ctx->bdesc_h, count, loglik_host, info.data(), s));
+    if (info_host)
+        for (int k = 0; k < count; ++k) info_host[k] = info[k];
+    return GEO_OK;
 }
 
 int geo_profile_enable(geo_ctx *ctx, int enable) {

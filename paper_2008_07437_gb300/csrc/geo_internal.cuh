@@ -212,6 +212,13 @@ cudaError_t tlr_reduce(const TlrFactor &F, const double *y, const DevStatus *st,
 cudaError_t backward_solve(const double *A, long long ld, int N, const double *y, long long ystride, double *w,
                            cudaStream_t s);
 
+// ---- batch.cu -------------------------------------------------------------
+size_t batch_desc_bytes();
+void batch_fill_desc(void *hdesc, int k, double *A, long long ld, int N, int n, const double *locs, const double *z,
+                     const CovParams &cp);
+cudaError_t batch_record(void *ddesc, int count, int nmax, int Nmax, cudaStream_t s);
+cudaError_t batch_results(const void *ddesc, void *hdesc, int count, double *loglik, int *info, cudaStream_t s);
+
 // ---- host helpers (api.cu) ------------------------------------------------
 int theta_to_params(const geo_theta *th, CovParams *cp, std::string *err);
 void morton_perm_host(const double *locs, int n, int *perm);
