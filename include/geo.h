@@ -259,6 +259,63 @@ int geo_loglik_batch(geo_ctx *ctx, int count, const geo_batch_item *items, doubl
                      void *stream);
 
 /*
+ * Request server: likelihood and cokriging requests of different sizes on one
+ * GPU, admitted continuously (no paper counterpart: the paper evaluates one
+ * likelihood at a time).  `slots` worker threads each own a context and a
+ * CUDA stream, so concurrent requests overlap on the device.  A request
+ * reserves its estimated device footprint from the server's budget before it
+ * starts (0 = no budget) and returns it when it ends; a free worker takes the
+ * oldest queued request that fits.  A likelihood request with keep = 1 leaves
+ * its factor on the device under `dataset`; prediction requests for that key
+ * run on the worker that owns the factor, and one with release = 1 frees it.
+ * Inputs are host memory and are copied at submission.
+ */
+enum { GEO_REQ_LOGLIK = 0, GEO_REQ_PREDICT = 1 };
+
+typedef struct {
+    int kind;                      /* GEO_REQ_LOGLIK or GEO_REQ_PREDICT */
+    long long dataset;             /* key of a kept factor */
+    int keep;                      /* LOGLIK: keep the factor under `dataset` */
+    int release;                   /* PREDICT: free the factor after this request */
+    int n;                         /* LOGLIK: locations */
+    const double *locs_host;       /* LOGLIK: n x 2 */
+    const double *z_host;          /* LOGLIK: p n, Representation I */
+    geo_theta theta;               /* LOGLIK */
+    const geo_opts *opts;          /* LOGLIK: NULL = defaults */
+    int m;                         /* PREDICT: new locations */
+    const double *new_locs_host;   /* PREDICT: m x 2 */
+} geo_request;
+
+typedef struct {
+    long long id, dataset;
+    int kind, status;              /* status: GEO_OK or the error of the call */
+    double loglik;                 /* LOGLIK */
+    double t_submit, t_start, t_end;   /* seconds, steady clock */
+} geo_result;
+
+typedef struct geo_server geo_server;
+
+int geo_server_create(geo_server **server, int device, size_t hbm_budget_bytes, int slots);
+/* zhat_host: PREDICT output (p m doubles, host, caller-owned, valid until the result is polled) */
+int geo_server_submit(geo_server *server, const geo_request *request, double *zhat_host, long long *id);
+/* Up to max finished results; waits up to wait_ms for the first one. */
+int geo_server_poll(geo_server *server, geo_result *out, int max, int *nout, int wait_ms);
+int geo_server_pending(geo_server *server, int *queued, int *inflight, long long *reserved_bytes);
+/* Drops queued requests, waits for running ones, frees everything. */
+int geo_server_destroy(geo_server *server);
+
+/*
+ * Autotuner for the tile size: times geo_loglik (one warm-up, one timed run)
+ * on the caller's problem for each candidate nb and returns the fastest; the
+ * choice is cached in the context for problems of the same form and order
+ * bucket (powers of two of N), and geo_loglik with opts->nb = 0 uses it (or
+ * 960 when nothing is cached).
+ */
+int geo_autotune_nb(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev, const geo_theta *theta,
+                    const geo_opts *base, const int *candidates, int ncand, int *best_nb, double *best_ms,
+                    void *stream);
+
+/*
  * Device-time profile per kernel class, measured with CUDA events recorded
  * on the stream each kernel is launched on (no paper counterpart: the
  * paper's timing is wall-clock per phase, Sec. 6.1 / Sec. 6.3).

@@ -66,6 +66,22 @@ class geo_batch_item(ctypes.Structure):
     _fields_ = [("locs_dev", ctypes.c_void_p), ("n", ctypes.c_int), ("z_dev", ctypes.c_void_p), ("theta", geo_theta)]
 
 
+GEO_REQ_LOGLIK, GEO_REQ_PREDICT = 0, 1
+
+
+class geo_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("dataset", ctypes.c_longlong), ("keep", ctypes.c_int),
+                ("release", ctypes.c_int), ("n", ctypes.c_int), ("locs_host", ctypes.c_void_p),
+                ("z_host", ctypes.c_void_p), ("theta", geo_theta), ("opts", ctypes.c_void_p), ("m", ctypes.c_int),
+                ("new_locs_host", ctypes.c_void_p)]
+
+
+class geo_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("dataset", ctypes.c_longlong), ("kind", ctypes.c_int),
+                ("status", ctypes.c_int), ("loglik", ctypes.c_double), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_end", ctypes.c_double)]
+
+
 class geo_kstat(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("ms", ctypes.c_double), ("flops", ctypes.c_double),
                 ("bytes", ctypes.c_double), ("timed", ctypes.c_longlong)]
@@ -98,6 +114,13 @@ SIGNATURES = {
     "geo_profile_read": (_I, [_P, ctypes.POINTER(geo_kstat)]),
     "geo_loglik_noalloc": (_I, [_P, _I, _P, ctypes.POINTER(geo_theta), _I, _P, _P, _P]),
     "geo_loglik_batch": (_I, [_P, _I, _P, _P, _P, _P]),
+    "geo_server_create": (_I, [ctypes.POINTER(_P), _I, ctypes.c_size_t, _I]),
+    "geo_server_submit": (_I, [_P, _P, _P, ctypes.POINTER(_LL)]),
+    "geo_server_poll": (_I, [_P, _P, _I, ctypes.POINTER(_I), _I]),
+    "geo_server_pending": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_LL)]),
+    "geo_server_destroy": (_I, [_P]),
+    "geo_autotune_nb": (_I, [_P, _P, _I, _P, ctypes.POINTER(geo_theta), ctypes.POINTER(geo_opts), _P, _I,
+                             ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
 }
 
 _lib = None
@@ -430,3 +453,81 @@ def geo_loglik_batch(ctx: Context, problems, stream=None):
     ctx.check(ctx.lib.geo_loglik_batch(ctx.handle, count, items, out.ctypes.data_as(ctypes.c_void_p),
                                        info.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
     return out, info
+
+
+class Server:
+    """geo_server: continuous admission of likelihood / cokriging requests (host inputs, copied at submit)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, slots: int = 4):
+        self.lib = load_library()
+        h = ctypes.c_void_p()
+        rc = self.lib.geo_server_create(ctypes.byref(h), device, int(hbm_budget_bytes), int(slots))
+        if rc != GEO_OK:
+            raise GeoError(rc, "geo_server_create")
+        self.handle = h
+        self._keep = {}   # request id -> host buffers kept alive until the result is polled
+
+    def submit_loglik(self, locs, z, theta: Theta, options: geo_opts | None = None, dataset: int = 0,
+                      keep: bool = False) -> int:
+        locs = np.ascontiguousarray(locs, dtype=np.float64)
+        z = np.ascontiguousarray(z, dtype=np.float64)
+        th, kk = theta.to_c()
+        req = geo_request(GEO_REQ_LOGLIK, int(dataset), int(keep), 0, locs.shape[0], locs.ctypes.data, z.ctypes.data,
+                          th, ctypes.addressof(options) if options is not None else None, 0, None)
+        rid = ctypes.c_longlong()
+        rc = self.lib.geo_server_submit(self.handle, ctypes.byref(req), None, ctypes.byref(rid))
+        if rc != GEO_OK:
+            raise GeoError(rc, "geo_server_submit")
+        self._keep[rid.value] = (locs, z, kk, options)
+        return rid.value
+
+    def submit_predict(self, dataset: int, new_locs, p: int, release: bool = False):
+        new_locs = np.ascontiguousarray(new_locs, dtype=np.float64)
+        out = np.zeros(p * new_locs.shape[0])
+        req = geo_request(GEO_REQ_PREDICT, int(dataset), 0, int(release), 0, None, None, geo_theta(), None,
+                          new_locs.shape[0], new_locs.ctypes.data)
+        rid = ctypes.c_longlong()
+        rc = self.lib.geo_server_submit(self.handle, ctypes.byref(req), out.ctypes.data_as(ctypes.c_void_p),
+                                        ctypes.byref(rid))
+        if rc != GEO_OK:
+            raise GeoError(rc, "geo_server_submit")
+        self._keep[rid.value] = (new_locs, out)
+        return rid.value, out
+
+    def poll(self, max_results: int = 256, wait_ms: int = 0):
+        arr = (geo_result * max_results)()
+        n = ctypes.c_int()
+        rc = self.lib.geo_server_poll(self.handle, arr, max_results, ctypes.byref(n), int(wait_ms))
+        if rc != GEO_OK:
+            raise GeoError(rc, "geo_server_poll")
+        out = []
+        for k in range(n.value):
+            r = arr[k]
+            out.append(dict(id=r.id, dataset=r.dataset, kind=r.kind, status=r.status, loglik=r.loglik,
+                            t_submit=r.t_submit, t_start=r.t_start, t_end=r.t_end))
+            self._keep.pop(r.id, None)
+        return out
+
+    def pending(self):
+        q, f, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        self.lib.geo_server_pending(self.handle, ctypes.byref(q), ctypes.byref(f), ctypes.byref(b))
+        return q.value, f.value, b.value
+
+    def close(self):
+        if self.handle:
+            self.lib.geo_server_destroy(self.handle)
+            self.handle = None
+
+
+def geo_autotune_nb(ctx: Context, locs, z, theta: Theta, candidates, options: geo_opts | None = None, stream=None):
+    """Fastest tile size among ``candidates`` on this problem (cached in the context for nb = 0)."""
+    import torch
+    th, _keep = theta.to_c()
+    cand = (ctypes.c_int * len(candidates))(*candidates)
+    best = ctypes.c_int()
+    ms = ctypes.c_double()
+    ctx.check(ctx.lib.geo_autotune_nb(ctx.handle, _dev_ptr(locs, "locs", torch.float64), locs.shape[0],
+                                      _dev_ptr(z, "z", torch.float64), ctypes.byref(th),
+                                      ctypes.byref(options) if options is not None else None, cand, len(candidates),
+                                      ctypes.byref(best), ctypes.byref(ms), _stream(stream)))
+    return best.value, ms.value

@@ -47,6 +47,7 @@ struct geo_ctx {
     size_t bws_bytes = 0, bdesc_cap = 0;
     std::map<std::tuple<int, int, int>, std::pair<cudaGraphExec_t, long long>> graphs;   // -> (exec, kernel nodes)
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture (the legacy stream cannot capture)
+    std::map<std::pair<int, int>, int> tuned_nb;   // (form, log2 N bucket) -> tile size
     std::vector<geo_factor *> factors;
     Profiler prof;
 };
@@ -627,6 +628,14 @@ int geo_loglik(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev,
     else
         geo_opts_default(&o);
     if (n <= 0 || !locs_dev || !z_dev) return fail(ctx, GEO_EINVAL, "n must be > 0 and pointers non-NULL");
+    if (o.nb == 0 && theta) {
+        // tile size from the autotuner's cache for this form and order bucket
+        const int N = theta->p * n;
+        int b = 0;
+        while ((1 << (b + 1)) <= N) ++b;
+        auto it = ctx->tuned_nb.find({o.prec, b});
+        o.nb = (it != ctx->tuned_nb.end()) ? it->second : (o.prec == GEO_PREC_MIXED ? 1024 : 960);
+    }
     if (o.nb < 64) return fail(ctx, GEO_EINVAL, "nb must be >= 64");
     if (o.prec != GEO_PREC_FP64 && o.prec != GEO_PREC_MIXED && o.prec != GEO_PREC_TLR)
         return fail(ctx, GEO_EUNSUPPORTED, "precision mode not built");
@@ -981,6 +990,55 @@ int geo_loglik_batch(geo_ctx *ctx, int count, const geo_batch_item *items, doubl
     CK(batch_results(ctx->bdesc_d, ctx->bdesc_h, count, loglik_host, info.data(), s));
     if (info_host)
         for (int k = 0; k < count; ++k) info_host[k] = info[k];
+    return GEO_OK;
+}
+
+int geo_autotune_nb(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev, const geo_theta *theta,
+                    const geo_opts *base, const int *candidates, int ncand, int *best_nb, double *best_ms,
+                    void *stream) {
+    if (!ctx || !theta || !candidates || ncand <= 0) return GEO_EINVAL;
+    SetDevice sd(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    geo_opts o;
+    if (base)
+        o = *base;
+    else
+        geo_opts_default(&o);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int best = -1;
+    double bms = 1e300;
+    for (int c = 0; c < ncand; ++c) {
+        o.nb = candidates[c];
+        double ll;
+        int rc = geo_loglik(ctx, locs_dev, n, z_dev, theta, &o, &ll, nullptr, nullptr, stream);   // warm-up
+        if (rc == GEO_EINVAL || rc == GEO_EUNSUPPORTED) continue;   // candidate not valid for this form
+        if (rc != GEO_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return rc;
+        }
+        cudaEventRecord(e0, s);
+        rc = geo_loglik(ctx, locs_dev, n, z_dev, theta, &o, &ll, nullptr, nullptr, stream);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rc == GEO_OK && ms < bms) {
+            bms = ms;
+            best = candidates[c];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best < 0) return fail(ctx, GEO_EINVAL, "no valid tile-size candidate");
+    const int N = theta->p * n;
+    int b = 0;
+    while ((1 << (b + 1)) <= N) ++b;
+    ctx->tuned_nb[{o.prec, b}] = best;
+    if (best_nb) *best_nb = best;
+    if (best_ms) *best_ms = bms;
     return GEO_OK;
 }
 
