@@ -81,13 +81,20 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bivariate-n20000", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--workload", default="bivariate-n20000", choices=sorted(inputs.WORKLOADS) + ["serving"])
     ap.add_argument("--n", type=int, default=0, help="override n (profiling runs on small cases only)")
     ap.add_argument("--n-pred", type=int, default=-1)
     ap.add_argument("--nb", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=2000)
+    # serving workload
+    ap.add_argument("--requests", type=int, default=48, help="serving: requests in the stream")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrival rate (req/s)")
+    ap.add_argument("--slots", type=int, default=4, help="serving: worker threads")
+    ap.add_argument("--budget-gb", type=float, default=200.0, help="serving: device-memory budget (GiB)")
+    ap.add_argument("--serving-prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-tune", action="store_true", help="serving: skip the tile-size autotuner")
     return ap.parse_args()
 
 
@@ -403,8 +410,259 @@ def run_ours(args):
     return 0
 
 
+# --------------------------------------------------------------------------
+# serving: a Poisson stream of likelihood and cokriging requests
+# --------------------------------------------------------------------------
+SERVING_METRIC = "serving latency p50 (ms; p99 beside)"
+
+
+def serving_opts(geo, prec):
+    if prec == "fp64":
+        return geo.opts(nb=0), "dense FP64"
+    return (geo.opts(nb=0, prec=1, band=1 << 20, refine_iters=2),
+            "FP64 diagonal tiles, FP32 off-diagonal tiles (FP32 TRSM and updates), 2 FP64 refinement sweeps; "
+            "run again in FP64 when the reduced form is not positive definite")
+
+
+def serving_config(args, stream, form, tuned):
+    nl = [r.n for r in stream if r.kind == "loglik"]
+    return {"workload": "serving", "stream": "Poisson, mean %.0f req/s, seed 3000 + rank" % args.rate,
+            "requests": len(stream), "loglik_requests": len(nl),
+            "predict_requests": len(stream) - len(nl), "p": 2,
+            "n_range": [1000, 20000], "m_range": [100, 2000], "form": form, "slots": args.slots,
+            "hbm_budget_gib": args.budget_gb, "tuned_nb": tuned,
+            "theta_box": "a in [0.03, 0.2], nu_i in [0.5, 1.5], beta in [-0.7, 0.7], sigma^2_i in [0.5, 2]",
+            "z": "seeded standard normals (cost does not depend on Z)",
+            "l2": "inputs larger than L2: every likelihood generates its own %d-%d MB matrix" % (
+                8 * (2 * 1000) ** 2 // 2 ** 20, 8 * (2 * 20000) ** 2 // 2 ** 20)}
+
+
+def fifo_latencies(arrivals, service, servers=1):
+    """Latencies of a first-come first-served queue with identical servers."""
+    import heapq
+    free = [0.0] * servers
+    out = []
+    for a, sv in zip(arrivals, service):
+        t = heapq.heappop(free)
+        end = max(a, t) + sv
+        heapq.heappush(free, end)
+        out.append(end - a)
+    return out
+
+
+def serving_cpu_model(stream, n_s=1000, m_s=200):
+    """Oracle service time per request, from one timed oracle evaluation at
+    n_s locations (+ m_s predictions), extrapolated per request by N^3 / N^2 / n m."""
+    import oracle
+    w = inputs.Workload("serving-sample", n_s, inputs.THETA_FIG5, n_pred=m_s, nb=256, loc_seed=3999, z_seed=3998)
+    _, det = oracle_sample_run(w, n_s, m_s)
+    service = []
+    for r in stream:
+        if r.kind == "loglik":
+            q = r.n / n_s
+            service.append(det["covgen_s"] * q * q + det["cholesky_s"] * q ** 3 + det["solve_s"] * q * q)
+        else:
+            service.append(det["predict_s"] * (r.m / m_s))
+    return service, det, oracle.num_threads()
+
+
+def serving_cpu_json(stream, service, det, cores):
+    lat = fifo_latencies([r.t_arrival for r in stream], service, 1)
+    span = max(r.t_arrival + v for r, v in zip(stream, lat)) - stream[0].t_arrival
+    return {"value": float(np.percentile(lat, 50)) * 1e3, "unit": "ms", "cores": cores, "kind": "oracle",
+            "p99_ms": float(np.percentile(lat, 99)) * 1e3, "throughput_req_s": len(stream) / span,
+            "sample": ("oracle (C, OpenMP, FP64) timed once at n = %d (N = %d) + %d predictions in %.1f s; each "
+                       "request's service time extrapolated (N^3 Cholesky, N^2 generation and solve, m for "
+                       "cokriging on a kept factor), the stream replayed through a one-server FIFO queue"
+                       % (det["n_sample"], 2 * det["n_sample"], det["m_sample"], det["sample_s"]))}
+
+
+def run_serving(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2008_07437_gb300 as geo
+    from paper_2008_07437_gb300 import build as gbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0 or world == 1:
+        gbuild.build()
+    if world > 1:
+        dist.barrier()
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    stream = inputs.serving_stream(args.requests, rate=args.rate, seed=3000 + rank)
+    o, form = serving_opts(geo, args.serving_prec)
+    # host inputs, prepared before the timed region
+    prep = {}
+    for r in stream:
+        if r.kind == "loglik":
+            prep[r.k] = (r.locations(), r.observations(), geo.Theta.from_spec(r.theta))
+        else:
+            prep[r.k] = r.new_locations()
+
+    # tile sizes for the reduced form, one per order bucket of the stream (untimed)
+    tuned = {}
+    ctx = geo.geo_create(dev.index)
+    if args.serving_prec != "fp64" and not args.no_tune:
+        th_t = geo.Theta.from_spec(inputs.THETA_FIG5)
+        by_bucket = {}
+        for r in stream:
+            if r.kind == "loglik":
+                b = (2 * r.n).bit_length() - 1
+                if r.n > by_bucket.get(b, 0):
+                    by_bucket[b] = r.n
+        for b, n in sorted(by_bucket.items()):
+            locs = inputs.jittered_grid(n, 3997)
+            dl = torch.as_tensor(locs, device=dev)
+            dz = torch.as_tensor(inputs.normals(3996, 2 * n), device=dev)
+            cands = [c for c in (256, 512, 1024) if c <= 2 * n] or [256]
+            best, _ = geo.geo_autotune_nb(ctx, dl, dz, th_t, cands, o)
+            tuned["N>=%d" % (1 << b)] = best
+
+    srv = geo.Server(dev.index, int(args.budget_gb * 2 ** 30), args.slots)
+
+    def collect(want, timeout=3600.0):
+        got, t0 = {}, time.time()
+        while len(got) < len(want) and time.time() - t0 < timeout:
+            for x in srv.poll(256, wait_ms=100):
+                if x["id"] in want:
+                    got[x["id"]] = x
+        return got
+
+    # warm-up: small likelihoods on every worker
+    wids = {}
+    for i in range(max(args.warmup, 1) * args.slots):
+        wr = inputs.ServingRequest(10 ** 6 + i, 0.0, "loglik", n=1000, theta=inputs.THETA_FIG5)
+        wids[srv.submit_loglik(wr.locations(), wr.observations(), geo.Theta.from_spec(wr.theta), o,
+                               escalate=True)] = wr
+    collect(wids)
+    torch.cuda.synchronize()
+    launches0 = sum(v["launches"] for v in srv.profile().values())
+
+    # ---- timed region: the open-loop stream -------------------------------
+    clocks = ClockSampler(dev.index)
+    if world > 1:
+        dist.barrier()
+    clocks.start()
+    t0 = time.perf_counter()
+    ids = {}
+    for r in stream:
+        delay = t0 + r.t_arrival - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        if r.kind == "loglik":
+            locs, z, th = prep[r.k]
+            rid = srv.submit_loglik(locs, z, th, o, dataset=r.dataset, keep=r.keep, escalate=True)
+        else:
+            rid, _ = srv.submit_predict(r.dataset, prep[r.k], 2, release=r.release)
+        ids[rid] = r
+    res = collect(ids)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = sum(v["launches"] for v in srv.profile().values()) - launches0
+    srv.close()
+
+    rows = []
+    for rid, r in ids.items():
+        x = res.get(rid)
+        if x is None:
+            continue
+        rows.append((r, x))
+    lat = [x["t_end"] - x["t_submit"] for _, x in rows]
+    svc = [x["t_end"] - x["t_start"] for _, x in rows]
+    span = max(x["t_end"] for _, x in rows) - min(x["t_submit"] for _, x in rows)
+    n_ll = sum(1 for r, x in rows if r.kind == "loglik" and x["status"] == 0)
+    escalated = sum(1 for r, x in rows if r.kind == "loglik" and x["prec"] == 0 and args.serving_prec != "fp64")
+    failed = sum(1 for _, x in rows if x["status"] != 0)
+    lat_k = {k: [x["t_end"] - x["t_submit"] for r, x in rows if r.kind == k] for k in ("loglik", "predict")}
+    if world > 1:
+        allv = [None] * world
+        dist.all_gather_object(allv, {"lat": lat, "span": span, "n": len(rows), "n_ll": n_ll, "launches": launches})
+        lat = [v for a in allv for v in a["lat"]]
+        span = max(a["span"] for a in allv)
+        total, n_ll = sum(a["n"] for a in allv), sum(a["n_ll"] for a in allv)
+        launches = sum(a["launches"] for a in allv)
+    else:
+        total = len(rows)
+
+    # accuracy of the served reduced form: |dl| / |l| against FP64 on Z drawn
+    # from the model, at the theta and locations of the smallest served likelihoods
+    acc = None
+    if args.serving_prec != "fp64":
+        acc = []
+        small = sorted((r for r, x in rows if r.kind == "loglik" and x["prec"] == 1), key=lambda r: r.n)[:3]
+        for r in small:
+            locs, _, th = prep[r.k]
+            dl = torch.as_tensor(locs, device=dev)
+            de = torch.as_tensor(inputs.normals(45000 + r.k, 2 * r.n), device=dev)
+            dz = torch.empty(2 * r.n, dtype=torch.float64, device=dev)
+            geo.geo_simulate(ctx, dl, de, th, dz, geo.opts(nb=0))
+            l64, _ = geo.geo_loglik(ctx, dl, dz, th, geo.opts(nb=0))
+            try:
+                lmx, _ = geo.geo_loglik(ctx, dl, dz, th, o)
+                acc.append({"n": r.n, "rel": abs(lmx - l64) / abs(l64)})
+            except geo.GeoError as e:
+                acc.append({"n": r.n, "rel": None, "status": e.code})
+    ctx.close()
+
+    p50, p99 = float(np.percentile(lat, 50)) * 1e3, float(np.percentile(lat, 99)) * 1e3
+    h2d = sum(32 * r.n if r.kind == "loglik" else 16 * r.m for r in stream) / len(stream)
+    d2h = sum(16 * r.m if r.kind == "predict" else 8 for r in stream) / len(stream)
+    out = {"metric": SERVING_METRIC, "value": p50, "unit": "ms", "n_gpus": world, "steps": total,
+           "warmup": max(args.warmup, 1) * args.slots, "ms_per_step": span * 1e3 / max(total, 1),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64+f32" if args.serving_prec != "fp64" else "f64", "data": "synthetic",
+           "config": serving_config(args, stream, form, tuned),
+           "p50_ms": p50, "p99_ms": p99,
+           "p50_ms_by_kind": {k: float(np.percentile(v, 50)) * 1e3 for k, v in lat_k.items() if v},
+           "p99_ms_by_kind": {k: float(np.percentile(v, 99)) * 1e3 for k, v in lat_k.items() if v},
+           "service_p50_ms": float(np.percentile(svc, 50)) * 1e3, "service_p99_ms": float(np.percentile(svc, 99)) * 1e3,
+           "throughput_req_s": total / span, "loglik_evals_s": n_ll / span, "offered_req_s": args.rate * world,
+           "makespan_s": span, "escalated_to_fp64": escalated, "failed": failed,
+           "accuracy_vs_fp64": acc, "gpu_launches": launches, "clocks": clk,
+           "roofline": None,
+           "e2e": {"value": p50, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                   "note": "the served latency is already end to end: host inputs, copies and the result read"}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        service, det, cores = serving_cpu_model(stream)
+        out["cpu_baseline"] = serving_cpu_json(stream, service, det, cores)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_serving_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    stream = inputs.serving_stream(args.requests, rate=args.rate, seed=3000)
+    service, det, cores = serving_cpu_model(stream)
+    cb = serving_cpu_json(stream, service, det, cores)
+    line = {"impl": "reference", "metric": SERVING_METRIC, "value": cb["value"], "unit": "ms", "n_gpus": args.gpus,
+            "steps": len(stream), "warmup": 0, "ms_per_step": sum(service) * 1e3 / len(stream),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": serving_config(args, stream, "oracle FP64 (extrapolated)", {}),
+            "p50_ms": cb["value"], "p99_ms": cb["p99_ms"], "throughput_req_s": cb["throughput_req_s"],
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "serving":
+        return run_serving_reference(args) if args.impl == "reference" else run_serving(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -262,13 +262,25 @@ int geo_loglik_batch(geo_ctx *ctx, int count, const geo_batch_item *items, doubl
  * Request server: likelihood and cokriging requests of different sizes on one
  * GPU, admitted continuously (no paper counterpart: the paper evaluates one
  * likelihood at a time).  `slots` worker threads each own a context and a
- * CUDA stream, so concurrent requests overlap on the device.  A request
- * reserves its estimated device footprint from the server's budget before it
- * starts (0 = no budget) and returns it when it ends; a free worker takes the
- * oldest queued request that fits.  A likelihood request with keep = 1 leaves
- * its factor on the device under `dataset`; prediction requests for that key
- * run on the worker that owns the factor, and one with release = 1 frees it.
- * Inputs are host memory and are copied at submission.
+ * CUDA stream, so concurrent requests overlap on the device.
+ * Admission by device memory (hbm_budget_bytes, 0 = no budget): each worker's
+ * footprint is what its context holds (cached workspaces, kept factors) plus
+ * its staging buffers, and while it runs a request, plus an upper bound of
+ * what the request may allocate.  A free worker takes the oldest queued
+ * request for which the sum of the footprints stays within the budget,
+ * dropping its own cached workspaces first if that makes it fit; idle workers
+ * drop theirs while a request waits for memory.  A likelihood request whose
+ * bound alone exceeds the budget is refused at submission with GEO_ENOMEM.
+ * A likelihood request with keep = 1 leaves its factor on the device under
+ * `dataset`; prediction requests for that key run on the worker that owns
+ * the factor (after the likelihood has finished), and one with release = 1
+ * frees it.  If that likelihood failed, its predictions finish with
+ * GEO_EINVAL.  With escalate = 1, a mixed-precision or TLR likelihood that
+ * finds its reduced-precision Sigma not positive definite is run again in
+ * FP64 on the same worker; geo_result.prec gives the form that produced the
+ * result.  Inputs are host memory and are copied at submission.
+ * geo_server_pending reports the queued and running requests and the summed
+ * footprint in bytes.
  */
 enum { GEO_REQ_LOGLIK = 0, GEO_REQ_PREDICT = 1 };
 
@@ -284,6 +296,7 @@ typedef struct {
     const geo_opts *opts;          /* LOGLIK: NULL = defaults */
     int m;                         /* PREDICT: new locations */
     const double *new_locs_host;   /* PREDICT: m x 2 */
+    int escalate;                  /* LOGLIK: on GEO_ENOTSPD in a reduced form, run again in FP64 */
 } geo_request;
 
 typedef struct {
@@ -291,6 +304,7 @@ typedef struct {
     int kind, status;              /* status: GEO_OK or the error of the call */
     double loglik;                 /* LOGLIK */
     double t_submit, t_start, t_end;   /* seconds, steady clock */
+    int prec;                      /* LOGLIK: GEO_PREC_* of the evaluation that produced the result */
 } geo_result;
 
 typedef struct geo_server geo_server;
@@ -307,9 +321,9 @@ int geo_server_destroy(geo_server *server);
 /*
  * Autotuner for the tile size: times geo_loglik (one warm-up, one timed run)
  * on the caller's problem for each candidate nb and returns the fastest; the
- * choice is cached in the context for problems of the same form and order
- * bucket (powers of two of N), and geo_loglik with opts->nb = 0 uses it (or
- * 960 when nothing is cached).
+ * choice is cached for the whole process, per device, form and order bucket
+ * (powers of two of N), and geo_loglik with opts->nb = 0 on any context of
+ * that device uses it (or 960 FP64 / 1024 mixed when nothing is cached).
  */
 int geo_autotune_nb(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev, const geo_theta *theta,
                     const geo_opts *base, const int *candidates, int ncand, int *best_nb, double *best_ms,
@@ -349,6 +363,10 @@ typedef struct {
 
 int geo_profile_enable(geo_ctx *ctx, int enable);
 int geo_profile_read(geo_ctx *ctx, geo_kstat *out);
+/* Kernel counters summed over a server's worker contexts (launch counts
+ * always; times only where profiling was on).  out: GEO_K_COUNT entries.
+ * GEO_EINVAL while requests are queued or running. */
+int geo_server_profile_read(geo_server *server, geo_kstat *out);
 
 /*
  * geo_loglik_noalloc -- the log-likelihood of geo_loglik for small problems,

@@ -73,13 +73,13 @@ class geo_request(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("dataset", ctypes.c_longlong), ("keep", ctypes.c_int),
                 ("release", ctypes.c_int), ("n", ctypes.c_int), ("locs_host", ctypes.c_void_p),
                 ("z_host", ctypes.c_void_p), ("theta", geo_theta), ("opts", ctypes.c_void_p), ("m", ctypes.c_int),
-                ("new_locs_host", ctypes.c_void_p)]
+                ("new_locs_host", ctypes.c_void_p), ("escalate", ctypes.c_int)]
 
 
 class geo_result(ctypes.Structure):
     _fields_ = [("id", ctypes.c_longlong), ("dataset", ctypes.c_longlong), ("kind", ctypes.c_int),
                 ("status", ctypes.c_int), ("loglik", ctypes.c_double), ("t_submit", ctypes.c_double),
-                ("t_start", ctypes.c_double), ("t_end", ctypes.c_double)]
+                ("t_start", ctypes.c_double), ("t_end", ctypes.c_double), ("prec", ctypes.c_int)]
 
 
 class geo_kstat(ctypes.Structure):
@@ -112,6 +112,7 @@ SIGNATURES = {
     "geo_mle_best": (_I, [ctypes.POINTER(geo_mle_state), _P, _P, _P, _P, _P]),
     "geo_profile_enable": (_I, [_P, _I]),
     "geo_profile_read": (_I, [_P, ctypes.POINTER(geo_kstat)]),
+    "geo_server_profile_read": (_I, [_P, ctypes.POINTER(geo_kstat)]),
     "geo_loglik_noalloc": (_I, [_P, _I, _P, ctypes.POINTER(geo_theta), _I, _P, _P, _P]),
     "geo_loglik_batch": (_I, [_P, _I, _P, _P, _P, _P]),
     "geo_server_create": (_I, [ctypes.POINTER(_P), _I, ctypes.c_size_t, _I]),
@@ -468,12 +469,12 @@ class Server:
         self._keep = {}   # request id -> host buffers kept alive until the result is polled
 
     def submit_loglik(self, locs, z, theta: Theta, options: geo_opts | None = None, dataset: int = 0,
-                      keep: bool = False) -> int:
+                      keep: bool = False, escalate: bool = False) -> int:
         locs = np.ascontiguousarray(locs, dtype=np.float64)
         z = np.ascontiguousarray(z, dtype=np.float64)
         th, kk = theta.to_c()
         req = geo_request(GEO_REQ_LOGLIK, int(dataset), int(keep), 0, locs.shape[0], locs.ctypes.data, z.ctypes.data,
-                          th, ctypes.addressof(options) if options is not None else None, 0, None)
+                          th, ctypes.addressof(options) if options is not None else None, 0, None, int(escalate))
         rid = ctypes.c_longlong()
         rc = self.lib.geo_server_submit(self.handle, ctypes.byref(req), None, ctypes.byref(rid))
         if rc != GEO_OK:
@@ -485,7 +486,7 @@ class Server:
         new_locs = np.ascontiguousarray(new_locs, dtype=np.float64)
         out = np.zeros(p * new_locs.shape[0])
         req = geo_request(GEO_REQ_PREDICT, int(dataset), 0, int(release), 0, None, None, geo_theta(), None,
-                          new_locs.shape[0], new_locs.ctypes.data)
+                          new_locs.shape[0], new_locs.ctypes.data, 0)
         rid = ctypes.c_longlong()
         rc = self.lib.geo_server_submit(self.handle, ctypes.byref(req), out.ctypes.data_as(ctypes.c_void_p),
                                         ctypes.byref(rid))
@@ -504,7 +505,7 @@ class Server:
         for k in range(n.value):
             r = arr[k]
             out.append(dict(id=r.id, dataset=r.dataset, kind=r.kind, status=r.status, loglik=r.loglik,
-                            t_submit=r.t_submit, t_start=r.t_start, t_end=r.t_end))
+                            t_submit=r.t_submit, t_start=r.t_start, t_end=r.t_end, prec=r.prec))
             self._keep.pop(r.id, None)
         return out
 
@@ -512,6 +513,15 @@ class Server:
         q, f, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
         self.lib.geo_server_pending(self.handle, ctypes.byref(q), ctypes.byref(f), ctypes.byref(b))
         return q.value, f.value, b.value
+
+    def profile(self) -> dict:
+        """Kernel counters summed over the workers (call when nothing is queued or running)."""
+        arr = (geo_kstat * GEO_K_COUNT)()
+        rc = self.lib.geo_server_profile_read(self.handle, arr)
+        if rc != GEO_OK:
+            raise GeoError(rc, "geo_server_profile_read")
+        return {GEO_K_NAMES[k]: dict(launches=arr[k].launches, ms=arr[k].ms, flops=arr[k].flops,
+                                     bytes=arr[k].bytes) for k in range(GEO_K_COUNT)}
 
     def close(self):
         if self.handle:

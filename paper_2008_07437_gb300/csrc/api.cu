@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <map>
+#include <mutex>
 #include <tuple>
 #include <numeric>
 #include <stdexcept>
@@ -47,7 +48,6 @@ struct geo_ctx {
     size_t bws_bytes = 0, bdesc_cap = 0;
     std::map<std::tuple<int, int, int>, std::pair<cudaGraphExec_t, long long>> graphs;   // -> (exec, kernel nodes)
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture (the legacy stream cannot capture)
-    std::map<std::pair<int, int>, int> tuned_nb;   // (form, log2 N bucket) -> tile size
     std::vector<geo_factor *> factors;
     Profiler prof;
 };
@@ -177,6 +177,24 @@ struct SetDevice {
 };
 
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+// Tile sizes picked by geo_autotune_nb, shared by every context of the
+// process: (device, form, floor(log2 N)) -> nb.
+std::mutex g_tuned_mu;
+std::map<std::tuple<int, int, int>, int> g_tuned_nb;
+
+int order_bucket(int N) {
+    int b = 0;
+    while ((1 << (b + 1)) <= N) ++b;
+    return b;
+}
+
+int resolve_nb(int device, int prec, int N) {
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    auto it = g_tuned_nb.find(std::make_tuple(device, prec, order_bucket(N)));
+    if (it != g_tuned_nb.end()) return it->second;
+    return prec == GEO_PREC_MIXED ? 1024 : 960;
+}
 
 // Grow a context-cached device buffer to at least `need` bytes.
 int ensure_buffer(geo_ctx *ctx, void **buf, size_t *have, size_t need, cudaStream_t s) {
@@ -628,14 +646,7 @@ int geo_loglik(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev,
     else
         geo_opts_default(&o);
     if (n <= 0 || !locs_dev || !z_dev) return fail(ctx, GEO_EINVAL, "n must be > 0 and pointers non-NULL");
-    if (o.nb == 0 && theta) {
-        // tile size from the autotuner's cache for this form and order bucket
-        const int N = theta->p * n;
-        int b = 0;
-        while ((1 << (b + 1)) <= N) ++b;
-        auto it = ctx->tuned_nb.find({o.prec, b});
-        o.nb = (it != ctx->tuned_nb.end()) ? it->second : (o.prec == GEO_PREC_MIXED ? 1024 : 960);
-    }
+    if (o.nb == 0 && theta) o.nb = resolve_nb(ctx->device, o.prec, theta->p * n);
     if (o.nb < 64) return fail(ctx, GEO_EINVAL, "nb must be >= 64");
     if (o.prec != GEO_PREC_FP64 && o.prec != GEO_PREC_MIXED && o.prec != GEO_PREC_TLR)
         return fail(ctx, GEO_EUNSUPPORTED, "precision mode not built");
@@ -1033,10 +1044,10 @@ int geo_autotune_nb(geo_ctx *ctx, const double *locs_dev, int n, const double *z
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (best < 0) return fail(ctx, GEO_EINVAL, "no valid tile-size candidate");
-    const int N = theta->p * n;
-    int b = 0;
-    while ((1 << (b + 1)) <= N) ++b;
-    ctx->tuned_nb[{o.prec, b}] = best;
+    {
+        std::lock_guard<std::mutex> lk(g_tuned_mu);
+        g_tuned_nb[std::make_tuple(ctx->device, o.prec, order_bucket(theta->p * n))] = best;
+    }
     if (best_nb) *best_nb = best;
     if (best_ms) *best_ms = bms;
     return GEO_OK;
@@ -1075,3 +1086,53 @@ int geo_morton_order(const double *locs_host, int n, int *perm_host) {
 }
 
 }  // extern "C"
+
+// ---- for the request server (serve.cu) --------------------------------------
+
+size_t ctx_device_bytes(const geo_ctx *ctx) { return ctx ? ctx->used : 0; }
+
+size_t ctx_trim(geo_ctx *ctx, cudaStream_t s) {
+    if (!ctx) return 0;
+    SetDevice sd(ctx->device);
+    cudaStreamSynchronize(s);
+    const size_t before = ctx->used;
+    void **bufs[] = {(void **)&ctx->ws, &ctx->mws, &ctx->sws, &ctx->zws, &ctx->rws, &ctx->tws, &ctx->bws};
+    size_t *sizes[] = {&ctx->ws_bytes, &ctx->mws_bytes, &ctx->sws_bytes, &ctx->zws_bytes,
+                       &ctx->rws_bytes, &ctx->tws_bytes, &ctx->bws_bytes};
+    for (int k = 0; k < 7; ++k) {
+        dev_free(ctx, *bufs[k], *sizes[k]);
+        *bufs[k] = nullptr;
+        *sizes[k] = 0;
+    }
+    // batch graphs refer to the freed batch workspace
+    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.second.first);
+    ctx->graphs.clear();
+    return before - ctx->used;
+}
+
+size_t loglik_device_bytes(int device, int n, int p, const geo_opts *opts) {
+    geo_opts o;
+    if (opts)
+        o = *opts;
+    else
+        geo_opts_default(&o);
+    const size_t N = (size_t)p * n;
+    if (o.nb == 0) o.nb = resolve_nb(device, o.prec, (int)N);
+    const size_t nb = (size_t)std::max(o.nb, 64);
+    size_t b = sizeof(double) * 2 * n + sizeof(int) * 2 * n + sizeof(double) * N;   // locations, perms, w
+    if (o.prec == GEO_PREC_TLR) {
+        const int kmax = std::min(o.tlr_kmax, (int)nb);
+        const size_t T = (N + nb - 1) / nb;
+        b += tlr_factor_bytes((int)N, (int)nb, kmax) + sizeof(double) * N;
+        b += std::max(tlr_workspace_bytes((int)N, (int)nb, kmax), tlr_solve_workspace_bytes((int)N, (int)nb, kmax));
+        b += sizeof(double) * (T * (T - 1) / 2) * 2 * nb * nb;   // U / V pool if every tile fell back to dense
+        return b + ((size_t)1 << 24);
+    }
+    const size_t ld = (size_t)round_up((long long)N + 1, 32);
+    b += sizeof(double) * ld * N;
+    if (o.prec == GEO_PREC_MIXED) {
+        b += mixed_workspace_bytes((int)N, (int)nb);
+        if (o.refine_iters > 0) b += sizeof(double) * ld * N + sizeof(double) * N + refine_workspace_bytes((int)N);
+    }
+    return b;
+}

@@ -101,6 +101,15 @@ cudaError_t chol_mixed_factor(double *A, long long ld, int N, int nrows, int nb,
                               size_t ws_bytes, DevStatus *st, cudaStream_t s);
 
 
+// ---- api.cu (for the request server) ---------------------------------------
+// Device bytes a context holds (cached workspaces and kept factors).
+size_t ctx_device_bytes(const geo_ctx *ctx);
+// Free the context's cached workspaces (after synchronising s); kept factors stay.
+size_t ctx_trim(geo_ctx *ctx, cudaStream_t s);
+// Upper bound of the device bytes one geo_loglik call with these options may
+// add to a context that holds no cached workspace.
+size_t loglik_device_bytes(int device, int n, int p, const geo_opts *opts);
+
 // ---- solve.cu -----------------------------------------------------------
 // logdet = 2 sum log L_kk, quad = sum y_k^2 (y = row N of A), loglik = Eq. 1.
 cudaError_t launch_loglik_reduce(const double *A, long long ld, int N, const double *y, long long ystride,

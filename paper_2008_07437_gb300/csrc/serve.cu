@@ -3,10 +3,14 @@
 //
 // * `slots` worker threads, each with its own context and CUDA stream, so the
 //   kernels of concurrent requests overlap on the device.
-// * Admission by device memory: a request reserves its estimated footprint
-//   (matrix, workspaces) from the server's budget before it starts and gives
-//   it back when it ends; a free worker takes the oldest queued request that
-//   fits (later, smaller requests may start while a large one waits).
+// * Admission by device memory.  Every worker publishes its footprint: idle,
+//   the bytes its context holds (cached workspaces and kept factors) plus its
+//   staging buffers; running, that plus an upper bound of what the request
+//   may allocate.  A free worker takes the oldest queued request for which the
+//   sum of footprints stays within the budget, dropping its own cached
+//   workspaces first when that is what makes the request fit; when a request
+//   cannot be admitted, idle workers drop theirs.  Later, smaller requests may
+//   start while a large one waits.
 // * A likelihood request may keep its factor on the device under a dataset
 //   key; cokriging requests for that key run on the worker that owns the
 //   factor (affinity), reuse it, and the last one may release it.
@@ -34,14 +38,14 @@ double now_s() {
 
 struct Req {
     long long id;
-    int kind, keep, release;
+    int kind, keep, release, escalate;
     long long dataset;
     int n, m, p;
     std::vector<double> locs, z, new_locs, sigma2, nu, beta;
     double a;
     geo_opts opts;
     double *zhat_out;   // caller's host buffer (PREDICT)
-    size_t bytes;       // reserved device bytes
+    size_t bytes;       // upper bound of the device bytes the request may add
     int affinity;       // worker index, or -1
     double t_submit;
 };
@@ -59,10 +63,10 @@ struct geo_server {
     std::vector<geo_result> done;
     std::vector<Worker *> workers;
     std::map<long long, std::pair<int, geo_factor *>> factors;   // dataset -> (worker, factor)
-    std::map<long long, size_t> factor_bytes;
     std::atomic<long long> next_id{1};
     int inflight = 0;
     bool stop = false;
+    bool starved = false;   // a queued request did not fit: idle workers drop their caches
 };
 
 namespace {
@@ -75,15 +79,22 @@ struct Worker {
     std::thread th;
     double *d_locs = nullptr, *d_z = nullptr, *d_new = nullptr, *d_zhat = nullptr;
     size_t cap_locs = 0, cap_z = 0, cap_new = 0, cap_zhat = 0;
+    // published under the server lock
+    size_t foot = 0;     // device bytes held now (running: plus the request's bound)
+    size_t kept = 0;     // bytes of the factors kept in this worker's context
+    bool busy = false;
 };
 
-size_t estimate_bytes(const Req &r) {
-    if (r.kind == GEO_REQ_PREDICT) return sizeof(double) * (size_t)(3 * r.m * r.p + r.n * r.p) + (1u << 20);
+size_t staging_bytes(const Worker *w) { return sizeof(double) * (w->cap_locs + w->cap_z + w->cap_new + w->cap_zhat); }
+
+// Upper bound of the device bytes a request adds to its worker (staging
+// buffers included).  Predictions: the weight vector w = Sigma^-1 Z (computed
+// once per factor) and the new locations and predictions.
+size_t request_bytes(const geo_server *S, const Req &r, int N_factor) {
+    if (r.kind == GEO_REQ_PREDICT)
+        return sizeof(double) * ((size_t)N_factor + 2 * (size_t)r.m + (size_t)GEO_PMAX * r.m) + 4096;
     const size_t N = (size_t)r.p * r.n;
-    const size_t ld = (N + 1 + 31) / 32 * 32;
-    size_t b = sizeof(double) * ld * N + sizeof(double) * 4 * N + (8u << 20);
-    if (r.opts.prec == GEO_PREC_MIXED) b += sizeof(double) * ld * N / 2 + (size_t)N * r.opts.nb * 10;
-    return b;
+    return loglik_device_bytes(S->device, r.n, r.p, &r.opts) + sizeof(double) * (2 * (size_t)r.n + N);
 }
 
 bool grow(double **p, size_t *cap, size_t n) {
@@ -118,13 +129,31 @@ void run_request(Worker *w, Req *r, geo_result *res) {
         geo_factor *f = nullptr;
         double ll = 0.0;
         int info = 0;
+        res->prec = r->opts.prec;
         res->status = geo_loglik(w->ctx, w->d_locs, r->n, w->d_z, &th, &r->opts, &ll, r->keep ? &f : nullptr, &info,
                                  w->stream);
+        if (res->status == GEO_ENOTSPD && r->escalate && r->opts.prec != GEO_PREC_FP64) {
+            // the reduced form lost positive definiteness: the FP64 form decides
+            geo_opts o64;
+            geo_opts_default(&o64);
+            o64.nb = 0;
+            o64.morton = r->opts.morton;
+            res->prec = GEO_PREC_FP64;
+            res->status = geo_loglik(w->ctx, w->d_locs, r->n, w->d_z, &th, &o64, &ll, r->keep ? &f : nullptr, &info,
+                                     w->stream);
+        }
         res->loglik = ll;
         if (r->keep) {
             // a failed likelihood leaves a null factor: its predictions complete with an error
+            size_t fb = 0;
+            if (res->status == GEO_OK && f) {
+                geo_factor_stats st;
+                geo_factor_stats_get(f, &st);
+                fb = (size_t)st.device_bytes;
+            }
             std::lock_guard<std::mutex> lk(S->mu);
             S->factors[r->dataset] = {w->index, (res->status == GEO_OK) ? f : nullptr};
+            w->kept += fb;
         }
     } else {
         geo_factor *f = nullptr;
@@ -154,16 +183,29 @@ void run_request(Worker *w, Req *r, geo_result *res) {
             cudaMemcpyAsync(r->zhat_out, w->d_zhat, sizeof(double) * pm, cudaMemcpyDeviceToHost, w->stream);
         cudaStreamSynchronize(w->stream);
         if (r->release) {
-            std::lock_guard<std::mutex> lk(S->mu);
-            S->factors.erase(r->dataset);
-            auto fb = S->factor_bytes.find(r->dataset);
-            if (fb != S->factor_bytes.end()) {
-                S->reserved -= fb->second;
-                S->factor_bytes.erase(fb);
+            geo_factor_stats st;
+            geo_factor_stats_get(f, &st);
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->factors.erase(r->dataset);
+                w->kept -= std::min(w->kept, (size_t)st.device_bytes);
             }
             geo_factor_free(f);
         }
     }
+}
+
+// Publish the worker's idle footprint (called with the lock held).
+void publish_idle(Worker *w) {
+    w->foot = ctx_device_bytes(w->ctx) + staging_bytes(w);
+    w->busy = false;
+}
+
+void trim_unlocked(Worker *w, std::unique_lock<std::mutex> &lk) {
+    lk.unlock();
+    ctx_trim(w->ctx, w->stream);
+    lk.lock();
+    publish_idle(w);
 }
 
 void worker_loop(Worker *w) {
@@ -171,31 +213,61 @@ void worker_loop(Worker *w) {
     cudaSetDevice(S->device);
     for (;;) {
         Req *r = nullptr;
+        bool trim_first = false;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             for (;;) {
                 if (S->stop && S->queue.empty()) return;
+                size_t others = 0;
+                for (Worker *v : S->workers)
+                    if (v != w) others += v->foot;
+                const size_t cached = w->foot - std::min(w->foot, w->kept + staging_bytes(w));
                 // the oldest request that is routed here (or anywhere) and fits in the budget
                 for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
                     Req *q = *it;
                     if (q->affinity >= 0 && q->affinity != w->index) continue;
-                    if (q->kind == GEO_REQ_PREDICT && q->affinity < 0) {
+                    int Nf = 0;
+                    if (q->kind == GEO_REQ_PREDICT) {
                         auto f = S->factors.find(q->dataset);
                         if (f == S->factors.end()) continue;   // its factor is not ready yet
                         q->affinity = f->second.first;
                         if (q->affinity != w->index) continue;
+                        if (f->second.second) {
+                            geo_factor_stats st;
+                            geo_factor_stats_get(f->second.second, &st);
+                            Nf = st.N;
+                        }
+                        q->bytes = request_bytes(S, *q, Nf);
                     }
-                    if (S->budget && S->reserved + q->bytes > S->budget) continue;
+                    if (S->budget) {
+                        if (others + w->foot + q->bytes > S->budget) {
+                            if (others + (w->foot - cached) + q->bytes > S->budget) {
+                                S->starved = true;
+                                continue;
+                            }
+                            trim_first = true;
+                        }
+                    }
                     r = q;
                     S->queue.erase(it);
-                    S->reserved += r->bytes;
+                    w->foot += q->bytes;
+                    w->busy = true;
+                    S->reserved = others + w->foot;
                     S->inflight += 1;
                     break;
                 }
                 if (r) break;
+                if (S->starved && cached > 0) {
+                    // another request waits for memory: give back this idle worker's cache
+                    trim_unlocked(w, lk);
+                    S->starved = false;
+                    S->cv_work.notify_all();
+                    continue;
+                }
                 S->cv_work.wait_for(lk, std::chrono::milliseconds(5));
             }
         }
+        if (trim_first) ctx_trim(w->ctx, w->stream);
         geo_result res;
         memset(&res, 0, sizeof(res));
         res.t_submit = r->t_submit;
@@ -203,14 +275,15 @@ void worker_loop(Worker *w) {
         run_request(w, r, &res);
         res.t_end = now_s();
         {
-            std::lock_guard<std::mutex> lk(S->mu);
-            S->reserved -= r->bytes;
-            if (r->kind == GEO_REQ_LOGLIK && r->keep && res.status == GEO_OK) {
-                // the kept factor stays on the device: keep its matrix reserved
-                const size_t keep_bytes = r->bytes / 2;
-                S->reserved += keep_bytes;
-                S->factor_bytes[r->dataset] = keep_bytes;
+            std::unique_lock<std::mutex> lk(S->mu);
+            publish_idle(w);
+            if (S->starved) {
+                trim_unlocked(w, lk);
+                S->starved = false;
             }
+            size_t tot = 0;
+            for (Worker *v : S->workers) tot += v->foot;
+            S->reserved = tot;
             S->inflight -= 1;
             S->done.push_back(res);
         }
@@ -265,6 +338,7 @@ int geo_server_submit(geo_server *S, const geo_request *q, double *zhat_host, lo
     r->kind = q->kind;
     r->keep = q->keep;
     r->release = q->release;
+    r->escalate = q->escalate;
     r->dataset = q->dataset;
     r->n = q->n;
     r->m = q->m;
@@ -302,8 +376,8 @@ int geo_server_submit(geo_server *S, const geo_request *q, double *zhat_host, lo
         delete r;
         return GEO_EINVAL;
     }
-    r->bytes = estimate_bytes(*r);
-    if (S->budget && r->bytes > S->budget) {
+    r->bytes = request_bytes(S, *r, 0);
+    if (S->budget && r->kind == GEO_REQ_LOGLIK && r->bytes > S->budget) {
         delete r;
         return GEO_ENOMEM;
     }
@@ -334,6 +408,28 @@ int geo_server_pending(geo_server *S, int *queued, int *inflight, long long *res
     if (queued) *queued = (int)S->queue.size();
     if (inflight) *inflight = S->inflight;
     if (reserved_bytes) *reserved_bytes = (long long)S->reserved;
+    return GEO_OK;
+}
+
+int geo_server_profile_read(geo_server *S, geo_kstat *out) {
+    if (!S || !out) return GEO_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (!S->queue.empty() || S->inflight) return GEO_EINVAL;
+    }
+    for (int k = 0; k < GEO_K_COUNT; ++k) out[k] = geo_kstat{0, 0.0, 0.0, 0.0, 0};
+    for (Worker *w : S->workers) {
+        geo_kstat ks[GEO_K_COUNT];
+        int rc = geo_profile_read(w->ctx, ks);
+        if (rc != GEO_OK) return rc;
+        for (int k = 0; k < GEO_K_COUNT; ++k) {
+            out[k].launches += ks[k].launches;
+            out[k].ms += ks[k].ms;
+            out[k].flops += ks[k].flops;
+            out[k].bytes += ks[k].bytes;
+            out[k].timed += ks[k].timed;
+        }
+    }
     return GEO_OK;
 }
 

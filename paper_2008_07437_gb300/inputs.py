@@ -139,3 +139,63 @@ WORKLOADS = {
                                       ThetaSpec((1.0, 1.0, 1.0), 0.05, (0.5, 1.0, 1.5), (0.5, 0.3, 0.4)),
                                       nb=1800, loc_seed=1003, z_seed=2003),
 }
+
+
+@dataclass
+class ServingRequest:
+    """One request of a serving stream.  kind: "loglik" or "predict"."""
+    k: int
+    t_arrival: float          # seconds after the stream starts
+    kind: str
+    n: int = 0                # loglik: locations (bivariate, N = 2 n)
+    theta: ThetaSpec | None = None
+    dataset: int = 0          # key of the factor a loglik keeps / a predict reuses
+    keep: bool = False
+    release: bool = False
+    m: int = 0                # predict: new locations
+
+    def locations(self) -> np.ndarray:
+        return jittered_grid(self.n, 30000 + self.k)
+
+    def observations(self) -> np.ndarray:
+        """Z for a loglik request: seeded standard normals (the evaluation's
+        cost does not depend on Z's values)."""
+        return normals(40000 + self.k, 2 * self.n)
+
+    def new_locations(self) -> np.ndarray:
+        return jittered_grid(self.m, 50000 + self.k)
+
+
+def serving_stream(count: int, rate: float = 200.0, seed: int = 3000, n_lo: int = 1000, n_hi: int = 20000,
+                   m_lo: int = 100, m_hi: int = 2000, p_loglik: float = 0.7) -> list[ServingRequest]:
+    """A seeded Poisson stream of bivariate requests: exponential gaps of mean
+    1/rate; a fraction p_loglik of likelihood evaluations with n uniform in
+    [n_lo, n_hi] at a random theta (a in [0.03, 0.2], nu_i in [0.5, 1.5],
+    beta in [-0.7, 0.7], sigma^2_i in [0.5, 2]); the rest cokriging requests
+    of m uniform in [m_lo, m_hi] new locations on the factor of the latest
+    likelihood request, which then keeps its factor; the last request on a
+    factor releases it.  A cokriging request with no likelihood before it
+    becomes a likelihood request."""
+    U = uniforms(seed, 10 * count).reshape(count, 10)
+    out: list[ServingRequest] = []
+    t = 0.0
+    last_ll = None
+    for k in range(count):
+        u = U[k]
+        t += -math.log1p(-u[0]) / rate
+        if u[1] < p_loglik or last_ll is None:
+            th = ThetaSpec(sigma2=(0.5 + 1.5 * u[3], 0.5 + 1.5 * u[4]), a=0.03 + 0.17 * u[5],
+                           nu=(0.5 + u[6], 0.5 + u[7]), beta=(-0.7 + 1.4 * u[8],))
+            r = ServingRequest(k, t, "loglik", n=n_lo + int(u[2] * (n_hi - n_lo + 1)), theta=th, dataset=k)
+            last_ll = r
+        else:
+            last_ll.keep = True
+            r = ServingRequest(k, t, "predict", dataset=last_ll.dataset, m=m_lo + int(u[9] * (m_hi - m_lo + 1)))
+        out.append(r)
+    last_use = {}
+    for r in out:
+        if r.kind == "predict":
+            last_use[r.dataset] = r
+    for r in last_use.values():
+        r.release = True
+    return out

@@ -95,10 +95,11 @@ def test_server_result_same_alone_and_in_the_mix(built):
 
 
 def test_server_budget_admission_and_rejection(built):
-    # a budget that admits about one request of this size at a time
+    # a budget that admits one request of this size at a time: the matrix
+    # (ld x N doubles, ld = N + 1 rounded up to 32) dominates the footprint
     n = 800
     N = 2 * n
-    one = 8 * (N + 32) * N + 8 * 4 * N + (8 << 20)
+    one = 8 * ((N + 1 + 31) // 32 * 32) * N
     srv = geo.Server(0, int(one * 1.5), slots=4)
     try:
         data = [_dataset(n, 5, 40 + k) for k in range(4)]
@@ -108,6 +109,8 @@ def test_server_budget_admission_and_rejection(built):
         spans = sorted((res[i]["t_start"], res[i]["t_end"]) for i in ids)
         for (s0, e0), (s1, e1) in zip(spans, spans[1:]):
             assert s1 >= e0 - 1e-6   # never two at once under this budget
+        _, _, reserved = srv.pending()
+        assert reserved <= int(one * 1.5)
         big = _dataset(3000, 5, 50)
         with pytest.raises(geo.GeoError) as ei:
             srv.submit_loglik(big[0], big[1], big[3], geo.opts(nb=128))
@@ -142,3 +145,28 @@ def test_autotuner_picks_a_candidate_and_nb0_uses_it(built):
         assert v0 == vb
     finally:
         ctx.close()
+
+
+def test_server_escalates_a_reduced_form_that_is_not_spd(built):
+    # a = 0.2, nu_2 = 1.5 at 5,000 locations: FP32 off-diagonal tiles lose
+    # positive definiteness, FP64 does not
+    th = geo.Theta((1.0, 1.0), 0.2, (0.5, 1.5), 0.7)
+    locs = inputs.jittered_grid(5000, 77)
+    z = inputs.normals(78, 10000)
+    mixed = geo.opts(nb=0, prec=1, band=1 << 20, refine_iters=2)
+    srv = geo.Server(0, 0, slots=2)
+    try:
+        r_plain = srv.submit_loglik(locs, z, th, mixed)
+        r_esc = srv.submit_loglik(locs, z, th, mixed, escalate=True)
+        res = _collect(srv, 2)
+    finally:
+        srv.close()
+    assert res[r_plain]["status"] == geo.GEO_ENOTSPD and res[r_plain]["prec"] == 1
+    assert res[r_esc]["status"] == geo.GEO_OK and res[r_esc]["prec"] == 0
+    ctx = geo.geo_create(0)
+    try:
+        l64, _ = geo.geo_loglik(ctx, torch.as_tensor(locs, device="cuda"), torch.as_tensor(z, device="cuda"), th,
+                                geo.opts(nb=0))
+    finally:
+        ctx.close()
+    assert res[r_esc]["loglik"] == l64
