@@ -109,7 +109,9 @@ const char *geo_last_error(const geo_ctx *ctx);
  * i.e. column-major (p*n1) x (p*n2) with leading dimension ld >= p*n1.
  * locs2_dev == NULL means locs2 = locs1 (then Sigma itself, all entries).
  * h = 0 uses the limit rho_ij sigma_ii sigma_jj (no nugget).  The Bessel
- * function K_nu is evaluated in FP64 on the device.  No reordering.
+ * function K_nu is evaluated in FP64 on the device.  No reordering.  The
+ * call first builds the per-theta K_nu tables in a buffer of the context on
+ * `stream`: calls on one context must not overlap on different streams.
  */
 int geo_covgen(geo_ctx *ctx, const double *locs1_dev, int n1, const double *locs2_dev, int n2,
                const geo_theta *theta, double *out_dev, long long ld, void *stream);
@@ -379,10 +381,10 @@ int geo_server_profile_read(geo_server *server, geo_kstat *out);
  * loop that cannot afford cudaMalloc / cudaFree, which may synchronise the
  * device and may fail at unpredictable times.  This entry point allocates
  * nothing and needs no context: every intermediate (the covariance matrix and
- * its factor, the reordered locations, the status words) lives in one
- * fixed-size array in device global memory owned by the library, about
- * GEO_NOALLOC_SCRATCH_DOUBLES * 8 bytes (34 MB), which every GPU that loads the
- * library holds until the process exits.
+ * its factor, the reordered locations, the K_nu tables of theta, the status
+ * words) lives in one fixed-size array in device global memory owned by the
+ * library, about GEO_NOALLOC_SCRATCH_DOUBLES * 8 bytes (34 MB), which every
+ * GPU that loads the library holds until the process exits.
  *
  *   locs_dev  n x 2 locations (device, caller-owned); used in the caller's order
  *   z_dev     N = p*n observations in Representation I (device)
@@ -402,7 +404,7 @@ int geo_server_profile_read(geo_server *server, geo_kstat *out);
  * serialise them (one stream, one thread).
  */
 #define GEO_NOALLOC_MAX_N 2048
-#define GEO_NOALLOC_SCRATCH_DOUBLES 4263938LL
+#define GEO_NOALLOC_SCRATCH_DOUBLES 4267778LL
 int geo_loglik_noalloc(const double *locs_dev, int n, const double *z_dev, const geo_theta *theta, int nb,
                        double *out_dev, int *info_dev, void *stream);
 

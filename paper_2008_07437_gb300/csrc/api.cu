@@ -49,6 +49,8 @@ struct geo_ctx {
     std::map<std::tuple<int, int, int>, std::pair<cudaGraphExec_t, long long>> graphs;   // -> (exec, kernel nodes)
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture (the legacy stream cannot capture)
     std::vector<geo_factor *> factors;
+    // K_nu tables of the theta of the last geo_covgen call
+    double *ctab = nullptr;
     Profiler prof;
 };
 
@@ -316,8 +318,18 @@ int theta_to_params(const geo_theta *th, CovParams *cp, std::string *err) {
             c.mu = nij - nl;
             temme_gammas(c.mu, &c.g1, &c.g2, &c.gp, &c.gm, &c.fact);
             c.kind = (nij == 0.5) ? 1 : (nij == 1.5) ? 2 : (nij == 2.5) ? 3 : 0;
+            c.toff = -1;
         }
     }
+    // K_nu tables for the general orders nu_ij <= GEO_CHEB_NU_MAX, one per i <= j
+    int g = 0;
+    for (int i = 0; i < p; ++i)
+        for (int j = i; j < p; ++j) {
+            MaternConst &c = cp->m[i * p + j];
+            if (c.kind == 0 && c.nu <= GEO_CHEB_NU_MAX) c.toff = (g++) * GEO_TAB_PER_PAIR;
+            cp->m[j * p + i].toff = c.toff;
+        }
+    cp->tab = nullptr;
     return GEO_OK;
 }
 
@@ -410,6 +422,7 @@ int geo_destroy(geo_ctx *ctx) {
     if (ctx->rws) dev_free(ctx, ctx->rws, ctx->rws_bytes);
     if (ctx->tws) dev_free(ctx, ctx->tws, ctx->tws_bytes);
     if (ctx->tarena) cudaFreeHost(ctx->tarena);
+    if (ctx->ctab) dev_free(ctx, ctx->ctab, sizeof(double) * GEO_TAB_DOUBLES);
     for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.second.first);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->bws) dev_free(ctx, ctx->bws, ctx->bws_bytes);
@@ -439,6 +452,13 @@ int geo_covgen(geo_ctx *ctx, const double *locs1_dev, int n1, const double *locs
     if ((n1 > 0 && (!locs1_dev || !out_dev))) return fail(ctx, GEO_EINVAL, "NULL pointer");
     SetDevice sd(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
+    if (n1 == 0 || n2 == 0) return GEO_OK;
+    if (!ctx->ctab && cov_needs_tables(cp)) {
+        void *pt;
+        if ((rc = dev_alloc(ctx, &pt, sizeof(double) * GEO_TAB_DOUBLES))) return rc;
+        ctx->ctab = (double *)pt;
+    }
+    CK(launch_cheb_build(cp, ctx->ctab, s));
     CK(launch_covgen_rect(cp, locs1_dev, n1, locs2_dev ? locs2_dev : locs1_dev, n2, out_dev, ld, s));
     return GEO_OK;
 }
@@ -469,9 +489,10 @@ static int prepare_matrix(geo_ctx *ctx, const double *locs_dev, int n, const geo
         std::iota(f->perm.begin(), f->perm.end(), 0);
     // device buffers: locations (SoA) + permutation
     void *p1, *p2;
-    if ((rc = dev_alloc(ctx, &p1, sizeof(double) * 2 * n))) return rc;
+    if ((rc = dev_alloc(ctx, &p1, sizeof(double) * (2 * (size_t)n + GEO_TAB_DOUBLES)))) return rc;
     f->lx = (double *)p1;
     f->ly = f->lx + n;
+    CK(launch_cheb_build(f->cp, f->lx + 2 * (size_t)n, s));   // K_nu tables after the locations
     if ((rc = dev_alloc(ctx, &p2, sizeof(int) * n))) return rc;
     int *d_perm = (int *)p2;
     CK(cudaMemcpyAsync(d_perm, f->perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
@@ -522,7 +543,7 @@ static void release_factor_buffers(geo_ctx *ctx, geo_factor *f, bool keep_matrix
         }
         f->A = nullptr;
     }
-    if (f->lx) dev_free(ctx, f->lx, sizeof(double) * 2 * f->n);
+    if (f->lx) dev_free(ctx, f->lx, sizeof(double) * (2 * (size_t)f->n + GEO_TAB_DOUBLES));
     if (f->w) dev_free(ctx, f->w, sizeof(double) * f->N);
     f->lx = f->ly = f->w = nullptr;
     if (f->ybuf) dev_free(ctx, f->ybuf, sizeof(double) * f->N);
@@ -839,7 +860,8 @@ int geo_factor_stats_get(const geo_factor *f, geo_factor_stats *out) {
     out->loglik = f->loglik;
     out->logdet = f->logdet;
     out->quad = f->quad;
-    out->device_bytes = (long long)(f->A_bytes + sizeof(double) * 2 * f->n + (f->w ? sizeof(double) * f->N : 0));
+    out->device_bytes = (long long)(f->A_bytes + sizeof(double) * (2 * (size_t)f->n + GEO_TAB_DOUBLES) +
+                                    (f->w ? sizeof(double) * f->N : 0));
     out->tlr_bytes_ratio = 1.0;
     if (f->tlr) {
         const TlrFactor &F = *f->tlr;
@@ -849,7 +871,7 @@ int geo_factor_stats_get(const geo_factor *f, geo_factor_stats *out) {
         out->tlr_bytes_ratio = used / dense;
         out->tlr_max_rank = F.max_rank;
         out->tlr_dense_tiles = F.capped;
-        out->device_bytes = (long long)(8.0 * used + sizeof(double) * (2.0 * f->n + f->N));
+        out->device_bytes = (long long)(8.0 * used + sizeof(double) * (2.0 * f->n + GEO_TAB_DOUBLES + f->N));
     }
     return GEO_OK;
 }
@@ -944,7 +966,7 @@ int geo_loglik_batch(geo_ctx *ctx, int count, const geo_batch_item *items, doubl
         const int N = it.theta.p * it.n;
         const long long ld = round_up((long long)N + 1, 32);
         offs[k] = total;
-        total += (size_t)ld * N;
+        total += (size_t)ld * N + GEO_TAB_DOUBLES;   // matrix, then the theta's K_nu tables
         nmax = std::max(nmax, it.n);
         Nmax = std::max(Nmax, N);
     }
@@ -970,8 +992,9 @@ int geo_loglik_batch(geo_ctx *ctx, int count, const geo_batch_item *items, doubl
     for (int k = 0; k < count; ++k) {
         const geo_batch_item &it = items[k];
         const int N = it.theta.p * it.n;
-        batch_fill_desc(ctx->bdesc_h, k, base + offs[k], round_up((long long)N + 1, 32), N, it.n, it.locs_dev,
-                        it.z_dev, cps[k]);
+        const long long ld = round_up((long long)N + 1, 32);
+        cps[k].tab = base + offs[k] + (size_t)ld * N;
+        batch_fill_desc(ctx->bdesc_h, k, base + offs[k], ld, N, it.n, it.locs_dev, it.z_dev, cps[k]);
     }
     CK(cudaMemcpyAsync(ctx->bdesc_d, ctx->bdesc_h, dbytes, cudaMemcpyHostToDevice, s));
     const auto key = std::make_tuple(count, nmax, Nmax);
@@ -1119,7 +1142,7 @@ size_t loglik_device_bytes(int device, int n, int p, const geo_opts *opts) {
     const size_t N = (size_t)p * n;
     if (o.nb == 0) o.nb = resolve_nb(device, o.prec, (int)N);
     const size_t nb = (size_t)std::max(o.nb, 64);
-    size_t b = sizeof(double) * 2 * n + sizeof(int) * 2 * n + sizeof(double) * N;   // locations, perms, w
+    size_t b = sizeof(double) * (2 * (size_t)n + GEO_TAB_DOUBLES) + sizeof(int) * 2 * n + sizeof(double) * N;
     if (o.prec == GEO_PREC_TLR) {
         const int kmax = std::min(o.tlr_kmax, (int)nb);
         const size_t T = (N + nb - 1) / nb;

@@ -35,6 +35,13 @@ struct BatchDesc {
     DevResults res;
 };
 
+// K_nu tables of every problem's theta: block (q, k, problem).
+__global__ void __launch_bounds__(32) k_b_cheb_build(BatchDesc *d) {
+    __shared__ double hv[GEO_CHEB_N];
+    const CovParams &cp = d[blockIdx.z].cp;
+    cheb_build_block(cp, const_cast<double *>(cp.tab), blockIdx.x, blockIdx.y, hv);
+}
+
 __global__ void __launch_bounds__(256) k_b_covgen(BatchDesc *d) {
     BatchDesc &q = d[blockIdx.z];
     const int n = q.n;
@@ -48,7 +55,7 @@ __global__ void __launch_bounds__(256) k_b_covgen(BatchDesc *d) {
     const int p = cp.p;
     for (int i = 0; i < p; ++i)
         for (int j = 0; j < p; ++j) {
-            const double v = matern_cov(x, cp.m[(i <= j) ? i * p + j : j * p + i]);
+            const double v = matern_cov(x, cp.m[(i <= j) ? i * p + j : j * p + i], cp.tab);
             q.A[(long long)(p * r + j) * q.ld + p * l + i] = v;
         }
 }
@@ -239,6 +246,10 @@ void batch_fill_desc(void *hdesc_v, int k, double *A, long long ld, int N, int n
 
 cudaError_t batch_record(void *ddesc_v, int count, int nmax, int Nmax, cudaStream_t s) {
     BatchDesc *d = (BatchDesc *)ddesc_v;
+    {
+        KScope ks(GEO_K_COVGEN, s);
+        k_b_cheb_build<<<dim3(GEO_PMAX_DEV * GEO_PMAX_DEV, GEO_CHEB_NI + 1, count), 32, 0, s>>>(d);
+    }
     {
         KScope ks(GEO_K_COVGEN, s);
         dim3 grid((nmax + 3) / 4, (nmax + 63) / 64, count);

@@ -18,11 +18,17 @@ __device__ __forceinline__ void cov_block(const CovParams &cp, double h, double 
     const int p = cp.p;
     for (int i = 0; i < p; ++i) {
         for (int j = i; j < p; ++j) {
-            const double c = matern_cov(x, cp.m[i * p + j]);
+            const double c = matern_cov(x, cp.m[i * p + j], cp.tab);
             v[i * GEO_PMAX_DEV + j] = c;
             v[j * GEO_PMAX_DEV + i] = c;
         }
     }
+}
+
+// K_nu tables of one theta (cheb_build_block, matern.cuh): block (q, k).
+__global__ void __launch_bounds__(32) k_cheb_build(const CovParams cp, double *tab) {
+    __shared__ double hv[GEO_CHEB_N];
+    cheb_build_block(cp, tab, blockIdx.x, blockIdx.y, hv);
 }
 
 // Lower triangle (location blocks l >= r) of Sigma, column-major A[c*ld + r].
@@ -129,6 +135,21 @@ __global__ void k_scatter_vec(const double *__restrict__ in, long long stride, c
 }
 
 }  // namespace
+
+bool cov_needs_tables(const CovParams &cp) {
+    for (int q = 0; q < cp.p * cp.p; ++q)
+        if (cp.m[q].kind == 0 && cp.m[q].toff >= 0) return true;
+    return false;
+}
+
+cudaError_t launch_cheb_build(CovParams &cp, double *tab, cudaStream_t s) {
+    cp.tab = tab;
+    if (!cov_needs_tables(cp)) return cudaSuccess;
+    if (!tab) return cudaErrorInvalidValue;
+    KScope ks(GEO_K_COVGEN, s);
+    k_cheb_build<<<dim3(cp.p * cp.p, GEO_CHEB_NI + 1), 32, 0, s>>>(cp, tab);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_covgen_sym(const CovParams &cp, const double *lx, const double *ly, int n, double *A,
                               long long ld, cudaStream_t s) {

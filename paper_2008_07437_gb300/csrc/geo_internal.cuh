@@ -64,6 +64,11 @@ struct KScope {
 };
 
 // ---- covgen.cu ----------------------------------------------------------
+// Build the K_nu tables of theta into tab (GEO_TAB_DOUBLES device doubles) on
+// stream s and point cp.tab at them; every covariance kernel launched with cp
+// afterwards reads them.  Nothing is launched when theta has no tabulated order.
+cudaError_t launch_cheb_build(CovParams &cp, double *tab, cudaStream_t s);
+bool cov_needs_tables(const CovParams &cp);
 // Lower triangle of Sigma (order p*n) into A (column-major, ld), from
 // SoA locations; the full p x p block on the location diagonal.
 cudaError_t launch_covgen_sym(const CovParams &cp, const double *lx, const double *ly, int n, double *A,

@@ -14,7 +14,7 @@
 // doubles (about 34 MB), present on every GPU that loads the library until
 // the process exits.  It holds the matrix (order N = p*n <= GEO_NOALLOC_MAX_N,
 // leading dimension round_up(N + 1, 32), the extra row carrying Z / L^-1 Z),
-// the SoA locations and the status words.  In host code the array's name is
+// the SoA locations, the K_nu tables of theta and the status words.  In host code the array's name is
 // only a host-side stand-in, so its device address is looked up once per
 // device with cudaGetSymbolAddress (with that device current) and cached;
 // that look-up happens during the first call on each device, which should
@@ -36,8 +36,9 @@ namespace {
 constexpr long long kLdMax = ((GEO_NOALLOC_MAX_N + 1 + 31) / 32) * 32;
 constexpr long long kMatDoubles = kLdMax * GEO_NOALLOC_MAX_N;
 constexpr long long kLocDoubles = 2LL * GEO_NOALLOC_MAX_N;
+constexpr long long kTabDoubles = GEO_TAB_DOUBLES;
 constexpr long long kStatusDoubles = (sizeof(DevStatus) + sizeof(double) - 1) / sizeof(double);
-constexpr long long kScratchDoubles = kMatDoubles + kLocDoubles + kStatusDoubles;
+constexpr long long kScratchDoubles = kMatDoubles + kLocDoubles + kTabDoubles + kStatusDoubles;
 
 __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
@@ -85,12 +86,14 @@ extern "C" int geo_loglik_noalloc(const double *locs_dev, int n, const double *z
     double *A = scratch;
     double *lx = scratch + kMatDoubles;
     double *ly = lx + n;
-    DevStatus *st = (DevStatus *)(scratch + kMatDoubles + kLocDoubles);
+    double *tab = scratch + kMatDoubles + kLocDoubles;
+    DevStatus *st = (DevStatus *)(scratch + kMatDoubles + kLocDoubles + kTabDoubles);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
     if ((e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s)) ||
         (e = launch_gather_locs(locs_dev, nullptr, n, lx, ly, s)) ||
         (e = launch_gather_vec(z_dev, nullptr, n, theta->p, A + N, ld, s)) ||
+        (e = launch_cheb_build(cp, tab, s)) ||
         (e = launch_covgen_sym(cp, lx, ly, n, A, ld, s)) ||
         (e = chol64_factor(A, ld, N, N + 1, nb, st, s)) ||
         (e = launch_loglik_reduce(A, ld, N, A + N, ld, st, (DevResults *)out_dev, s))) {

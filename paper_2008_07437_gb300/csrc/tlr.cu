@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) k_covgen_block(const CovParams cp, const 
     const int p = cp.p;
     for (int i = 0; i < p; ++i)
         for (int j = 0; j < p; ++j) {
-            const double v = matern_cov(x, cp.m[(i <= j) ? i * p + j : j * p + i]);
+            const double v = matern_cov(x, cp.m[(i <= j) ? i * p + j : j * p + i], cp.tab);
             out[(long long)(p * (r - r0) + j) * ld + p * (l - l0) + i] = v;
         }
 }

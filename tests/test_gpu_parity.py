@@ -92,6 +92,31 @@ def test_covgen_rect_all_ranges(ctx, a):
     assert_cov_close(got, ref, cov_rtol(theta, l1, l2))
 
 
+@pytest.mark.parametrize("nu", [(0.5, 1.0), (0.3, 0.8), (0.05, 0.15), (1.2, 2.7), (2.9, 3.3), (0.6, 3.4)])
+def test_covgen_bessel_every_interval(ctx, nu):
+    # x = h / a from 1e-4 to 1.1e3: the small-x series (x < 1/4), every
+    # Chebyshev interval [2^k, 2^(k+1)), k = -2 .. 9, the cut-off at 1024, and
+    # orders above 3 (reference evaluator)
+    a = 0.01
+    h = np.geomspace(1e-6, 11.0, 701)
+    l1 = np.array([[0.25, 0.5]])
+    l2 = np.stack([0.25 + h, np.full_like(h, 0.5)], axis=1)
+    theta = geo.Theta((1.0, 2.0), a, nu, 0.3)
+    out = torch.zeros((2 * len(h), 2), dtype=torch.float64, device="cuda")
+    geo.geo_covgen(ctx, dev(l1), theta, out, locs2=dev(l2), ld=2)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().T
+    ref = oracle.covgen(o_theta(theta), l1, l2)
+    x = np.repeat(h / a, 2)[None, :]
+    tiny = np.abs(ref) < 1e-280
+    assert np.all(np.abs(got[tiny]) < 1e-280)
+    rtol = 1e-14 + 1e-15 * x
+    err = np.abs(got - ref)
+    bad = (err > rtol * np.abs(ref)) & ~tiny
+    assert not bad.any(), "%d entries off; worst rel %.3e at x = %s" % (
+        bad.sum(), (err / np.abs(ref))[bad].max(), x[bad][:5])
+
+
 # ------------------------------------------------------------------ loglik --
 
 def _problem(n, theta, seed=1):
