@@ -29,6 +29,7 @@ struct geo_ctx {
     std::string err;
     DevStatus *st = nullptr;
     DevResults *res = nullptr;
+    int *sync = nullptr;          // 4 ints: sync words of the one-launch triangular solves
     DevStatus *h_st = nullptr;    // pinned
     DevResults *h_res = nullptr;  // pinned
     // reusable workspace for the matrix of a discarded evaluation
@@ -399,6 +400,7 @@ int geo_create(geo_ctx **out, int device, size_t hbm_budget_bytes) {
     SetDevice sd(device);
     if (cudaMalloc(&ctx->st, sizeof(DevStatus)) != cudaSuccess ||
         cudaMalloc(&ctx->res, sizeof(DevResults)) != cudaSuccess ||
+        cudaMalloc(&ctx->sync, 4 * sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_st, sizeof(DevStatus)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_res, sizeof(DevResults)) != cudaSuccess) {
         cudaGetLastError();
@@ -430,6 +432,7 @@ int geo_destroy(geo_ctx *ctx) {
     if (ctx->bdesc_h) cudaFreeHost(ctx->bdesc_h);
     if (ctx->st) cudaFree(ctx->st);
     if (ctx->res) cudaFree(ctx->res);
+    if (ctx->sync) cudaFree(ctx->sync);
     if (ctx->h_st) cudaFreeHost(ctx->h_st);
     if (ctx->h_res) cudaFreeHost(ctx->h_res);
     delete ctx;
@@ -780,7 +783,7 @@ int geo_predict(geo_ctx *ctx, const geo_factor *factor, const double *new_locs_d
             CK(cudaMemcpyAsync(f->w, f->ybuf, sizeof(double) * f->N, cudaMemcpyDeviceToDevice, s));
             CK(tlr_solve(*f->tlr, f->w, true, ctx->tws, ctx->tarena, s));
         } else {
-            CK(backward_solve(f->A, f->ld, f->N, f->A + f->N, f->ld, f->w, s));
+            CK(backward_solve(f->A, f->ld, f->N, f->A + f->N, f->ld, f->w, ctx->sync, &ctx->st->timeout, s));
         }
     }
     CK(launch_predict(f->cp, new_locs_dev, m, f->lx, f->ly, f->n, f->w, zhat_dev, s));

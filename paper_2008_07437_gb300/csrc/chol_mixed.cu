@@ -24,19 +24,40 @@
 
 namespace {
 
-constexpr int SB = 128, SK = 8;   // SIMT FP32 GEMM: 128 x 128 tile, K slices of 8
+constexpr int SB = 128, SK = 16;   // SIMT FP32 GEMM: 128 x 128 tile, K slices of 16, double-buffered
+
+// Asynchronous global -> shared copies (cp.async, bytes beyond src_bytes
+// are zero-filled; src_bytes = 0 reads nothing).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem, int src_bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // C[i, j] -= sum_k A[i, k] B[j, k] (i < m, j < n); A, B column-major FP32; C
 // column-major TC.  gr0 / gc0: global row / col of C(0, 0) for the class
 // filter (nb-tile distance in [dlo, dhi]) and, when tri, the skip of tiles
 // entirely above the diagonal.
+//
+// 256 threads; thread (tx, ty) = (t % 16, t / 16) owns rows {4 tx .. 4 tx + 3,
+// 64 + 4 tx ..} and cols {4 ty .., 64 + 4 ty ..} of the tile: the fragments
+// are float4 reads of shared memory, and the epilogue updates 4 consecutive
+// rows of a column per access (32 bytes of FP64 C).  K slices of 16 are
+// copied into two shared-memory stages with cp.async while the other stage
+// is used.  vec: A, B, C and their leading dimensions allow 16-byte accesses.
 template <typename TC>
-__global__ void __launch_bounds__(256) k_sgemm_nt(TC *C, long long ldc, const float *__restrict__ A, long long lda,
-                                                  const float *__restrict__ B, long long ldb, int m, int n, int k,
-                                                  int gr0, int gc0, int nb, int dlo, int dhi, int tri,
-                                                  const DevStatus *st) {
-    __shared__ float As[SK][SB + 4];
-    __shared__ float Bs[SK][SB + 4];
+__global__ void __launch_bounds__(256, 2) k_sgemm_nt(TC *C, long long ldc, const float *__restrict__ A, long long lda,
+                                                     const float *__restrict__ B, long long ldb, int m, int n, int k,
+                                                     int gr0, int gc0, int nb, int dlo, int dhi, int tri, int vec,
+                                                     const DevStatus *st) {
+    __shared__ __align__(16) float As[2][SK][SB + 4];
+    __shared__ __align__(16) float Bs[2][SK][SB + 4];
     if (st->info) return;
     const int tm = blockIdx.x * SB, tn = blockIdx.y * SB;
     const int gr = gr0 + tm, gc = gc0 + tn;
@@ -47,28 +68,52 @@ __global__ void __launch_bounds__(256) k_sgemm_nt(TC *C, long long ldc, const fl
     }
     if (tri && gr + SB - 1 < gc) return;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    // slice element e = threadIdx.x + 256 q (q = 0, 1): k row e / 32, rows 4 (e % 32) .. + 3
+    auto load = [&](int k0, int buf) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int e = threadIdx.x + 256 * q;
+            const int kk = e / 32, r = 4 * (e % 32);
+            const bool kin = k0 + kk < k;
+            const int va = kin ? max(0, min(4, m - (tm + r))) : 0;   // valid elements of the 4
+            const int vb = kin ? max(0, min(4, n - (tn + r))) : 0;
+            const float *pa = va ? A + (long long)(k0 + kk) * lda + tm + r : A;
+            const float *pb = vb ? B + (long long)(k0 + kk) * ldb + tn + r : B;
+            if (vec) {
+                cp_async16(&As[buf][kk][r], pa, 4 * va);
+                cp_async16(&Bs[buf][kk][r], pb, 4 * vb);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    cp_async4(&As[buf][kk][r + i], i < va ? pa + i : A, i < va ? 4 : 0);
+                    cp_async4(&Bs[buf][kk][r + i], i < vb ? pb + i : B, i < vb ? 4 : 0);
+                }
+            }
+        }
+        cp_async_commit();
+    };
     float acc[8][8];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    load(0, 0);
+    int buf = 0;
     for (int k0 = 0; k0 < k; k0 += SK) {
-#pragma unroll
-        for (int t = 0; t < (SK * SB) / 256; ++t) {
-            const int idx = threadIdx.x + t * 256;
-            const int kk = idx / SB, r = idx % SB;
-            const bool kin = k0 + kk < k;
-            As[kk][r] = (kin && tm + r < m) ? A[(long long)(k0 + kk) * lda + tm + r] : 0.f;
-            Bs[kk][r] = (kin && tn + r < n) ? B[(long long)(k0 + kk) * ldb + tn + r] : 0.f;
+        if (k0 + SK < k) {
+            load(k0 + SK, buf ^ 1);   // the other stage: released by the barrier that ended its last use
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < SK; ++kk) {
             float a[8], b[8];
-            const float4 a0 = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
-            const float4 a1 = *reinterpret_cast<const float4 *>(&As[kk][64 + ty * 4]);
-            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
-            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[kk][64 + tx * 4]);
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][tx * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + tx * 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][ty * 4]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + ty * 4]);
             a[0] = a0.x, a[1] = a0.y, a[2] = a0.z, a[3] = a0.w, a[4] = a1.x, a[5] = a1.y, a[6] = a1.z, a[7] = a1.w;
             b[0] = b0.x, b[1] = b0.y, b[2] = b0.z, b[3] = b0.w, b[4] = b1.x, b[5] = b1.y, b[6] = b1.z, b[7] = b1.w;
 #pragma unroll
@@ -76,17 +121,42 @@ __global__ void __launch_bounds__(256) k_sgemm_nt(TC *C, long long ldc, const fl
 #pragma unroll
                 for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
         }
-        __syncthreads();
+        __syncthreads();   // every thread is done with this stage before it is refilled
+        buf ^= 1;
     }
+    // epilogue: C -= acc, 4 consecutive rows of a column per access
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const int c = tn + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+        const int c = tn + (j < 4 ? ty * 4 + j : 64 + ty * 4 + (j - 4));
         if (c >= n) continue;
         TC *col = C + (long long)c * ldc + tm;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int r = (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
-            if (tm + r < m) col[r] -= (TC)acc[i][j];
+        for (int h = 0; h < 2; ++h) {
+            const int r = h * 64 + tx * 4;
+            if (vec && tm + r + 3 < m) {
+                if constexpr (sizeof(TC) == 8) {
+                    double2 *pc = reinterpret_cast<double2 *>(col + r);
+                    double2 u = pc[0], w = pc[1];
+                    u.x -= (double)acc[4 * h + 0][j];
+                    u.y -= (double)acc[4 * h + 1][j];
+                    w.x -= (double)acc[4 * h + 2][j];
+                    w.y -= (double)acc[4 * h + 3][j];
+                    pc[0] = u;
+                    pc[1] = w;
+                } else {
+                    float4 *pc = reinterpret_cast<float4 *>(col + r);
+                    float4 u = *pc;
+                    u.x -= acc[4 * h + 0][j];
+                    u.y -= acc[4 * h + 1][j];
+                    u.z -= acc[4 * h + 2][j];
+                    u.w -= acc[4 * h + 3][j];
+                    *pc = u;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (tm + r + i < m) col[r + i] -= (TC)acc[4 * h + i][j];
+            }
         }
     }
 }
@@ -208,8 +278,11 @@ cudaError_t sgemm(TC *C, long long ldc, const float *A, long long lda, const flo
                   cudaStream_t s) {
     if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
     dim3 grid((m + SB - 1) / SB, (n + SB - 1) / SB);
+    // 16-byte vector accesses when every tile row start is 16-byte aligned
+    const int vec = ((uintptr_t)A % 16 == 0) && ((uintptr_t)B % 16 == 0) && ((uintptr_t)C % 16 == 0) && lda % 4 == 0 &&
+                    ldb % 4 == 0 && (ldc * (long long)sizeof(TC)) % 16 == 0;
     KScope ks(GEO_K_SGEMM, s, flops, 0.0);
-    k_sgemm_nt<TC><<<grid, 256, 0, s>>>(C, ldc, A, lda, B, ldb, m, n, k, gr0, gc0, nb, dlo, dhi, tri, st);
+    k_sgemm_nt<TC><<<grid, 256, 0, s>>>(C, ldc, A, lda, B, ldb, m, n, k, gr0, gc0, nb, dlo, dhi, tri, vec, st);
     return cudaGetLastError();
 }
 

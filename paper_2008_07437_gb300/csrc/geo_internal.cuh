@@ -119,14 +119,20 @@ size_t loglik_device_bytes(int device, int n, int p, const geo_opts *opts);
 // logdet = 2 sum log L_kk, quad = sum y_k^2 (y = row N of A), loglik = Eq. 1.
 cudaError_t launch_loglik_reduce(const double *A, long long ld, int N, const double *y, long long ystride,
                                  const DevStatus *st, DevResults *res, cudaStream_t s);
-// w = L^-T y (y strided), w contiguous.
+// ---- trsv.cu --------------------------------------------------------------
+// One-launch triangular solves with the column-major lower factor in A.
+// sync: 4 device ints of scratch (zeroed here); timeout_word: NULL or the int
+// that records a bounded wait that expired (the solve is then unfinished).
+// x <- L^-1 x.
+cudaError_t forward_solve(const double *A, long long ld, int N, double *x, int *sync, int *timeout_word,
+                          cudaStream_t s);
+// w = L^-T y (y strided; w may be y's storage when ystride == 1).
 cudaError_t backward_solve(const double *A, long long ld, int N, const double *y, long long ystride, double *w,
-                           cudaStream_t s);
+                           int *sync, int *timeout_word, cudaStream_t s);
 // z = L e (lower-triangular matrix-vector product).
 cudaError_t launch_trmv_lower(const double *A, long long ld, int N, const double *e, double *z, cudaStream_t s);
 
 // ---- refine.cu ------------------------------------------------------------
-cudaError_t forward_solve(const double *A, long long ld, int N, double *x, cudaStream_t s);
 size_t refine_workspace_bytes(int N);
 // x = Sigma^-1 z by FP64 iterative refinement with the factor in A and the
 // lower triangle of Sigma in S; writes l, log|Sigma|, z'x to res.
@@ -223,8 +229,6 @@ cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, cons
                        size_t ws_bytes, void *arena_host, DevStatus *st, DevStatus *h_st, cudaStream_t s);
 cudaError_t tlr_solve(const TlrFactor &F, double *x, bool transpose, void *ws, void *arena_host, cudaStream_t s);
 cudaError_t tlr_reduce(const TlrFactor &F, const double *y, const DevStatus *st, DevResults *res, cudaStream_t s);
-cudaError_t backward_solve(const double *A, long long ld, int N, const double *y, long long ystride, double *w,
-                           cudaStream_t s);
 
 // ---- batch.cu -------------------------------------------------------------
 size_t batch_desc_bytes();

@@ -6,50 +6,14 @@
 // Then Z' Sigma^-1 Z = Z' x, and the cokriging weights of Eq. 3 are x.
 // log|Sigma| is taken from the diagonal of L~ (FP64 diagonal tiles).
 //
-// Kernels: a blocked forward substitution (64 x 64 diagonal solves, then a
-// row-parallel update of the rest, coalesced along the column-major L), a
-// symmetric matrix-vector product from the lower triangle in 256 x 256 tiles
+// Kernels: the one-launch triangular solves of trsv.cu, a symmetric
+// matrix-vector product from the lower triangle in 256 x 256 tiles
 // with per-tile partial sums reduced in a fixed order (deterministic), and
 // small FP64 vector kernels.  All HBM-bound: each pass streams the lower
 // triangle once.
 #include "geo_internal.cuh"
 
 namespace {
-
-constexpr int FB = 64;
-
-// x[j0:j0+jb] <- L[j0:j0+jb, j0:j0+jb]^-1 x[j0:j0+jb]; one CTA.
-__global__ void __launch_bounds__(FB) k_trsv_l_diag(const double *__restrict__ A, long long ld, int j0, int jb,
-                                                   double *x) {
-    __shared__ double Ls[FB][FB + 1];
-    __shared__ double v[FB];
-    for (int c = 0; c < jb; ++c)
-        if (threadIdx.x < jb) Ls[c][threadIdx.x] = A[(long long)(j0 + c) * ld + j0 + threadIdx.x];
-    if (threadIdx.x < jb) v[threadIdx.x] = x[j0 + threadIdx.x];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int r = 0; r < jb; ++r) {
-            double t = v[r];
-            for (int c = 0; c < r; ++c) t -= Ls[c][r] * v[c];
-            v[r] = t / Ls[r][r];
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < jb) x[j0 + threadIdx.x] = v[threadIdx.x];
-}
-
-// x[r] -= sum_{c < jb} L[r, j0 + c] x[j0 + c] for r in [j0 + jb, N).
-__global__ void __launch_bounds__(256) k_gemv_n_update(const double *__restrict__ A, long long ld, int N, int j0,
-                                                       int jb, double *x) {
-    __shared__ double xs[FB];
-    if (threadIdx.x < jb) xs[threadIdx.x] = x[j0 + threadIdx.x];
-    __syncthreads();
-    const int r = j0 + jb + blockIdx.x * 256 + threadIdx.x;
-    if (r >= N) return;
-    double t = 0.0;
-    for (int c = 0; c < jb; ++c) t += A[(long long)(j0 + c) * ld + r] * xs[c];
-    x[r] -= t;
-}
 
 constexpr int ST = 256;   // symv tile
 
@@ -157,25 +121,9 @@ __global__ void __launch_bounds__(1024) k_ir_reduce(const double *__restrict__ A
 
 }  // namespace
 
-cudaError_t forward_solve(const double *A, long long ld, int N, double *x, cudaStream_t s) {
-    for (int j0 = 0; j0 < N; j0 += FB) {
-        const int jb = min(FB, N - j0);
-        {
-            KScope ks(GEO_K_SOLVE, s, (double)jb * jb, 8.0 * jb * jb / 2.0);
-            k_trsv_l_diag<<<1, FB, 0, s>>>(A, ld, j0, jb, x);
-        }
-        const int rest = N - j0 - jb;
-        if (rest > 0) {
-            KScope ks(GEO_K_SOLVE, s, 2.0 * rest * jb, 8.0 * (double)rest * jb);
-            k_gemv_n_update<<<(rest + 255) / 256, 256, 0, s>>>(A, ld, N, j0, jb, x);
-        }
-    }
-    return cudaGetLastError();
-}
-
 size_t refine_workspace_bytes(int N) {
     const size_t T = ((size_t)N + ST - 1) / ST;
-    return sizeof(double) * (2 * T * (size_t)N + 4 * (size_t)N) + 1024;
+    return sizeof(double) * (2 * T * (size_t)N + 4 * (size_t)N) + 1024 + 64;   // + the solves' sync words
 }
 
 // x = Sigma^-1 z by iterative refinement; S = lower triangle of Sigma (copy),
@@ -188,7 +136,9 @@ cudaError_t refine_solve(const double *S, const double *A, long long ld, int N, 
     double *pcol = prow + (size_t)T * N;
     double *sy = pcol + (size_t)T * N;
     double *r = sy + N;
-    cudaError_t e = backward_solve(A, ld, N, y, ystride, x, s);
+    int *sync = (int *)(r + N);
+    int *tw = const_cast<int *>(&st->timeout);
+    cudaError_t e = backward_solve(A, ld, N, y, ystride, x, sync, tw, s);
     if (e != cudaSuccess) return e;
     for (int it = 0; it < iters; ++it) {
         {
@@ -197,8 +147,8 @@ cudaError_t refine_solve(const double *S, const double *A, long long ld, int N, 
             k_symv_reduce<<<(N + 255) / 256, 256, 0, s>>>(prow, pcol, N, T, sy);
             k_residual<<<(N + 255) / 256, 256, 0, s>>>(z, sy, N, r);
         }
-        if ((e = forward_solve(A, ld, N, r, s)) != cudaSuccess) return e;
-        if ((e = backward_solve(A, ld, N, r, 1, r, s)) != cudaSuccess) return e;
+        if ((e = forward_solve(A, ld, N, r, sync, tw, s)) != cudaSuccess) return e;
+        if ((e = backward_solve(A, ld, N, r, 1, r, sync, tw, s)) != cudaSuccess) return e;
         {
             KScope ks(GEO_K_AUX, s);
             k_axpy1<<<(N + 255) / 256, 256, 0, s>>>(x, r, N);

@@ -54,49 +54,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_loglik_reduce(const double *__r
     }
 }
 
-constexpr int BS = 64;   // backward-solve block
-
-// Solve L[j0:j0+jb, j0:j0+jb]' w = r (r = rhs segment, already updated); one CTA.
-__global__ void __launch_bounds__(BS) k_trsv_ut_diag(const double *__restrict__ A, long long ld, int j0, int jb,
-                                                    double *r, double *w) {
-    __shared__ double Ls[BS][BS + 1];   // Ls[c][r] = L[j0 + r, j0 + c]
-    __shared__ double x[BS];
-    for (int c = 0; c < jb; ++c) {
-        const int rr = threadIdx.x;
-        if (rr < jb) Ls[c][rr] = A[(long long)(j0 + c) * ld + j0 + rr];
-    }
-    if (threadIdx.x < jb) x[threadIdx.x] = r[j0 + threadIdx.x];
-    __syncthreads();
-    // L' is upper triangular: w_c = (x_c - sum_{k > c} L[k][c] w_k) / L[c][c], from the bottom
-    if (threadIdx.x == 0) {
-        for (int c = jb - 1; c >= 0; --c) {
-            double t = x[c];
-            for (int k = c + 1; k < jb; ++k) t -= Ls[c][k] * x[k];
-            x[c] = t / Ls[c][c];
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < jb) w[j0 + threadIdx.x] = x[threadIdx.x];
-}
-
-// r[c] -= sum_{k < jb} L[j0 + k, c] w[j0 + k] for c < j0: one warp per column.
-__global__ void __launch_bounds__(256) k_gemv_t_update(const double *__restrict__ A, long long ld, int j0, int jb,
-                                                       const double *__restrict__ w, double *r) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= j0) return;
-    const double *col = A + (long long)warp * ld + j0;
-    double t = 0.0;
-    for (int k = lane; k < jb; k += 32) t += col[k] * w[j0 + k];
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    if (lane == 0) r[warp] -= t;
-}
-
-__global__ void k_copy_strided(const double *__restrict__ in, long long stride, int N, double *out) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < N) out[k] = in[(long long)k * stride];
-}
-
 // z[i] = sum_{k <= i} L[i, k] e[k]; one thread per row, columns in chunks staged in shared memory.
 __global__ void __launch_bounds__(256) k_trmv_lower(const double *__restrict__ A, long long ld, int N,
                                                    const double *__restrict__ e, double *z) {
@@ -122,32 +79,6 @@ cudaError_t launch_loglik_reduce(const double *A, long long ld, int N, const dou
                                  const DevStatus *st, DevResults *res, cudaStream_t s) {
     KScope ks(GEO_K_REDUCE, s, 3.0 * N, 16.0 * N);
     k_loglik_reduce<<<1, RED_THREADS, 0, s>>>(A, ld, N, y, ystride, st, res);
-    return cudaGetLastError();
-}
-
-// w = L^-T y.  r (the running right-hand side) lives in w's buffer: w is
-// overwritten block by block from the bottom, the blocks above still hold
-// the partially updated right-hand side.
-cudaError_t backward_solve(const double *A, long long ld, int N, const double *y, long long ystride, double *w,
-                           cudaStream_t s) {
-    if (N <= 0) return cudaSuccess;
-    {
-        KScope ks(GEO_K_AUX, s);
-        k_copy_strided<<<(N + 255) / 256, 256, 0, s>>>(y, ystride, N, w);
-    }
-    const int nblk = (N + BS - 1) / BS;
-    for (int b = nblk - 1; b >= 0; --b) {
-        const int j0 = b * BS, jb = min(BS, N - j0);
-        {
-            KScope ks(GEO_K_SOLVE, s, (double)jb * jb, 8.0 * jb * jb / 2.0);
-            k_trsv_ut_diag<<<1, BS, 0, s>>>(A, ld, j0, jb, w, w);
-        }
-        if (j0 > 0) {
-            const int threads = j0 * 32;
-            KScope ks(GEO_K_SOLVE, s, 2.0 * j0 * jb, 8.0 * (double)j0 * jb);
-            k_gemv_t_update<<<(threads + 255) / 256, 256, 0, s>>>(A, ld, j0, jb, w, w);
-        }
-    }
     return cudaGetLastError();
 }
 

@@ -570,6 +570,7 @@ cudaError_t tlr_solve(const TlrFactor &F, double *x, bool transpose, void *ws, v
     arena.dev = (uint8_t *)(((uintptr_t)arena.dev + 255) & ~(uintptr_t)255);
     arena.host = (uint8_t *)arena_host;
     arena.cap = TLR_ARENA_BYTES;
+    int *sync = (int *)(arena.dev + TLR_ARENA_BYTES);   // the diagonal solves' sync words
     cudaError_t e = cudaSuccess;
     for (int step = 0; step < T; ++step) {
         const int i = transpose ? T - 1 - step : step;
@@ -603,9 +604,10 @@ cudaError_t tlr_solve(const TlrFactor &F, double *x, bool transpose, void *ws, v
         }
         const double *Dii = F.D + (size_t)i * nb * nb;
         if (transpose) {
-            if ((e = backward_solve(Dii, nb, mt(i), x + (size_t)i * nb, 1, x + (size_t)i * nb, s))) return e;
+            if ((e = backward_solve(Dii, nb, mt(i), x + (size_t)i * nb, 1, x + (size_t)i * nb, sync, nullptr, s)))
+                return e;
         } else {
-            if ((e = forward_solve(Dii, nb, mt(i), x + (size_t)i * nb, s))) return e;
+            if ((e = forward_solve(Dii, nb, mt(i), x + (size_t)i * nb, sync, nullptr, s))) return e;
         }
         if (arena.used > TLR_ARENA_BYTES / 2) {
             if ((e = cudaStreamSynchronize(s))) return e;
@@ -618,7 +620,7 @@ cudaError_t tlr_solve(const TlrFactor &F, double *x, bool transpose, void *ws, v
 size_t tlr_solve_workspace_bytes(int N, int nb, int kmax) {
     (void)kmax;
     const size_t T = ((size_t)N + nb - 1) / nb;
-    return sizeof(double) * (T * (size_t)nb + (size_t)nb * T) + TLR_ARENA_BYTES + 512;
+    return sizeof(double) * (T * (size_t)nb + (size_t)nb * T) + TLR_ARENA_BYTES + 512 + 64;
 }
 
 cudaError_t tlr_reduce(const TlrFactor &F, const double *y, const DevStatus *st, DevResults *res, cudaStream_t s) {
