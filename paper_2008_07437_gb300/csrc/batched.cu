@@ -5,7 +5,11 @@
 // kernel maps one problem (or one 64 x 64 tile of it) to one CTA.
 #include <math.h>
 
+#include <cooperative_groups.h>
+
 #include "geo_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -239,6 +243,130 @@ __global__ void __launch_bounds__(LA_THREADS) k_jacobi_svd(const SvdDesc *__rest
     }
 }
 
+// ---- the same one-sided Jacobi SVD on a cluster of JC CTAs ------------------
+// One FP64 SM needs ~13 ms per sweep at r = 232, so the SVD of a tile is
+// spread over a thread-block cluster: CTA c holds rows [c rs, (c+1) rs) of M
+// and V in shared memory.  Each round (r/2 disjoint pairs, the same circle
+// order), two threads per pair form partial (alpha, beta, gamma) over the
+// CTA's rows, the partials are exchanged through distributed shared memory
+// (one cluster barrier, double-buffered), every CTA sums them in rank order
+// (so every CTA takes the same rotation decisions, bit for bit) and rotates
+// its own rows.  Column norms are reduced the same way at the end.  r <= 256.
+constexpr int JC = 8, JT = 256, JR_MAX = 256, JLD = JR_MAX / JC + 1;
+
+size_t jacobi_cl_smem(int r) {
+    return sizeof(double) * (2 * (size_t)r * JLD + 2 * 3 * (JR_MAX / 2) + JR_MAX);
+}
+
+__global__ void __launch_bounds__(JT, 1) k_jacobi_svd_cl(const SvdDesc *__restrict__ d, int count, int max_sweeps) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int tile = blockIdx.x / JC;
+    if (tile >= count) return;   // uniform over the cluster
+    const int rank = (int)cluster.block_rank();
+    extern __shared__ double sm[];
+    const SvdDesc s = d[tile];
+    const int r = s.r;
+    const long long ld = s.ld;
+    const int rs = (r + JC - 1) / JC;
+    const int row0 = rank * rs, nrow = max(0, min(rs, r - row0));
+    double *Ms = sm;                          // [r][JLD], rows of this CTA
+    double *Vs = Ms + (size_t)r * JLD;
+    double *P = Vs + (size_t)r * JLD;         // [2][3][JR_MAX / 2]
+    double *nrm = P + 2 * 3 * (JR_MAX / 2);   // [JR_MAX]
+    for (int e = threadIdx.x; e < r * rs; e += JT) {
+        const int c = e / rs, i = e % rs;
+        Ms[c * JLD + i] = (i < nrow) ? s.M[(long long)c * ld + row0 + i] : 0.0;
+        Vs[c * JLD + i] = (i < nrow && row0 + i == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const int rr = r + (r & 1), npairs = rr / 2;
+    const int p = threadIdx.x >> 1, half = threadIdx.x & 1;
+    const double skip2 = s.skip * s.skip;
+    int buf = 0;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        int rotated = 0;
+        for (int round = 0; round < rr - 1; ++round) {
+            int a = -1, b = -1;
+            double al = 0.0, be = 0.0, ga = 0.0;
+            if (p < npairs) {
+                a = (p == 0) ? 0 : 1 + (p - 1 + round) % (rr - 1);
+                b = 1 + (rr - 2 - p + round) % (rr - 1);
+                if (a >= r || b >= r || a == b) {
+                    a = -1;
+                } else if (a > b) {
+                    const int t = a;
+                    a = b;
+                    b = t;
+                }
+                if (a >= 0)
+                    for (int i = half; i < nrow; i += 2) {
+                        const double x = Ms[a * JLD + i], y = Ms[b * JLD + i];
+                        al = fma(x, x, al);
+                        be = fma(y, y, be);
+                        ga = fma(x, y, ga);
+                    }
+            }
+            al += __shfl_xor_sync(0xffffffffu, al, 1);
+            be += __shfl_xor_sync(0xffffffffu, be, 1);
+            ga += __shfl_xor_sync(0xffffffffu, ga, 1);
+            double *Pb = P + buf * 3 * (JR_MAX / 2);
+            if (half == 0 && p < npairs) {
+                Pb[p] = al;
+                Pb[JR_MAX / 2 + p] = be;
+                Pb[JR_MAX + p] = ga;
+            }
+            cluster.sync();
+            if (a >= 0) {
+                double A = 0.0, B = 0.0, G = 0.0;
+                for (int c = 0; c < JC; ++c) {
+                    const double *rp = cluster.map_shared_rank(Pb, c);
+                    A += rp[p];
+                    B += rp[JR_MAX / 2 + p];
+                    G += rp[JR_MAX + p];
+                }
+                if (!(A < skip2 && B < skip2) && !(fabs(G) <= 1e-13 * sqrt(A * B) || G == 0.0)) {
+                    const double zeta = (B - A) / (2.0 * G);
+                    const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+                    for (int i = half; i < nrow; i += 2) {
+                        const double x = Ms[a * JLD + i], y = Ms[b * JLD + i];
+                        Ms[a * JLD + i] = cs * x - sn * y;
+                        Ms[b * JLD + i] = sn * x + cs * y;
+                        const double u = Vs[a * JLD + i], v = Vs[b * JLD + i];
+                        Vs[a * JLD + i] = cs * u - sn * v;
+                        Vs[b * JLD + i] = sn * u + cs * v;
+                    }
+                    rotated = 1;
+                }
+            }
+            __syncthreads();   // rotated columns before the next round's partials
+            buf ^= 1;          // the other partial buffer: free since this round's barrier
+        }
+        if (!__syncthreads_or(rotated)) break;   // the same decision in every CTA
+    }
+    // singular values = column norms
+    for (int c = threadIdx.x; c < r; c += JT) {
+        double t = 0.0;
+        for (int i = 0; i < nrow; ++i) t = fma(Ms[c * JLD + i], Ms[c * JLD + i], t);
+        nrm[c] = t;
+    }
+    cluster.sync();
+    if (rank == 0)
+        for (int c = threadIdx.x; c < r; c += JT) {
+            double t = 0.0;
+            for (int q = 0; q < JC; ++q) t += cluster.map_shared_rank(nrm, q)[c];
+            s.sigma[c] = sqrt(t);
+        }
+    for (int e = threadIdx.x; e < r * rs; e += JT) {
+        const int c = e / rs, i = e % rs;
+        if (i < nrow) {
+            s.M[(long long)c * ld + row0 + i] = Ms[c * JLD + i];
+            s.V[(long long)c * ld + row0 + i] = Vs[c * JLD + i];
+        }
+    }
+    cluster.sync();   // no CTA leaves while another still reads its shared memory
+}
+
 // ---- Gaussian test matrices: counter-based SplitMix64 -> Box-Muller ---------
 __device__ __forceinline__ unsigned long long splitmix(unsigned long long z) {
     z += 0x9E3779B97F4A7C15ull;
@@ -274,11 +402,30 @@ cudaError_t launch_house_qr(const QrDesc *d_desc, int count, cudaStream_t s, dou
     return cudaGetLastError();
 }
 
-cudaError_t launch_jacobi_svd(const SvdDesc *d_desc, int count, int max_sweeps, cudaStream_t s, double flops) {
+cudaError_t launch_jacobi_svd(const SvdDesc *d_desc, int count, int max_sweeps, int rmax, cudaStream_t s,
+                              double flops) {
     if (count <= 0) return cudaSuccess;
     KScope ks(GEO_K_TLR, s, flops, 0.0);
-    k_jacobi_svd<<<count, LA_THREADS, 0, s>>>(d_desc, count, max_sweeps);
-    return cudaGetLastError();
+    if (rmax > JR_MAX) {
+        k_jacobi_svd<<<count, LA_THREADS, 0, s>>>(d_desc, count, max_sweeps);
+        return cudaGetLastError();
+    }
+    const size_t smem = jacobi_cl_smem(rmax);
+    cudaError_t e = cudaFuncSetAttribute(k_jacobi_svd_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)count * JC);
+    cfg.blockDim = dim3(JT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = JC;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_jacobi_svd_cl, d_desc, count, max_sweeps);
 }
 
 cudaError_t launch_gaussian(double *O, long long n, unsigned long long seed, cudaStream_t s) {

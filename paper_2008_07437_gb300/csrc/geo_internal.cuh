@@ -168,7 +168,9 @@ struct SvdDesc {            // one-sided Jacobi SVD of M (r x r): M <- M V, V, s
 };
 cudaError_t launch_bgemm(const GemmDesc *d_desc, int count, int max_tiles, cudaStream_t s, double flops);
 cudaError_t launch_house_qr(const QrDesc *d_desc, int count, cudaStream_t s, double flops);
-cudaError_t launch_jacobi_svd(const SvdDesc *d_desc, int count, int max_sweeps, cudaStream_t s, double flops);
+// rmax: the largest r of the batch (the cluster kernel serves r <= 256).
+cudaError_t launch_jacobi_svd(const SvdDesc *d_desc, int count, int max_sweeps, int rmax, cudaStream_t s,
+                              double flops);
 cudaError_t launch_gaussian(double *O, long long n, unsigned long long seed, cudaStream_t s);
 
 // ---- tlr.cu ---------------------------------------------------------------

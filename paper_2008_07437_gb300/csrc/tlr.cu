@@ -409,7 +409,7 @@ cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, cons
             }
             SvdDesc *sv = push(arena, dsv, s, &e);
             TCK(e);
-            TCK(launch_jacobi_svd(sv, (int)dsv.size(), 30, s, 3.0 * 12.0 * (double)dsv.size() * r * r * r));
+            TCK(launch_jacobi_svd(sv, (int)dsv.size(), 30, r, s, 3.0 * 12.0 * (double)dsv.size() * r * r * r));
             // singular values to the host
             for (size_t t = 0; t < todo.size(); ++t) {
                 const int q = todo[t];
