@@ -134,10 +134,11 @@ WORKLOADS = {
                                        ThetaSpec((1.0, 1.0), 0.1, (0.5, 1.0), (0.7,)),
                                        nb=1024, loc_seed=1002, z_seed=2002,
                                        extra={"prec": 1, "band": 4, "lowp": 0, "refine_iters": 2}),
-    # 60,000 locations, trivariate (N = 180,000), tile low-rank.
+    # 60,000 locations, trivariate (N = 180,000), tile low-rank at accuracy 1e-9, rank <= 200.
     "trivariate-n60000-tlr": Workload("trivariate-n60000-tlr", 60000,
                                       ThetaSpec((1.0, 1.0, 1.0), 0.05, (0.5, 1.0, 1.5), (0.5, 0.3, 0.4)),
-                                      nb=1800, loc_seed=1003, z_seed=2003),
+                                      nb=1800, loc_seed=1003, z_seed=2003,
+                                      extra={"prec": 2, "tlr_tol": 1e-9, "tlr_kmax": 200}),
 }
 
 
