@@ -84,7 +84,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bivariate-n20000", choices=sorted(inputs.WORKLOADS) + ["serving"])
+    ap.add_argument("--workload", default="bivariate-n20000",
+                    choices=sorted(inputs.WORKLOADS) + ["serving", "batch"])
     ap.add_argument("--n", type=int, default=0, help="override n (profiling runs on small cases only)")
     ap.add_argument("--n-pred", type=int, default=-1)
     ap.add_argument("--nb", type=int, default=0)
@@ -98,6 +99,8 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=200.0, help="serving: device-memory budget (GiB)")
     ap.add_argument("--serving-prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-tune", action="store_true", help="serving: skip the tile-size autotuner")
+    ap.add_argument("--batch-count", type=int, default=512, help="batch: problems per call")
+    ap.add_argument("--mle", type=int, default=0, help="run this many Nelder-Mead steps instead of evaluations")
     return ap.parse_args()
 
 
@@ -259,7 +262,8 @@ def config_json(w, args):
             "l2": ("inputs larger than L2: every tile column (%.1f GB) is regenerated every step" % (
                 8.0 * p * w.n * w.nb / 1e9) if w.extra.get("prec") == 2 else
                 "inputs larger than L2: the %.1f GB matrix is regenerated every step" % (8.0 * (p * w.n) ** 2 / 1e9)),
-            "z": "white noise (cost does not depend on Z)" if w.extra.get("prec") == 2 else "Z = L e, joint draw"}
+            "z": ("white noise (cost does not depend on Z)" if w.extra.get("prec") == 2 and not args.mle
+                  else "Z = L e, joint draw")}
 
 
 # --------------------------------------------------------------------------
@@ -303,16 +307,19 @@ def run_ours(args):
     d_all = torch.as_tensor(allp, device=dev)
     d_e = torch.as_tensor(e, device=dev)
     d_zall = torch.empty(p * len(allp), dtype=torch.float64, device=dev)
-    if tlr:
+    if tlr and not args.mle:
         d_zall.copy_(d_e)
     else:
-        geo.geo_simulate(ctx, d_all, d_e, theta, d_zall, o)
+        geo.geo_simulate(ctx, d_all, d_e, theta, d_zall, geo.opts(nb=960) if tlr else o)
     d_locs = torch.as_tensor(obs, device=dev).contiguous()
     d_pred = torch.as_tensor(pred, device=dev).contiguous()
     d_z = d_zall[:N].clone()
     z_true_pred = d_zall[N:].cpu().numpy()
     d_zhat = torch.empty(p * w.n_pred, dtype=torch.float64, device=dev)
     del d_all, d_e, d_zall
+
+    if args.mle:
+        return run_mle(args, w, ctx, d_locs, d_z, theta, o, dev)
 
     def step():
         ll, fac = geo.geo_loglik(ctx, d_locs, d_z, theta, o, keep=True)
@@ -657,6 +664,158 @@ def run_serving(args):
     return 0
 
 
+# --------------------------------------------------------------------------
+# MLE: Nelder-Mead steps (Sec. 5.1) on the workload's data and form
+# --------------------------------------------------------------------------
+def run_mle(args, w, ctx, d_locs, d_z, theta, o, dev):
+    import torch
+
+    import paper_2008_07437_gb300 as geo
+    spec = w.theta
+    # start: a x 1.3, nu x 0.9, sigma^2 x 1.1, beta x 0.8
+    th0 = geo.Theta(tuple(1.1 * v for v in spec.sigma2), 1.3 * spec.a, tuple(0.9 * v for v in spec.nu),
+                    tuple(0.8 * v for v in spec.beta) if spec.p > 1 else None)
+    st = geo.geo_mle_init(th0)
+    ll_true, _ = geo.geo_loglik(ctx, d_locs, d_z, theta, o)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    t0 = time.perf_counter()
+    traj = []
+    for _ in range(args.mle):
+        geo.geo_mle_step(ctx, st, d_locs, d_z, o)
+        traj.append(geo.geo_mle_best(st)[1])
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    clk = clocks.stop()
+    best, ll = geo.geo_mle_best(st)
+    out = {"metric": "MLE wall time", "value": t, "unit": "s", "n_gpus": 1, "steps": args.mle, "warmup": 0,
+           "ms_per_step": 1e3 * t / args.mle, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic", "config": config_json(w, args),
+           "evals": st.evals, "evals_per_s": st.evals / t, "loglik_at_truth": ll_true,
+           "best_loglik": ll, "best_loglik_by_step": traj,
+           "best_theta": {"sigma2": list(best.sigma2), "a": best.a, "nu": list(best.nu),
+                          "beta": [float(b) for b in np.asarray(best.beta).ravel()]},
+           "start_theta": {"sigma2": list(th0.sigma2), "a": th0.a, "nu": list(th0.nu)},
+           "clocks": clk}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    return 0
+
+
+# --------------------------------------------------------------------------
+# batch: many small uneven likelihoods per call
+# --------------------------------------------------------------------------
+def run_batch(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2008_07437_gb300 as geo
+    from paper_2008_07437_gb300 import build as gbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0 or world == 1:
+        gbuild.build()
+    if world > 1:
+        dist.barrier()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    probs = inputs.batch_problems(args.batch_count, seed=3100 + rank)
+    ctx = geo.geo_create(dev.index)
+    # setup (untimed): locations and Z = L e for every problem
+    items, host = [], []
+    for n, th_spec, ls, zs in probs:
+        th = geo.Theta.from_spec(th_spec)
+        locs = inputs.jittered_grid(n, ls)
+        dl = torch.as_tensor(locs, device=dev)
+        de = torch.as_tensor(inputs.normals(zs, 2 * n), device=dev)
+        dz = torch.empty(2 * n, dtype=torch.float64, device=dev)
+        geo.geo_simulate(ctx, dl, de, th, dz, geo.opts(nb=128))
+        items.append((dl, dz, th))
+        host.append((locs, dz.cpu().numpy()))
+    Ntot3 = sum((2.0 * n) ** 3 / 3.0 for n, _, _, _ in probs)
+    for _ in range(args.warmup):
+        geo.geo_loglik_batch(ctx, items)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index)
+    geo.geo_profile_enable(ctx, True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        vals, info = geo.geo_loglik_batch(ctx, items)
+    ev1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = geo.geo_profile_read(ctx)
+    geo.geo_profile_enable(ctx, False)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    # the same problems one geo_loglik call at a time (context, not the metric)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    single = [geo.geo_loglik(ctx, dl, dz, th, geo.opts(nb=128))[0] for dl, dz, th in items]
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t0
+    worst = max(abs(a - b) / abs(b) for a, b in zip(vals, single))
+    # end to end: host inputs copied every step, results read back
+    e2e = None
+    if not args.no_e2e:
+        pinned = [(torch.as_tensor(l).pin_memory(), torch.as_tensor(z).pin_memory()) for l, z in host]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for (hl, hz), (dl, dz, _) in zip(pinned, items):
+                dl.copy_(hl, non_blocking=True)
+                dz.copy_(hz, non_blocking=True)
+            geo.geo_loglik_batch(ctx, items)   # returns host results (synchronises)
+        t_e2e = time.perf_counter() - t0
+        e2e = {"value": world * args.steps * len(items) / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": sum(8 * 4 * n for n, _, _, _ in probs),
+               "d2h_bytes_per_step": 8 * len(items)}
+    launches = sum(v["launches"] for v in prof.values())
+    dom = max(("gemm", "covgen", "potrf", "trsm"), key=lambda k: prof[k]["ms"])
+    bound, peak, peak_src = class_roofline("gemm")
+    tflops = (Ntot3 * args.steps) / (ms * 1e-3) / 1e12
+    out = {"metric": METRIC, "value": world * args.steps * len(items) / (ms * 1e-3), "unit": UNIT,
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "batch", "problems": len(items), "p": 2, "n_range": [50, 1000],
+                      "theta_box": "a in [0.03, 0.2], nu_i in [0.5, 1.5], beta in [-0.7, 0.7], sigma^2_i in [0.5, 2]",
+                      "form": "dense FP64, one launch sequence per panel step for the whole batch, CUDA graph replay",
+                      "l2": "inputs larger than L2: %.1f GB of matrices regenerated every step" % (
+                          sum(8.0 * (2 * n) ** 2 for n, _, _, _ in probs) / 1e9)},
+           "dense_equivalent_tflops": tflops,
+           "roofline": {"bound": bound, "kernel": "whole batch (N^3/3 per problem over the call's time)",
+                        "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+                        "peak_source": peak_src, "traffic": None},
+           "gpu_launches": launches, "dominant_class": dom,
+           "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
+           "single_call_evals_s": len(items) / t_single, "max_rel_diff_vs_single": worst,
+           "clocks": clk, "e2e": e2e}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_serving_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -679,6 +838,11 @@ def main():
     args = parse()
     if args.workload == "serving":
         return run_serving_reference(args) if args.impl == "reference" else run_serving(args)
+    if args.workload == "batch":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "batch mode: use the default workload's reference arm"}))
+            return 0
+        return run_batch(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

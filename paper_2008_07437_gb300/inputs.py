@@ -200,3 +200,18 @@ def serving_stream(count: int, rate: float = 200.0, seed: int = 3000, n_lo: int 
     for r in last_use.values():
         r.release = True
     return out
+
+
+def batch_problems(count: int, seed: int = 3100, n_lo: int = 50, n_hi: int = 1000) -> list[tuple]:
+    """count bivariate likelihood problems of uneven size for the batched
+    path: (n, theta, location seed, noise seed) with n uniform in [n_lo, n_hi]
+    and theta drawn from the serving box (a in [0.03, 0.2], nu_i in [0.5, 1.5],
+    beta in [-0.7, 0.7], sigma^2_i in [0.5, 2])."""
+    U = uniforms(seed, 8 * count).reshape(count, 8)
+    out = []
+    for k in range(count):
+        u = U[k]
+        th = ThetaSpec(sigma2=(0.5 + 1.5 * u[1], 0.5 + 1.5 * u[2]), a=0.03 + 0.17 * u[3],
+                       nu=(0.5 + u[4], 0.5 + u[5]), beta=(-0.7 + 1.4 * u[6],))
+        out.append((n_lo + int(u[0] * (n_hi - n_lo + 1)), th, seed * 10 + 2 * k, seed * 10 + 2 * k + 1))
+    return out
