@@ -16,6 +16,8 @@
 //   * the extra right-hand-side row N (Z', becoming (L^-1 Z)') is solved and
 //     updated in FP64 throughout.
 #include <cuda.h>
+
+#include <algorithm>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 
@@ -259,6 +261,16 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    }
+    return n;
+}
+
 EncodeTiledFn encode_fn() {
     static EncodeTiledFn fn = nullptr;
     if (!fn) {
@@ -414,15 +426,14 @@ cudaError_t chol_mixed_factor(double *A, long long ld, int N, int nrows, int nb,
             tc::TcArgs a;
             a.C = A;
             a.ldc = ld;
-            a.r0 = t0;
-            a.c0 = t0;
-            a.m = R;
-            a.n = R;
+            a.N = N;
             a.prow0 = t0;
             a.K = nb;   // columns jb..nb of the low-precision copy are zero
             a.nb = nb;
-            a.dlo = band + 1;
-            a.dhi = 1 << 30;
+            a.band = band;
+            a.T0 = t0 / nb;
+            const long long far_rows = std::max(0, (N - 1) / nb - a.T0 - band);
+            a.ntiles = far_rows * (far_rows + 1) / 2 * (long long)(nb / tc::BM) * (nb / tc::BM);
             a.inv_scale = inv_scale;
             a.terms = terms;
             a.st = st;
@@ -432,9 +443,9 @@ cudaError_t chol_mixed_factor(double *A, long long ld, int N, int nrows, int nb,
                 const double hi = min(N, (I + 1) * nb) - I * nb;
                 for (int J = T0; J < I - band; ++J) ent += hi * nb;
             }
-            dim3 grid((R + tc::BM - 1) / tc::BM, (R + tc::BN - 1) / tc::BN);
+            const int grid = (int)std::min<long long>(a.ntiles, num_sms());
             KScope ks(GEO_K_TCGEMM, s, 2.0 * jb * ent * (terms == 2 ? 3 : 1), 16.0 * ent + 2.0 * terms * (double)R * jb);
-            tc::k_tc_update<<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(map, map_lo, a, idesc);
+            if (grid > 0) tc::k_tc_update<<<grid, tc::THREADS_P, tc::SMEM_BYTES, s>>>(map, map_lo, a, idesc);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         // 4c. right-hand-side rows in FP64

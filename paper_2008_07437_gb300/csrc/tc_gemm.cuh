@@ -6,18 +6,24 @@
 // accumulates hi hi' + hi lo' + lo hi' (three MMAs per K step): about 22
 // significant bits per operand instead of 11.
 //
-// Per CTA: one 128 x 128 output tile, K in 64-wide blocks.
+// Persistent: one CTA per SM walks a compact list of the 128 x 128 output
+// tiles of the far class (nb-tile distance > band), K in 64-wide blocks.
 //   warp 0 (one lane): TMA producer, 3-stage ring of (A, B) tiles (hi, and lo
-//                      with two terms), 128 x 64 FP16 each, 128-byte swizzle;
-//   warp 1: allocates 128 TMEM columns; one lane issues tcgen05.mma
-//           (M = 128, N = 128, K = 16, kind::f16, FP32 accumulate) and
-//           commits each stage back to the producer;
-//   warps 2-5: epilogue, tcgen05.ld of the accumulator (warp w reads TMEM
-//           lanes 32 (w % 4) .. + 31 = tile rows), scale, FP64 read-modify-write
-//           of C with stores contiguous across each warp.
+//                      with two terms), 128 x 64 FP16 each, 128-byte swizzle,
+//                      running ahead across tile boundaries;
+//   warp 1: allocates 256 TMEM columns (two 128-column accumulators); one
+//           lane issues tcgen05.mma (M = 128, N = 128, K = 16, kind::f16,
+//           FP32 accumulate) into the accumulator of the tile's parity and
+//           commits each stage back to the producer and each finished tile
+//           to the epilogue;
+//   warps 2-9: epilogue, tcgen05.ld of the accumulator (warp w reads TMEM
+//           lanes 32 (w % 4) .. + 31 = tile rows, half of the columns each),
+//           scale, FP64 read-modify-write of C with stores contiguous across
+//           each warp; then it frees the accumulator, so the epilogue of one
+//           tile overlaps the MMAs of the next.
 // Every wait on an mbarrier is bounded by a clock budget; on expiry the
-// thread records an error code in the status word and the CTA drains, frees
-// its TMEM and returns.
+// thread records an error code in the status word and the CTA drains (its
+// copies and MMAs in flight), frees its TMEM and returns.
 #pragma once
 
 #include <cuda.h>
@@ -32,8 +38,6 @@ constexpr int TILE_A_BYTES = BM * BK * 2;
 constexpr int TILE_B_BYTES = BN * BK * 2;
 constexpr int TILE_BYTES = TILE_A_BYTES;                   // A and B tiles have the same shape
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;                // A_hi, B_hi, A_lo, B_lo
-constexpr int THREADS = 192;
-constexpr int TMEM_COLS = 128;
 constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024;   // + alignment slack
 constexpr long long WAIT_CYCLES = 4000000000LL;                        // ~2 s at 2 GHz
 
@@ -126,38 +130,49 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// Which 128 x 128 output tiles a launch computes: the grid spans the
-// 128-tiles (ti, tj) of rows [r0, r0 + m) x cols [c0, c0 + n); a tile runs
-// when its nb-tile distance |I - J| (I = global row / nb) lies in [dlo, dhi].
+// The far tiles of one trailing update: nb-tiles (I, J) with I - J > band,
+// T0 <= J, I <= T1 (T0 = t0 / nb), enumerated row by row (u = I - T0 - band - 1,
+// v = J - T0 <= u), each split into (nb / 128)^2 output tiles of 128 x 128.
 struct TcArgs {
     double *C;
     long long ldc;
-    int r0, c0, m, n;      // output region (global indices)
+    int N;                 // matrix order: rows and cols >= N are outside
     int prow0;             // global row of panel row 0 (A / B operand row = global - prow0)
     int K;                 // panel width (multiple of 64)
-    int nb, dlo, dhi;      // class filter
+    int nb, band, T0;      // class geometry
+    long long ntiles;      // output tiles in the list
     const double *inv_scale;   // per panel row
     int terms;                 // 1: hi only, 2: hi + lo
     DevStatus *st;
 };
 
-__global__ void __launch_bounds__(THREADS, 1)
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS_P = 64 + 32 * EPI_WARPS;
+constexpr int TMEM_COLS_P = 2 * BN;
+
+// Global row / col of output tile L; false if it lies beyond the matrix.
+__device__ __forceinline__ bool tile_coords(const TcArgs &a, long long L, int *gr, int *gc) {
+    const int per = a.nb / BM;                       // 128-tiles per nb along each side
+    const long long sub = L % ((long long)per * per), f = L / ((long long)per * per);
+    long long u = (long long)((sqrt(8.0 * (double)f + 1.0) - 1.0) * 0.5);
+    while ((u + 1) * (u + 2) / 2 <= f) ++u;
+    while (u * (u + 1) / 2 > f) --u;
+    const long long v = f - u * (u + 1) / 2;
+    const int I = a.T0 + a.band + 1 + (int)u, J = a.T0 + (int)v;
+    *gr = I * a.nb + (int)(sub / per) * BM;
+    *gc = J * a.nb + (int)(sub % per) * BN;
+    return *gr < a.N;
+}
+
+__global__ void __launch_bounds__(THREADS_P, 1)
     k_tc_update(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap map_lo,
                 const TcArgs args, const uint32_t idesc) {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], acc_bar;
+    __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], acc_full[2], acc_empty[2], drain_bar;
     __shared__ uint32_t tmem_slot;
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int gr = args.r0 + blockIdx.x * BM;   // global row of the tile
-    const int gc = args.c0 + blockIdx.y * BN;   // global col of the tile
-    // class filter (uniform across the CTA; decided before any barrier or TMEM use)
-    {
-        const int I = gr / args.nb, J = gc / args.nb;
-        const int I2 = (gr + BM - 1) / args.nb, J2 = (gc + BN - 1) / args.nb;
-        const int dmin = I - J2, dmax = I2 - J;
-        if (dmin < args.dlo || dmax > args.dhi || args.st->info) return;
-    }
+    if (args.st->info) return;   // uniform: an earlier step failed
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int nk = args.K / BK;
 
@@ -166,13 +181,17 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
-        mbar_init(&acc_bar, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], EPI_WARPS);
+        }
+        mbar_init(&drain_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(TMEM_COLS)
+                     "r"(TMEM_COLS_P)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -184,93 +203,131 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            const int arow = gr - args.prow0, brow = gc - args.prow0;
-            int issued = 0, consumed_ok = 1;
-            for (int kb = 0; kb < nk; ++kb) {
-                const int s = kb % STAGES;
-                if (kb >= STAGES) {
-                    if (!mbar_wait(&empty_bar[s], ((kb / STAGES) & 1) ^ 1, tword, 1)) {
-                        consumed_ok = 0;
+            long long g = 0;   // stages issued
+            bool ok = true;
+            for (long long L = blockIdx.x; L < args.ntiles && ok; L += gridDim.x) {
+                int gr, gc;
+                if (!tile_coords(args, L, &gr, &gc)) continue;
+                const int arow = gr - args.prow0, brow = gc - args.prow0;
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const int s = (int)(g % STAGES);
+                    if (g >= STAGES && !mbar_wait(&empty_bar[s], (uint32_t)(((g / STAGES) & 1) ^ 1), tword, 1)) {
+                        ok = false;
                         break;
                     }
+                    uint8_t *sa = smem + (size_t)s * STAGE_BYTES;
+                    uint8_t *sb = sa + TILE_BYTES;
+                    mbar_arrive_expect_tx(&full_bar[s], (args.terms == 2 ? 4 : 2) * TILE_BYTES);
+                    tma_load_2d(&map, &full_bar[s], sa, kb * BK, arow);
+                    tma_load_2d(&map, &full_bar[s], sb, kb * BK, brow);
+                    if (args.terms == 2) {
+                        tma_load_2d(&map_lo, &full_bar[s], sa + 2 * TILE_BYTES, kb * BK, arow);
+                        tma_load_2d(&map_lo, &full_bar[s], sb + 2 * TILE_BYTES, kb * BK, brow);
+                    }
                 }
-                uint8_t *sa = smem + (size_t)s * STAGE_BYTES;
-                uint8_t *sb = sa + TILE_BYTES;
-                mbar_arrive_expect_tx(&full_bar[s], (args.terms == 2 ? 4 : 2) * TILE_BYTES);
-                tma_load_2d(&map, &full_bar[s], sa, kb * BK, arow);
-                tma_load_2d(&map, &full_bar[s], sb, kb * BK, brow);
-                if (args.terms == 2) {
-                    tma_load_2d(&map_lo, &full_bar[s], sa + 2 * TILE_BYTES, kb * BK, arow);
-                    tma_load_2d(&map_lo, &full_bar[s], sb + 2 * TILE_BYTES, kb * BK, brow);
-                }
-                ++issued;
             }
-            if (!consumed_ok) {
-                // drain: wait (bounded) for every copy this thread issued to land
-                for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-                    mbar_wait(&full_bar[kb % STAGES], (kb / STAGES) & 1, tword, 2);
+            if (!ok) {
+                // drain: wait (bounded) for the copies still in flight
+                for (long long q = (g > STAGES ? g - STAGES : 0); q < g; ++q)
+                    mbar_wait(&full_bar[q % STAGES], (uint32_t)((q / STAGES) & 1), tword, 2);
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
+            long long g = 0;
+            int lt = 0;   // tiles of this CTA
             bool ok = true;
-            for (int kb = 0; kb < nk && ok; ++kb) {
-                const int s = kb % STAGES;
-                if (!mbar_wait(&full_bar[s], (kb / STAGES) & 1, tword, 3)) {
+            for (long long L = blockIdx.x; L < args.ntiles && ok; L += gridDim.x) {
+                int gr, gc;
+                if (!tile_coords(args, L, &gr, &gc)) continue;
+                const int b = lt & 1;
+                if (lt >= 2 && !mbar_wait(&acc_empty[b], (uint32_t)(((lt >> 1) & 1) ^ 1), tword, 5)) {
                     ok = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t sa = smem_u32(smem + (size_t)s * STAGE_BYTES);
-                const uint32_t sb = sa + TILE_BYTES;
-                const uint32_t sal = sa + 2 * TILE_BYTES, sbl = sb + 2 * TILE_BYTES;
-#pragma unroll
-                for (int kk = 0; kk < BK / 16; ++kk) {
-                    mma_f16(tmem, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32), idesc, (kb | kk) != 0);
-                    if (args.terms == 2) {
-                        mma_f16(tmem, smem_desc(sa + kk * 32), smem_desc(sbl + kk * 32), idesc, 1);
-                        mma_f16(tmem, smem_desc(sal + kk * 32), smem_desc(sb + kk * 32), idesc, 1);
+                const uint32_t acc = tmem + (uint32_t)(b * BN);
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const int s = (int)(g % STAGES);
+                    if (!mbar_wait(&full_bar[s], (uint32_t)((g / STAGES) & 1), tword, 3)) {
+                        ok = false;
+                        break;
                     }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = smem_u32(smem + (size_t)s * STAGE_BYTES);
+                    const uint32_t sb = sa + TILE_BYTES;
+                    const uint32_t sal = sa + 2 * TILE_BYTES, sbl = sb + 2 * TILE_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        mma_f16(acc, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32), idesc, (kb | kk) != 0);
+                        if (args.terms == 2) {
+                            mma_f16(acc, smem_desc(sa + kk * 32), smem_desc(sbl + kk * 32), idesc, 1);
+                            mma_f16(acc, smem_desc(sal + kk * 32), smem_desc(sb + kk * 32), idesc, 1);
+                        }
+                    }
+                    mma_commit(&empty_bar[s]);
                 }
-                mma_commit(&empty_bar[s]);
+                if (!ok) break;
+                mma_commit(&acc_full[b]);
+                ++lt;
             }
-            if (ok) mma_commit(&acc_bar);
+            // every MMA issued so far has completed before TMEM can be freed
+            mma_commit(&drain_bar);
+            mbar_wait(&drain_bar, 0, tword, 6);
         }
         __syncwarp();
     } else {
-        // epilogue: warps 2..5, TMEM lane quarter q = warp % 4
-        const int q = warp % 4;
-        const int row = q * 32 + lane;
-        bool ok = mbar_wait(&acc_bar, 0, tword, 4);
-        // all lanes of the warp must take part in tcgen05.ld: agree on ok
-        ok = __all_sync(0xffffffffu, ok);
-        if (ok) {
+        // epilogue: warps 2..9; TMEM lane quarter q = warp % 4, column half h
+        const int q = warp % 4, h = (warp - 2) / 4;
+        int lt = 0;
+        for (long long L = blockIdx.x; L < args.ntiles; L += gridDim.x) {
+            int gr, gc;
+            if (!tile_coords(args, L, &gr, &gc)) continue;
+            const int b = lt & 1;
+            bool ok = mbar_wait(&acc_full[b], (uint32_t)((lt >> 1) & 1), tword, 4);
+            ok = __all_sync(0xffffffffu, ok);   // every lane takes part in tcgen05.ld
+            if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int grow = gr + row;
-            const bool rin = grow < args.r0 + args.m;
+            const int grow = gr + q * 32 + lane;
+            const bool rin = grow < args.N;
             const double si = rin ? args.inv_scale[grow - args.prow0] : 0.0;
-            for (int c = 0; c < BN / 32; ++c) {
+            for (int c = 0; c < BN / 64; ++c) {
+                const int col0 = h * (BN / 2) + c * 32;
                 float v[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 32), v);
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + col0), v);
                 if (rin) {
-#pragma unroll 4
-                    for (int j = 0; j < 32; ++j) {
-                        const int gcol = gc + c * 32 + j;
-                        if (gcol < args.c0 + args.n) {
-                            const double sj = args.inv_scale[gcol - args.prow0];
-                            double *p = args.C + (long long)gcol * args.ldc + grow;
-                            *p -= (si * sj) * (double)v[j];
+#pragma unroll
+                    for (int j0 = 0; j0 < 32; j0 += 8) {
+                        double cv[8];
+                        double *pc[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int gcol = gc + col0 + j0 + j;
+                            pc[j] = (gcol < args.N) ? args.C + (long long)gcol * args.ldc + grow : nullptr;
+                            cv[j] = pc[j] ? *pc[j] : 0.0;
                         }
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (pc[j]) {
+                                const double sj = args.inv_scale[gc + col0 + j0 + j - args.prow0];
+                                *pc[j] = cv[j] - (si * sj) * (double)v[j0 + j];
+                            }
                     }
                 }
             }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b]))
+                                        : "memory");
+            ++lt;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS_P)
+                     : "memory");
     }
 }
 
