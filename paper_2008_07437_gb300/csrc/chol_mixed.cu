@@ -300,7 +300,17 @@ cudaError_t sgemm(TC *C, long long ldc, const float *A, long long lda, const flo
 
 }  // namespace
 
-size_t mixed_workspace_bytes(int N, int nb) {
+namespace {
+
+// One panel's workspace: FP32 copy of the rows below the diagonal tile,
+// FP32 copy of the diagonal tile, FP16 (or BF16) hi / lo copies, row scales.
+struct PanelWs {
+    float *P32, *LD32;
+    void *P16, *P16lo;
+    double *inv_scale;
+};
+
+size_t panel_ws_bytes(int N, int nb) {
     const size_t rows = (size_t)N + 128;
     const size_t ldp = (rows + 3) / 4 * 4;
     return sizeof(float) * ldp * nb              // FP32 panel
@@ -309,6 +319,190 @@ size_t mixed_workspace_bytes(int N, int nb) {
            + sizeof(double) * rows               // row scales
            + 4096;
 }
+
+PanelWs carve(uint8_t *w, size_t rows_max, long long ldp, int nb) {
+    PanelWs W;
+    W.P32 = (float *)w;
+    w += sizeof(float) * ldp * nb;
+    W.LD32 = (float *)w;
+    w += sizeof(float) * (size_t)nb * nb;
+    w = (uint8_t *)(((uintptr_t)w + 255) & ~(uintptr_t)255);
+    W.P16 = w;
+    w += 2 * rows_max * (size_t)nb;
+    W.P16lo = w;
+    w += 2 * rows_max * (size_t)nb;
+    w = (uint8_t *)(((uintptr_t)w + 255) & ~(uintptr_t)255);
+    W.inv_scale = (double *)w;
+    return W;
+}
+
+struct MixedGeom {
+    double *A;
+    long long ld;
+    int N, nrows, nb, band, lowp;
+    long long ldp;
+    DevStatus *st;
+};
+
+// Diagonal tile of panel [j0, j0 + jb) in FP64, carrying the right-hand-side
+// rows [N, nrows): a chain of small latency-bound launches.
+cudaError_t mixed_panel_diag(const MixedGeom &G, int j0, cudaStream_t s) {
+    const int jb = min(G.nb, G.N - j0);
+    const int t0 = j0 + jb;
+    return chol64_panel(G.A, G.ld, j0, jb, (G.nrows > G.N) ? G.N : t0, (G.nrows > G.N) ? G.nrows : t0, G.st, s);
+}
+
+// Rows below the diagonal tile of panel j0: solved in FP32 against the
+// factored tile and written back, plus their low-precision copy with
+// per-row scales.
+cudaError_t mixed_panel_rows(const MixedGeom &G, int j0, const PanelWs &W, cudaStream_t s) {
+    double *A = G.A;
+    const long long ld = G.ld, ldp = G.ldp;
+    const int N = G.N, nb = G.nb;
+    DevStatus *st = G.st;
+    const int jb = min(nb, N - j0);
+    const int t0 = j0 + jb;
+    cudaError_t e;
+    if (t0 >= N) return cudaSuccess;
+    const int R = N - t0;   // rows of the panel below the diagonal tile
+    {
+        const long long tot = (long long)R * jb;
+        KScope ks(GEO_K_AUX, s);
+        k_to_f32<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(A + (long long)j0 * ld + t0, ld, R, jb, W.P32, ldp);
+    }
+    {
+        const long long tot = (long long)jb * jb;
+        KScope ks(GEO_K_AUX, s);
+        k_to_f32<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(A + (long long)j0 * ld + j0, ld, jb, jb, W.LD32, nb);
+    }
+    for (int c0 = 0; c0 < jb; c0 += 64) {
+        const int cb = min(64, jb - c0);
+        {
+            KScope ks(GEO_K_TRSM, s, (double)R * cb * cb, 0.0);
+            k_trsm32<<<(R + TR_ROWS - 1) / TR_ROWS, 256, 0, s>>>(W.P32 + (long long)c0 * ldp, ldp, R,
+                                                                 A + (long long)(j0 + c0) * ld + j0 + c0, ld, cb, st);
+        }
+        if (c0 + cb < jb) {
+            // P32[:, c0+cb:] -= P32[:, c0:c0+cb] LD[c0+cb:, c0:c0+cb]'
+            e = sgemm<float>(W.P32 + (long long)(c0 + cb) * ldp, ldp, W.P32 + (long long)c0 * ldp, ldp,
+                             W.LD32 + (long long)c0 * nb + c0 + cb, nb, R, jb - c0 - cb, cb, 0, 0, 0, 0, 0, 0, st,
+                             2.0 * R * (jb - c0 - cb) * cb, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    {
+        const long long tot = (long long)R * jb;
+        KScope ks(GEO_K_AUX, s);
+        k_to_f64<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(W.P32, ldp, R, jb, A + (long long)j0 * ld + t0, ld);
+    }
+    // low-precision copy with per-row scales (only needed when far tiles exist)
+    const bool far = (N - 1) / nb - t0 / nb > G.band;
+    if (far) {
+        const int nblk = (R + 63) / 64;
+        KScope ks(GEO_K_AUX, s);
+        if (G.lowp)
+            k_to_lowp<__nv_bfloat16><<<nblk, 256, 0, s>>>(W.P32, ldp, R, jb, (__nv_bfloat16 *)W.P16, nullptr, nb,
+                                                          W.inv_scale);
+        else
+            k_to_lowp<__half><<<nblk, 256, 0, s>>>(W.P32, ldp, R, jb, (__half *)W.P16, (__half *)W.P16lo, nb,
+                                                   W.inv_scale);
+    }
+    return cudaGetLastError();
+}
+
+// Update of the trailing columns [ca, cb) (nb-aligned, ca >= t0) by panel j0:
+// tiles within the band in FP32 SIMT, tiles beyond on the tensor cores, the
+// right-hand-side rows in FP64.
+cudaError_t mixed_update(const MixedGeom &G, int j0, int ca, int cb, const PanelWs &W, EncodeTiledFn enc,
+                         uint32_t idesc, int grid_cap, cudaStream_t s) {
+    double *A = G.A;
+    const long long ld = G.ld, ldp = G.ldp;
+    const int N = G.N, nrows = G.nrows, nb = G.nb, band = G.band;
+    DevStatus *st = G.st;
+    const int jb = min(nb, N - j0);
+    const int t0 = j0 + jb;
+    const int R = N - t0;
+    cudaError_t e;
+    // band and diagonal tiles in FP32: rows [ca, N), cols [ca, cb)
+    {
+        double ent = 0.0;
+        const int Ja = ca / nb, Jb = (cb - 1) / nb, T1 = (N - 1) / nb;
+        for (int I = Ja; I <= T1; ++I) {
+            const double hi = min(N, (I + 1) * nb) - I * nb;
+            for (int J = max(Ja, I - band); J <= min(I, Jb); ++J) {
+                const double wj = min(N, (J + 1) * nb) - J * nb;
+                ent += (I == J) ? hi * (hi + 1) / 2 : hi * wj;
+            }
+        }
+        e = sgemm<double>(A + (long long)ca * ld + ca, ld, W.P32 + (ca - t0), ldp, W.P32 + (ca - t0), ldp, N - ca,
+                          cb - ca, jb, ca, ca, nb, 0, band, 1, st, 2.0 * jb * ent, s);
+        if (e != cudaSuccess) return e;
+    }
+    // far tiles on the tensor cores
+    const int T0 = t0 / nb, Ja = ca / nb, T1 = (N - 1) / nb;
+    const bool col_only = (cb - ca <= nb) && Ja == T0;
+    const long long far_rows = std::max(0, T1 - Ja - band);
+    if (far_rows > 0) {
+        const int terms = G.lowp ? 1 : 2;   // FP16 keeps hi + lo; BF16 keeps one term
+        CUtensorMap map;
+        cuuint64_t dims[2] = {(cuuint64_t)nb, (cuuint64_t)R};
+        cuuint64_t strides[1] = {(cuuint64_t)nb * 2};
+        cuuint32_t box[2] = {64, 128};
+        cuuint32_t es[2] = {1, 1};
+        CUresult cr = enc(&map, G.lowp ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, W.P16,
+                          dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        CUtensorMap map_lo = map;
+        if (terms == 2) {
+            cr = enc(&map_lo, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, W.P16lo, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        }
+        tc::TcArgs a;
+        a.C = A;
+        a.ldc = ld;
+        a.N = N;
+        a.prow0 = t0;
+        a.K = nb;   // columns jb..nb of the low-precision copy are zero
+        a.nb = nb;
+        a.band = band;
+        a.T0 = Ja;
+        a.col_only = col_only ? 1 : 0;
+        const long long per2 = (long long)(nb / tc::BM) * (nb / tc::BM);
+        a.ntiles = (col_only ? far_rows : far_rows * (far_rows + 1) / 2) * per2;
+        a.inv_scale = W.inv_scale;
+        a.terms = terms;
+        a.st = st;
+        double ent = 0.0;
+        const int Jb = (cb - 1) / nb;
+        for (int I = Ja; I <= T1; ++I) {
+            const double hi = min(N, (I + 1) * nb) - I * nb;
+            for (int J = Ja; J < I - band && J <= Jb; ++J) ent += hi * nb;
+        }
+        const int grid = (int)std::min<long long>(a.ntiles, std::max(1, std::min(grid_cap, num_sms())));
+        KScope ks(GEO_K_TCGEMM, s, 2.0 * jb * ent * (terms == 2 ? 3 : 1), 16.0 * ent + 2.0 * terms * (double)R * jb);
+        if (grid > 0) tc::k_tc_update<<<grid, tc::THREADS_P, tc::SMEM_BYTES, s>>>(map, map_lo, a, idesc);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // right-hand-side rows in FP64
+    if (nrows > N) return chol64_gemm_update(A, ld, N, ca, nrows - N, cb - ca, j0, jb, st, s);
+    return cudaSuccess;
+}
+
+}  // namespace
+
+size_t mixed_workspace_bytes(int N, int nb) { return panel_ws_bytes(N, nb); }
+
+// Right-looking over panels with a lookahead of one: step j first updates the
+// next panel's tile column; the diagonal tile of that panel (a chain of small
+// FP64 launches) is then factored on a second, high-priority stream while the
+// rest of step j's trailing update runs (its persistent tensor-core launch
+// leaves SIDE_SMS SMs free for it); the rows below it are solved after the
+// join.  Every entry receives the same operations in the same order as
+// without the lookahead.
+constexpr int SIDE_SMS = 8;
 
 cudaError_t chol_mixed_factor(double *A, long long ld, int N, int nrows, int nb, int band, int lowp, void *ws,
                               size_t ws_bytes, DevStatus *st, cudaStream_t s) {
@@ -320,139 +514,47 @@ cudaError_t chol_mixed_factor(double *A, long long ld, int N, int nrows, int nb,
                                          (int)tc::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const size_t rows_max = (size_t)N + 128;
-    const long long ldp = (long long)((rows_max + 3) / 4 * 4);
-    uint8_t *w = (uint8_t *)ws;
-    float *P32 = (float *)w;
-    w += sizeof(float) * ldp * nb;
-    float *LD32 = (float *)w;
-    w += sizeof(float) * (size_t)nb * nb;
-    w = (uint8_t *)(((uintptr_t)w + 255) & ~(uintptr_t)255);
-    void *P16 = w;
-    w += 2 * rows_max * (size_t)nb;
-    void *P16lo = w;
-    w += 2 * rows_max * (size_t)nb;
-    w = (uint8_t *)(((uintptr_t)w + 255) & ~(uintptr_t)255);
-    double *inv_scale = (double *)w;
+    MixedGeom G{A, ld, N, nrows, nb, band, lowp, (long long)((rows_max + 3) / 4 * 4), st};
+    const PanelWs W = carve((uint8_t *)ws, rows_max, G.ldp, nb);
     const uint32_t idesc = tc::instr_desc(lowp ? 1 : 0);
-
-    for (int j0 = 0; j0 < N; j0 += nb) {
-        const int jb = min(nb, N - j0);
-        const int t0 = j0 + jb;
-        // 1. diagonal tile in FP64, carrying the right-hand-side rows [N, nrows)
-        e = chol64_panel(A, ld, j0, jb, (nrows > N) ? N : t0, (nrows > N) ? nrows : t0, st, s);
-        if (e != cudaSuccess) return e;
-        if (t0 >= N) break;
-        const int R = N - t0;   // rows of the panel below the diagonal tile
-        // 2. FP32 TRSM of rows [t0, N) against L_kk, inner 64-wide blocks
-        {
-            const long long tot = (long long)R * jb;
-            KScope ks(GEO_K_AUX, s);
-            k_to_f32<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(A + (long long)j0 * ld + t0, ld, R, jb, P32, ldp);
-        }
-        {
-            const long long tot = (long long)jb * jb;
-            KScope ks(GEO_K_AUX, s);
-            k_to_f32<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(A + (long long)j0 * ld + j0, ld, jb, jb, LD32, nb);
-        }
-        for (int c0 = 0; c0 < jb; c0 += 64) {
-            const int cb = min(64, jb - c0);
-            {
-                KScope ks(GEO_K_TRSM, s, (double)R * cb * cb, 0.0);
-                k_trsm32<<<(R + TR_ROWS - 1) / TR_ROWS, 256, 0, s>>>(P32 + (long long)c0 * ldp, ldp, R,
-                                                                     A + (long long)(j0 + c0) * ld + j0 + c0, ld, cb,
-                                                                     st);
-            }
-            if (c0 + cb < jb) {
-                // P32[:, c0+cb:] -= P32[:, c0:c0+cb] LD[c0+cb:, c0:c0+cb]'
-                e = sgemm<float>(P32 + (long long)(c0 + cb) * ldp, ldp, P32 + (long long)c0 * ldp, ldp,
-                                 LD32 + (long long)c0 * nb + c0 + cb, nb, R, jb - c0 - cb, cb, 0, 0, 0, 0, 0, 0, st,
-                                 2.0 * R * (jb - c0 - cb) * cb, s);
-                if (e != cudaSuccess) return e;
-            }
-        }
-        {
-            const long long tot = (long long)R * jb;
-            KScope ks(GEO_K_AUX, s);
-            k_to_f64<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P32, ldp, R, jb, A + (long long)j0 * ld + t0, ld);
-        }
-        // 3. low-precision copy with per-128-row-block scales (only needed when far tiles exist)
-        const bool far = (N - 1) / nb - t0 / nb > band;
-        const int nblk = (R + 63) / 64;
-        const int terms = lowp ? 1 : 2;   // FP16 keeps hi + lo; BF16 keeps one term
-        if (far) {
-            KScope ks(GEO_K_AUX, s);
-            if (lowp)
-                k_to_lowp<__nv_bfloat16><<<nblk, 256, 0, s>>>(P32, ldp, R, jb, (__nv_bfloat16 *)P16, nullptr, nb,
-                                                              inv_scale);
-            else
-                k_to_lowp<__half><<<nblk, 256, 0, s>>>(P32, ldp, R, jb, (__half *)P16, (__half *)P16lo, nb,
-                                                       inv_scale);
-        }
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        // 4a. trailing update of diagonal and band tiles in FP32
-        {
-            // algorithmic flops: lower-triangle entries of the classes d <= band
-            double ent = 0.0;
-            const int T0 = t0 / nb, T1 = (N - 1) / nb;
-            for (int I = T0; I <= T1; ++I) {
-                const double hi = min(N, (I + 1) * nb) - I * nb;
-                for (int J = max(T0, I - band); J <= I; ++J) {
-                    const double wj = min(N, (J + 1) * nb) - J * nb;
-                    ent += (I == J) ? hi * (hi + 1) / 2 : hi * wj;
-                }
-            }
-            e = sgemm<double>(A + (long long)t0 * ld + t0, ld, P32, ldp, P32, ldp, R, R, jb, t0, t0, nb, 0, band, 1,
-                              st, 2.0 * jb * ent, s);
-            if (e != cudaSuccess) return e;
-        }
-        // 4b. far tiles on tensor cores
-        if (far) {
-            CUtensorMap map;
-            cuuint64_t dims[2] = {(cuuint64_t)nb, (cuuint64_t)R};
-            cuuint64_t strides[1] = {(cuuint64_t)nb * 2};
-            cuuint32_t box[2] = {64, 128};
-            cuuint32_t es[2] = {1, 1};
-            CUresult cr = enc(&map, lowp ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, P16,
-                              dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
-            CUtensorMap map_lo = map;
-            if (terms == 2) {
-                cr = enc(&map_lo, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, P16lo, dims, strides, box, es,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-                if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
-            }
-            tc::TcArgs a;
-            a.C = A;
-            a.ldc = ld;
-            a.N = N;
-            a.prow0 = t0;
-            a.K = nb;   // columns jb..nb of the low-precision copy are zero
-            a.nb = nb;
-            a.band = band;
-            a.T0 = t0 / nb;
-            const long long far_rows = std::max(0, (N - 1) / nb - a.T0 - band);
-            a.ntiles = far_rows * (far_rows + 1) / 2 * (long long)(nb / tc::BM) * (nb / tc::BM);
-            a.inv_scale = inv_scale;
-            a.terms = terms;
-            a.st = st;
-            double ent = 0.0;
-            const int T0 = t0 / nb, T1 = (N - 1) / nb;
-            for (int I = T0; I <= T1; ++I) {
-                const double hi = min(N, (I + 1) * nb) - I * nb;
-                for (int J = T0; J < I - band; ++J) ent += hi * nb;
-            }
-            const int grid = (int)std::min<long long>(a.ntiles, num_sms());
-            KScope ks(GEO_K_TCGEMM, s, 2.0 * jb * ent * (terms == 2 ? 3 : 1), 16.0 * ent + 2.0 * terms * (double)R * jb);
-            if (grid > 0) tc::k_tc_update<<<grid, tc::THREADS_P, tc::SMEM_BYTES, s>>>(map, map_lo, a, idesc);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        }
-        // 4c. right-hand-side rows in FP64
-        if (nrows > N) {
-            e = chol64_gemm_update(A, ld, N, t0, nrows - N, N - t0, j0, jb, st, s);
-            if (e != cudaSuccess) return e;
-        }
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t e_upd = nullptr, e_pan = nullptr;
+    if ((e = cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, prio_hi)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&e_upd, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&e_pan, cudaEventDisableTiming)) != cudaSuccess) {
+        cudaStreamDestroy(s2);
+        if (e_upd) cudaEventDestroy(e_upd);
+        return e;
     }
-    return cudaSuccess;
+    const int all = num_sms();
+    auto run = [&]() -> cudaError_t {
+        cudaError_t r;
+        if ((r = mixed_panel_diag(G, 0, s)) != cudaSuccess || (r = mixed_panel_rows(G, 0, W, s)) != cudaSuccess)
+            return r;
+        for (int j0 = 0; j0 < N; j0 += nb) {
+            const int t0 = j0 + min(nb, N - j0);
+            if (t0 >= N) break;
+            const int n1 = min(N, t0 + nb);
+            // the next panel's tile column first, then its diagonal tile on the second stream
+            if ((r = mixed_update(G, j0, t0, n1, W, enc, idesc, all, s)) != cudaSuccess) return r;
+            if ((r = cudaEventRecord(e_upd, s)) != cudaSuccess) return r;
+            if ((r = cudaStreamWaitEvent(s2, e_upd, 0)) != cudaSuccess) return r;
+            if ((r = mixed_panel_diag(G, t0, s2)) != cudaSuccess) return r;
+            if ((r = cudaEventRecord(e_pan, s2)) != cudaSuccess) return r;
+            // the rest of this step's trailing update meanwhile
+            if (n1 < N && (r = mixed_update(G, j0, n1, N, W, enc, idesc, all - SIDE_SMS, s)) != cudaSuccess)
+                return r;
+            if ((r = cudaStreamWaitEvent(s, e_pan, 0)) != cudaSuccess) return r;
+            if ((r = mixed_panel_rows(G, t0, W, s)) != cudaSuccess) return r;
+        }
+        return cudaSuccess;
+    };
+    e = run();
+    if (e != cudaSuccess) cudaStreamSynchronize(s2);
+    cudaEventDestroy(e_upd);
+    cudaEventDestroy(e_pan);
+    cudaStreamDestroy(s2);
+    return e;
 }

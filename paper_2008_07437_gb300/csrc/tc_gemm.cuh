@@ -18,7 +18,8 @@
 //           to the epilogue;
 //   warps 2-9: epilogue, tcgen05.ld of the accumulator (warp w reads TMEM
 //           lanes 32 (w % 4) .. + 31 = tile rows, half of the columns each),
-//           scale, FP64 read-modify-write of C with stores contiguous across
+//           scale (in FP32: the scales are powers of two), FP64
+//           read-modify-write of C with stores contiguous across
 //           each warp; then it frees the accumulator, so the epilogue of one
 //           tile overlaps the MMAs of the next.
 // Every wait on an mbarrier is bounded by a clock budget; on expiry the
@@ -131,8 +132,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
 }
 
 // The far tiles of one trailing update: nb-tiles (I, J) with I - J > band,
-// T0 <= J, I <= T1 (T0 = t0 / nb), enumerated row by row (u = I - T0 - band - 1,
-// v = J - T0 <= u), each split into (nb / 128)^2 output tiles of 128 x 128.
+// T0 <= J, I <= T1, enumerated row by row (u = I - T0 - band - 1, v = J - T0
+// <= u), each split into (nb / 128)^2 output tiles of 128 x 128; with col_only
+// only the column J = T0 (u = I - T0 - band - 1, v = 0).
 struct TcArgs {
     double *C;
     long long ldc;
@@ -140,6 +142,7 @@ struct TcArgs {
     int prow0;             // global row of panel row 0 (A / B operand row = global - prow0)
     int K;                 // panel width (multiple of 64)
     int nb, band, T0;      // class geometry
+    int col_only;          // 1: only nb-tile column T0
     long long ntiles;      // output tiles in the list
     const double *inv_scale;   // per panel row
     int terms;                 // 1: hi only, 2: hi + lo
@@ -154,10 +157,13 @@ constexpr int TMEM_COLS_P = 2 * BN;
 __device__ __forceinline__ bool tile_coords(const TcArgs &a, long long L, int *gr, int *gc) {
     const int per = a.nb / BM;                       // 128-tiles per nb along each side
     const long long sub = L % ((long long)per * per), f = L / ((long long)per * per);
-    long long u = (long long)((sqrt(8.0 * (double)f + 1.0) - 1.0) * 0.5);
-    while ((u + 1) * (u + 2) / 2 <= f) ++u;
-    while (u * (u + 1) / 2 > f) --u;
-    const long long v = f - u * (u + 1) / 2;
+    long long u = f, v = 0;
+    if (!a.col_only) {
+        u = (long long)((sqrt(8.0 * (double)f + 1.0) - 1.0) * 0.5);
+        while ((u + 1) * (u + 2) / 2 <= f) ++u;
+        while (u * (u + 1) / 2 > f) --u;
+        v = f - u * (u + 1) / 2;
+    }
     const int I = a.T0 + a.band + 1 + (int)u, J = a.T0 + (int)v;
     *gr = I * a.nb + (int)(sub / per) * BM;
     *gc = J * a.nb + (int)(sub % per) * BN;
@@ -290,7 +296,8 @@ __global__ void __launch_bounds__(THREADS_P, 1)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int grow = gr + q * 32 + lane;
             const bool rin = grow < args.N;
-            const double si = rin ? args.inv_scale[grow - args.prow0] : 0.0;
+            // the scales are powers of two: v / (s_r s_c) is exact in FP32 as well
+            const float si = rin ? (float)args.inv_scale[grow - args.prow0] : 0.f;
             for (int c = 0; c < BN / 64; ++c) {
                 const int col0 = h * (BN / 2) + c * 32;
                 float v[32];
@@ -309,8 +316,8 @@ __global__ void __launch_bounds__(THREADS_P, 1)
 #pragma unroll
                         for (int j = 0; j < 8; ++j)
                             if (pc[j]) {
-                                const double sj = args.inv_scale[gc + col0 + j0 + j - args.prow0];
-                                *pc[j] = cv[j] - (si * sj) * (double)v[j0 + j];
+                                const float sj = (float)args.inv_scale[gc + col0 + j0 + j - args.prow0];
+                                *pc[j] = cv[j] - (double)((v[j0 + j] * si) * sj);
                             }
                     }
                 }
