@@ -261,6 +261,29 @@ int geo_loglik_batch(geo_ctx *ctx, int count, const geo_batch_item *items, doubl
                      void *stream);
 
 /*
+ * Multivariate MLOE / MMOM (Eq. 5 - Eq. 8, Algorithm 1 of Sec. 5.4): how much
+ * cokriging with theta_a instead of the true theta_t loses in prediction
+ * efficiency (LOE) and misstates the mean square prediction error (MOM),
+ * averaged over m prediction locations s0:
+ *   E_t  = tr{C(0; t) - c_t' S_t^-1 c_t}
+ *   E_ta = tr{C(0; t) - 2 c_t' S_a^-1 c_a + c_a' S_a^-1 S_t S_a^-1 c_a}
+ *   E_a  = tr{C(0; a) - c_a' S_a^-1 c_a}
+ *   LOE = E_ta / E_t - 1,  MOM = E_a / E_ta - 1,  MLOE / MMOM = their means,
+ * with S = Sigma(theta) at the observed locations and c the p n x p
+ * cross-covariance with s0.  Dense FP64: both matrices are factored with the
+ * cross-covariances of all m locations riding along as extra rows.
+ *   locs_dev  n x 2, pred_dev m x 2 (device, caller-owned)
+ *   theta_t, theta_a  host structs with the same p
+ *   opts      NULL or options (nb, morton; the form is always FP64)
+ *   mloe, mmom  host scalars; loe_host, mom_host  NULL or m doubles (host)
+ * Synchronises `stream`.  GEO_ENOTSPD if either matrix is not positive
+ * definite; GEO_ENOMEM beyond the budget (two N x (N + 2 p m) matrices).
+ */
+int geo_mloe_mmom(geo_ctx *ctx, const double *locs_dev, int n, const double *pred_dev, int m,
+                  const geo_theta *theta_t, const geo_theta *theta_a, const geo_opts *opts, double *mloe,
+                  double *mmom, double *loe_host, double *mom_host, void *stream);
+
+/*
  * Request server: likelihood and cokriging requests of different sizes on one
  * GPU, admitted continuously (no paper counterpart: the paper evaluates one
  * likelihood at a time).  `slots` worker threads each own a context and a

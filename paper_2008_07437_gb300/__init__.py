@@ -113,6 +113,8 @@ SIGNATURES = {
     "geo_profile_enable": (_I, [_P, _I]),
     "geo_profile_read": (_I, [_P, ctypes.POINTER(geo_kstat)]),
     "geo_server_profile_read": (_I, [_P, ctypes.POINTER(geo_kstat)]),
+    "geo_mloe_mmom": (_I, [_P, _P, _I, _P, _I, ctypes.POINTER(geo_theta), ctypes.POINTER(geo_theta), _P, _P, _P, _P,
+                           _P, _P]),
     "geo_loglik_noalloc": (_I, [_P, _I, _P, ctypes.POINTER(geo_theta), _I, _P, _P, _P]),
     "geo_loglik_batch": (_I, [_P, _I, _P, _P, _P, _P]),
     "geo_server_create": (_I, [ctypes.POINTER(_P), _I, ctypes.c_size_t, _I]),
@@ -527,6 +529,25 @@ class Server:
         if self.handle:
             self.lib.geo_server_destroy(self.handle)
             self.handle = None
+
+
+def geo_mloe_mmom(ctx: Context, locs, pred, theta_t: Theta, theta_a: Theta, options: geo_opts | None = None,
+                  stream=None):
+    """MLOE, MMOM and the per-location LOE / MOM of Eq. 5 - Eq. 8 (Algorithm 1)."""
+    import torch
+    tt, _k1 = theta_t.to_c()
+    ta, _k2 = theta_a.to_c()
+    m = pred.shape[0]
+    loe = np.zeros(m)
+    mom = np.zeros(m)
+    ml = ctypes.c_double()
+    mm = ctypes.c_double()
+    ctx.check(ctx.lib.geo_mloe_mmom(ctx.handle, _dev_ptr(locs, "locs", torch.float64), locs.shape[0],
+                                    _dev_ptr(pred, "pred", torch.float64), m, ctypes.byref(tt), ctypes.byref(ta),
+                                    ctypes.byref(options) if options is not None else None, ctypes.byref(ml),
+                                    ctypes.byref(mm), loe.ctypes.data_as(ctypes.c_void_p),
+                                    mom.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    return ml.value, mm.value, loe, mom
 
 
 def geo_autotune_nb(ctx: Context, locs, z, theta: Theta, candidates, options: geo_opts | None = None, stream=None):

@@ -1030,6 +1030,107 @@ int geo_loglik_batch(geo_ctx *ctx, int count, const geo_batch_item *items, doubl
     return GEO_OK;
 }
 
+int geo_mloe_mmom(geo_ctx *ctx, const double *locs_dev, int n, const double *pred_dev, int m,
+                  const geo_theta *theta_t, const geo_theta *theta_a, const geo_opts *opts, double *mloe,
+                  double *mmom, double *loe_host, double *mom_host, void *stream) {
+    if (!ctx) return GEO_EINVAL;
+    ProfBind pb(&ctx->prof);
+    if (!theta_t || !theta_a || theta_t->p != theta_a->p)
+        return fail(ctx, GEO_EINVAL, "theta_t and theta_a must be given with the same p");
+    if (n <= 0 || m <= 0 || !locs_dev || !pred_dev || !mloe || !mmom)
+        return fail(ctx, GEO_EINVAL, "n, m must be > 0 and pointers non-NULL");
+    geo_opts o;
+    if (opts)
+        o = *opts;
+    else
+        geo_opts_default(&o);
+    o.prec = GEO_PREC_FP64;
+    const int p = theta_t->p, N = p * n, pm = p * m;
+    if (o.nb == 0) o.nb = resolve_nb(ctx->device, GEO_PREC_FP64, N);
+    if (o.nb < 64) return fail(ctx, GEO_EINVAL, "nb must be >= 64");
+    SetDevice sd(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    geo_factor *ft = new geo_factor(), *fa = new geo_factor();
+    ft->ctx = fa->ctx = ctx;
+    const int nblk = (N + 63) / 64;
+    const long long ldv = round_up(pm, 32);
+    void *pv = nullptr, *psum = nullptr, *pdesc = nullptr, *hdesc = nullptr;
+    const size_t vbytes = sizeof(double) * (size_t)ldv * N, dbytes = sizeof(GemmDesc) * (size_t)(nblk + 64);
+    auto done = [&](int code) {
+        cudaStreamSynchronize(s);
+        release_factor_buffers(ctx, ft, true);
+        release_factor_buffers(ctx, fa, true);
+        delete ft;
+        delete fa;
+        if (pv) dev_free(ctx, pv, vbytes);
+        if (psum) dev_free(ctx, psum, sizeof(double) * 4 * pm);
+        if (pdesc) dev_free(ctx, pdesc, dbytes);
+        if (hdesc) cudaFreeHost(hdesc);
+        return code;
+    };
+    int rc;
+    // Sigma_t with C_t' in rows [N, N + pm); Sigma_a with C_a' and C_t' below it
+    if ((rc = prepare_matrix(ctx, locs_dev, n, theta_t, &o, pm, ft, s)) ||
+        (rc = prepare_matrix(ctx, locs_dev, n, theta_a, &o, 2 * pm, fa, s)))
+        return done(rc);
+    if ((rc = dev_alloc(ctx, &pv, vbytes)) || (rc = dev_alloc(ctx, &psum, sizeof(double) * 4 * pm)) ||
+        (rc = dev_alloc(ctx, &pdesc, dbytes)))
+        return done(rc);
+    if (cudaMallocHost(&hdesc, sizeof(GemmDesc) * (size_t)nblk) != cudaSuccess) {
+        cudaGetLastError();
+        hdesc = nullptr;
+        return done(fail(ctx, GEO_ENOMEM, "pinned descriptor buffer"));
+    }
+    double *sum_t = (double *)psum, *sum_a = sum_t + pm, *cross = sum_a + pm, *sum_v = cross + pm;
+    cudaError_t e;
+    if ((e = launch_covgen_cross(ft->cp, pred_dev, m, ft->lx, ft->ly, n, ft->A + N, ft->ld, s)) ||
+        (e = launch_covgen_cross(fa->cp, pred_dev, m, fa->lx, fa->ly, n, fa->A + N, fa->ld, s)) ||
+        (e = launch_covgen_cross(ft->cp, pred_dev, m, fa->lx, fa->ly, n, fa->A + N + pm, fa->ld, s)) ||
+        // factorisations: the rows below become (L^-1 c)'
+        (e = chol64_factor(ft->A, ft->ld, N, N + pm, o.nb, ctx->st, s)) ||
+        (e = chol64_factor(fa->A, fa->ld, N, N + 2 * pm, o.nb, ctx->st, s)) ||
+        // |L_t^-1 c_t|^2, |L_a^-1 c_a|^2, (L_a^-1 c_t) . (L_a^-1 c_a)
+        (e = launch_row_sums(ft->A + N, ft->ld, nullptr, 0, pm, N, sum_t, nullptr, s)) ||
+        (e = launch_row_sums(fa->A + N, fa->ld, fa->A + N + pm, fa->ld, pm, N, sum_a, cross, s)) ||
+        // w_a' = (L_a^-1 c_a)' L_a^-1 = (S_a^-1 c_a)', then (L_t' S_a^-1 c_a)' = w_a' L_t
+        (e = trsm_right_lower(fa->A + N, fa->ld, pm, fa->A, fa->ld, N, pdesc, s)) ||
+        (e = trmm_right_lower(fa->A + N, fa->ld, pm, ft->A, ft->ld, N, (double *)pv, ldv, (GemmDesc *)pdesc + 64,
+                              hdesc, s)) ||
+        (e = launch_row_sums((double *)pv, ldv, nullptr, 0, pm, N, sum_v, nullptr, s)) ||
+        (e = cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s)))
+        return done(cuda_fail(ctx, e, "geo_mloe_mmom"));
+    std::vector<double> h(4 * (size_t)pm);
+    if ((e = cudaMemcpyAsync(h.data(), psum, sizeof(double) * 4 * pm, cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s)))
+        return done(cuda_fail(ctx, e, "geo_mloe_mmom"));
+    if (ctx->h_st->info) return done(fail(ctx, GEO_ENOTSPD, "Sigma(theta_t) or Sigma(theta_a) is not positive definite"));
+    if (ctx->h_st->timeout) return done(fail(ctx, GEO_ETIMEOUT, "a bounded device wait expired"));
+    // Eq. 5 - Eq. 8 per location; C_ii(0) = sigma^2_i (rho_ii = 1)
+    double tr_t = 0.0, tr_a = 0.0;
+    for (int i = 0; i < p; ++i) {
+        tr_t += ft->cp.m[i * p + i].c0;
+        tr_a += fa->cp.m[i * p + i].c0;
+    }
+    double sl = 0.0, sm = 0.0;
+    for (int l = 0; l < m; ++l) {
+        double et = tr_t, ea = tr_a, eta = tr_t;
+        for (int i = 0; i < p; ++i) {
+            const int q = p * l + i;
+            et -= h[q];
+            ea -= h[pm + q];
+            eta += h[3 * (size_t)pm + q] - 2.0 * h[2 * (size_t)pm + q];
+        }
+        const double loe = eta / et - 1.0, mom = ea / eta - 1.0;
+        if (loe_host) loe_host[l] = loe;
+        if (mom_host) mom_host[l] = mom;
+        sl += loe;
+        sm += mom;
+    }
+    *mloe = sl / m;
+    *mmom = sm / m;
+    return done(GEO_OK);
+}
+
 int geo_autotune_nb(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev, const geo_theta *theta,
                     const geo_opts *base, const int *candidates, int ncand, int *best_nb, double *best_ms,
                     void *stream) {

@@ -33,15 +33,22 @@ __global__ void __launch_bounds__(256) k_bgemm(const GemmDesc *__restrict__ d, i
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
     for (int k0 = 0; k0 < g.k; k0 += BKK) {
+        // consecutive threads walk the operand's contiguous index: rows for a
+        // row-contiguous slice, K for a K-contiguous one (transposed A, plain B)
         for (int t = threadIdx.x; t < BKK * BT; t += 256) {
-            const int kk = t / BT, r = t % BT;
+            const int kk = g.ta ? t % BKK : t / BT, r = g.ta ? t / BKK : t % BT;
             const int kg = k0 + kk;
-            double a = 0.0, b = 0.0;
+            double a = 0.0;
             if (kg < g.k && tm + r < g.m)
                 a = g.ta ? g.A[(long long)(tm + r) * g.lda + kg] : g.A[(long long)kg * g.lda + tm + r];
+            As[kk][r] = a;
+        }
+        for (int t = threadIdx.x; t < BKK * BT; t += 256) {
+            const int kk = g.tb ? t / BT : t % BKK, r = g.tb ? t % BT : t / BKK;
+            const int kg = k0 + kk;
+            double b = 0.0;
             if (kg < g.k && tn + r < g.n)
                 b = g.tb ? g.B[(long long)kg * g.ldb + tn + r] : g.B[(long long)(tn + r) * g.ldb + kg];
-            As[kk][r] = a;
             Bs[kk][r] = b;
         }
         __syncthreads();

@@ -106,6 +106,22 @@ cudaError_t chol_mixed_factor(double *A, long long ld, int N, int nrows, int nb,
                               size_t ws_bytes, DevStatus *st, cudaStream_t s);
 
 
+// ---- mloe.cu --------------------------------------------------------------
+// Rows = prediction locations (AoS s0, m), cols = observed locations (SoA, n):
+// out[(p r + j) * ld + (p q + i)] = C_ij(|s0_q - s_r|).
+cudaError_t launch_covgen_cross(const CovParams &cp, const double *s0, int m, const double *lx, const double *ly,
+                                int n, double *out, long long ld, cudaStream_t s);
+// s[q] = sum_c X[q, c]^2, d[q] = sum_c X[q, c] Y[q, c] (Y, d may be NULL), q < R, c < N.
+cudaError_t launch_row_sums(const double *X, long long ldx, const double *Y, long long ldy, int R, int N, double *s,
+                            double *d, cudaStream_t st);
+// X <- X L^-1 (X: R x N, L lower); arena_dev: 64 GemmDesc of device scratch.
+cudaError_t trsm_right_lower(double *X, long long ldx, int R, const double *L, long long ldl, int N, void *arena_dev,
+                             cudaStream_t s);
+// V = X L (L lower; the upper parts of its 64 x 64 diagonal blocks are zeroed);
+// arena_dev / arena_host (pinned): ceil(N / 64) GemmDesc each.
+cudaError_t trmm_right_lower(const double *X, long long ldx, int R, double *L, long long ldl, int N, double *V,
+                             long long ldv, void *arena_dev, void *arena_host, cudaStream_t s);
+
 // ---- api.cu (for the request server) ---------------------------------------
 // Device bytes a context holds (cached workspaces and kept factors).
 size_t ctx_device_bytes(const geo_ctx *ctx);
