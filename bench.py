@@ -85,7 +85,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bivariate-n20000",
-                    choices=sorted(inputs.WORKLOADS) + ["serving", "batch"])
+                    choices=sorted(inputs.WORKLOADS) + ["serving", "batch", "mloe"])
     ap.add_argument("--n", type=int, default=0, help="override n (profiling runs on small cases only)")
     ap.add_argument("--n-pred", type=int, default=-1)
     ap.add_argument("--nb", type=int, default=0)
@@ -101,6 +101,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="serving: skip the tile-size autotuner")
     ap.add_argument("--batch-count", type=int, default=512, help="batch: problems per call")
     ap.add_argument("--mle", type=int, default=0, help="run this many Nelder-Mead steps instead of evaluations")
+    ap.add_argument("--mloe-m", type=int, default=100, help="mloe: prediction locations")
+    ap.add_argument("--tlr-tol", type=float, default=0.0, help="tile low-rank accuracy (default: the workload's)")
     return ap.parse_args()
 
 
@@ -113,6 +115,9 @@ def workload(args):
         w.n_pred = args.n_pred
     if args.nb:
         w.nb = args.nb
+    if args.tlr_tol > 0 and w.extra.get("prec") == 2:
+        w = inputs.Workload(w.name + "-tol%g" % args.tlr_tol, w.n, w.theta, n_pred=w.n_pred, nb=w.nb,
+                            loc_seed=w.loc_seed, z_seed=w.z_seed, extra=dict(w.extra, tlr_tol=args.tlr_tol))
     return w
 
 
@@ -321,10 +326,16 @@ def run_ours(args):
     if args.mle:
         return run_mle(args, w, ctx, d_locs, d_z, theta, o, dev)
 
+    tlr_stats = {}
+
     def step():
         ll, fac = geo.geo_loglik(ctx, d_locs, d_z, theta, o, keep=True)
         if w.n_pred:
             geo.geo_predict(ctx, fac, d_pred, d_zhat)
+        if tlr:
+            fs = geo.geo_factor_stats_get(fac)
+            tlr_stats.update(max_rank=fs.tlr_max_rank, dense_tiles=fs.tlr_dense_tiles,
+                             bytes_vs_dense=fs.tlr_bytes_ratio)
         fac.free()
         return ll
 
@@ -419,6 +430,7 @@ def run_ours(args):
            "gpu_launches": launches,
            "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
            "quality": {"loglik": ll, "mspe": mspe},
+           "tlr_factor": tlr_stats or None,
            "clocks": clk, "e2e": e2e}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -816,6 +828,85 @@ def run_batch(args):
     return 0
 
 
+# --------------------------------------------------------------------------
+# MLOE / MMOM (Eq. 5 - Eq. 8, Algorithm 1) on the bivariate n = 20,000 locations
+# --------------------------------------------------------------------------
+def mloe_setup(args):
+    w = inputs.WORKLOADS["bivariate-n20000"]
+    n = args.n or w.n
+    allp = inputs.jittered_grid(n + args.mloe_m, w.loc_seed)
+    spec = w.theta
+    th_a = inputs.ThetaSpec(tuple(1.1 * v for v in spec.sigma2), 1.2 * spec.a, tuple(0.9 * v for v in spec.nu),
+                            tuple(0.8 * b for b in spec.beta))
+    return w, n, allp[:n], allp[n:], spec, th_a
+
+
+def mloe_config(args, n, spec, th_a):
+    return {"workload": "mloe", "n": n, "p": 2, "N": 2 * n, "m": args.mloe_m,
+            "theta_t": {"sigma2": list(spec.sigma2), "a": spec.a, "nu": list(spec.nu), "beta": list(spec.beta)},
+            "theta_a": {"sigma2": list(th_a.sigma2), "a": th_a.a, "nu": list(th_a.nu), "beta": list(th_a.beta)},
+            "form": "dense FP64; both factorisations carry the m cross-covariances as extra rows",
+            "l2": "inputs larger than L2: two %.1f GB matrices generated every step" % (8.0 * (2 * n) ** 2 / 1e9)}
+
+
+def run_mloe(args):
+    import torch
+
+    import paper_2008_07437_gb300 as geo
+    from paper_2008_07437_gb300 import build as gbuild
+    torch.cuda.set_device(0)
+    gbuild.build()
+    dev = torch.device("cuda", 0)
+    w, n, locs, pred, spec, th_a_spec = mloe_setup(args)
+    ctx = geo.geo_create(0)
+    dl, dp = torch.as_tensor(locs, device=dev), torch.as_tensor(pred, device=dev)
+    th_t, th_a = geo.Theta.from_spec(spec), geo.Theta.from_spec(th_a_spec)
+    o = geo.opts(nb=960)
+    for _ in range(args.warmup):
+        geo.geo_mloe_mmom(ctx, dl, dp, th_t, th_a, o)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index)
+    geo.geo_profile_enable(ctx, True)
+    clocks.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ml, mm, loe, mom = geo.geo_mloe_mmom(ctx, dl, dp, th_t, th_a, o)
+    torch.cuda.synchronize()
+    t = (time.perf_counter() - t0) / args.steps
+    clk = clocks.stop()
+    prof = geo.geo_profile_read(ctx)
+    ph = {k: v["ms"] / args.steps for k, v in prof.items()}
+    gen = ph["covgen"]
+    fact = ph["potrf"] + ph["trsm"] + ph["gemm"]
+    comp = ph["solve"] + ph["reduce"] + ph["aux"]
+    dk = prof["gemm"]
+    bound, peak, peak_src = class_roofline("gemm")
+    ach = dk["flops"] / (dk["ms"] * 1e-3) / 1e12 if dk["ms"] > 0 else 0.0
+    out = {"metric": "MLOE/MMOM time", "value": t, "unit": "s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": mloe_config(args, n, spec, th_a_spec),
+           "mloe": ml, "mmom": mm, "phases_ms": {"GEN": gen, "FACT": fact, "COMP": comp},
+           "roofline": {"bound": bound, "kernel": "k_dgemm_update (both factorisations)", "achieved": ach,
+                        "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "peak_source": peak_src,
+                        "traffic": None},
+           "gpu_launches": sum(v["launches"] for v in prof.values()), "clocks": clk}
+    if not args.no_cpu_baseline:
+        import oracle
+        n_s = min(1000, n)
+        tt0 = time.perf_counter()
+        oracle.mloe_mmom(oracle.Theta(list(spec.sigma2), spec.a, list(spec.nu), spec.beta_matrix()),
+                         oracle.Theta(list(th_a_spec.sigma2), th_a_spec.a, list(th_a_spec.nu), th_a_spec.beta_matrix()),
+                         locs[:n_s], pred)
+        ts = time.perf_counter() - tt0
+        out["cpu_baseline"] = {"value": ts * (n / n_s) ** 3, "unit": "s", "cores": oracle.num_threads(),
+                               "kind": "oracle",
+                               "sample": "oracle at n = %d, m = %d in %.1f s, extrapolated by n^3" % (
+                                   n_s, args.mloe_m, ts)}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_serving_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -838,6 +929,11 @@ def main():
     args = parse()
     if args.workload == "serving":
         return run_serving_reference(args) if args.impl == "reference" else run_serving(args)
+    if args.workload == "mloe":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "mloe mode: the oracle time is this mode's cpu_baseline"}))
+            return 0
+        return run_mloe(args)
     if args.workload == "batch":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "batch mode: use the default workload's reference arm"}))
