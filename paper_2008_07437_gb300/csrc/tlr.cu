@@ -197,13 +197,15 @@ size_t tlr_factor_bytes(int N, int nb, int kmax) {
 size_t tlr_workspace_bytes(int N, int nb, int kmax) {
     const size_t T = ((size_t)N + nb - 1) / nb;
     const size_t rmax = std::min((size_t)kmax + 16, (size_t)nb);
-    const size_t per_tile = (4 * (size_t)nb * rmax + 4 * rmax * rmax + 4 * rmax) * sizeof(double);
+    const size_t per_tile = (5 * (size_t)nb * rmax + 4 * rmax * rmax + 4 * rmax) * sizeof(double);
     return sizeof(double) * ((size_t)N * nb                   // column panel W
                              + (size_t)nb * rmax                // Omega
                              + (size_t)nb * TLR_KCHUNK          // stacked U_jk chunk
                              + T * (size_t)nb * TLR_KCHUNK      // P_i per tile
-                             + T * TLR_MAXK_PER_CHUNK * (size_t)kmax * kmax)   // cores
-           + T * per_tile + 2 * TLR_ARENA_BYTES + (size_t)N * 2 * sizeof(double) + 4096;
+                             + T * TLR_MAXK_PER_CHUNK * (size_t)kmax * kmax   // cores
+                             + (size_t)TLR_KCHUNK * rmax        // Qc' Omega
+                             + T * (size_t)TLR_KCHUNK * rmax)   // P_i' Q_i per tile
+           + T * per_tile + 2 * TLR_ARENA_BYTES + (size_t)N * 2 * sizeof(double) + 16 * 256 + 4096;
 }
 
 cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, const double *ly, void *ws,
@@ -225,7 +227,10 @@ cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, cons
     double *Qc = (double *)take(sizeof(double) * (size_t)nb * TLR_KCHUNK);
     double *Pb = (double *)take(sizeof(double) * (size_t)T * nb * TLR_KCHUNK);
     double *Mb = (double *)take(sizeof(double) * (size_t)T * TLR_MAXK_PER_CHUNK * kmax * kmax);
-    const size_t per_tile = 4 * (size_t)nb * rmax + 4 * (size_t)rmax * rmax + 4 * (size_t)rmax;
+    double *Zb = (double *)take(sizeof(double) * (size_t)TLR_KCHUNK * rmax);
+    double *Tb = (double *)take(sizeof(double) * (size_t)T * TLR_KCHUNK * rmax);
+    // per tile: Y, Q, B', Q2 (nb x rmax), M, Vj, Ms, Vs (rmax^2), sigma, tau, v0, spare (rmax), saved Y (nb x rmax)
+    const size_t per_tile = 5 * (size_t)nb * rmax + 4 * (size_t)rmax * rmax + 4 * (size_t)rmax;
     double *TW = (double *)take(sizeof(double) * (size_t)T * per_tile);
     Arena arena;
     arena.dev = take(TLR_ARENA_BYTES);
@@ -263,111 +268,176 @@ cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, cons
             k_covgen_block<<<grid, 256, 0, s>>>(cp, lx, ly, l0, nl, r0, nr, W, ldw);
             TCK(cudaGetLastError());
         }
-        // 2. low-rank updates from the finished columns, in chunks of stacked rank
-        std::vector<int> ks;
-        for (int k = 0; k < j; ++k)
-            if (F.rank[slot(j, k)] > 0) ks.push_back(k);
-        size_t pos = 0;
-        while (pos < ks.size()) {
-            std::vector<int> chunk;
-            int Kc = 0;
-            while (pos < ks.size() && (int)chunk.size() < TLR_MAXK_PER_CHUNK &&
-                   Kc + F.rank[slot(j, ks[pos])] <= TLR_KCHUNK) {
-                Kc += F.rank[slot(j, ks[pos])];
-                chunk.push_back(ks[pos]);
-                ++pos;
-            }
-            std::vector<GemmDesc> dm, dp, dw;
-            int off = 0;
-            size_t mused = 0;
-            const size_t mcap = (size_t)T * TLR_MAXK_PER_CHUNK * kmax * kmax;
-            for (size_t ci = 0; ci < chunk.size(); ++ci) {
-                const int k = chunk[ci];
-                const size_t sjk = slot(j, k);
-                const int rjk = F.rank[sjk];
-                TCK(cudaMemcpyAsync(Qc + (size_t)off * nb, Uof(j, k), sizeof(double) * (size_t)nb * rjk,
-                                    cudaMemcpyDeviceToDevice, s));
-                for (int i = j; i < T; ++i) {
-                    // P_ik = U_ik (V_ik' V_jk), the block of columns [off, off + rjk) of P_i
-                    const size_t sik = slot(i, k);
-                    const int rik = F.rank[sik];
-                    if (rik == 0) continue;
-                    double *P = Pb + (size_t)(i - j) * nb * TLR_KCHUNK + (size_t)off * nb;
-                    if (F.dense[sjk]) {
-                        // V_jk = I: P = U_ik V_ik' (= U_ik itself when (i, k) is dense too)
-                        if (F.dense[sik])
-                            TCK(cudaMemcpyAsync(P, Uof(i, k), sizeof(double) * (size_t)nb * rjk, cudaMemcpyDeviceToDevice, s));
-                        else
-                            dp.push_back({mt(i), rjk, rik, 0, 1, Uof(i, k), nb, Vof(i, k), nb, P, nb, 1.0, 0.0});
-                    } else if (F.dense[sik]) {
-                        // V_ik = I: P = U_ik V_jk
-                        dp.push_back({mt(i), rjk, mt(k), 0, 0, Uof(i, k), nb, Vof(j, k), nb, P, nb, 1.0, 0.0});
-                    } else {
-                        double *M = Mb + mused;
-                        mused += (size_t)kmax * kmax;
-                        if (mused > mcap) return cudaErrorMemoryAllocation;
-                        dm.push_back({rik, rjk, nb, 1, 0, Vof(i, k), nb, Vof(j, k), nb, M, kmax, 1.0, 0.0});
-                        dp.push_back({mt(i), rjk, rik, 0, 0, Uof(i, k), nb, M, kmax, P, nb, 1.0, 0.0});
+        // 2. the updates of the finished columns k < j, applied implicitly:
+        //    W_ij = Sigma_ij - P_i Qc'  with  Qc = [U_jk]_k and P_i = [U_ik (V_ik' V_jk)]_k
+        //    (stacked over k in chunks).  Only the diagonal tile and the tiles
+        //    stored dense are formed; the others enter the randomized SVD through
+        //    Y_i = Sigma_ij Omega - P_i (Qc' Omega) and B_i' = Sigma_ij' Q_i - Qc (P_i' Q_i).
+        const int nt = T - j - 1;
+        std::vector<int> rk(nt, 0), rused(nt, 0), rwant(nt);
+        std::vector<char> dense_now(nt, 0);   // tiles formed densely with the diagonal tile (none)
+        for (int q = 0; q < nt; ++q) {
+            const int d = q + 1;
+            const int hint = (j > 0 && d < (int)rank_hint.size()) ? rank_hint[d] : 16;
+            // sketch width: the rank at the same distance in the previous column plus
+            // oversampling, rounded up to 32 (the widest sketch after a dense tile); the
+            // widest sketch if that fails.  Whether a tile is stored dense is decided by
+            // its own compression only (a forecast from the previous column would feed
+            // on itself and spread the dense band).
+            rwant[q] = std::min(rmax, std::max(32, (hint + 16 + 31) / 32 * 32));
+        }
+        auto Ysave = [&](int q) { return tb(q) + 4 * (size_t)nb * rmax + 4 * (size_t)rmax * rmax + 4 * (size_t)rmax; };
+        // for each chunk of row j's finished columns: Qc, and P_i for the tiles i in `rows`
+        // (i - j in 0 .. nt), then apply(Kc, has) with has[i - j] = some rank of the chunk in row i
+        auto chunk_loop = [&](const std::vector<int> &rows, auto &&apply) -> cudaError_t {
+            cudaError_t ce = cudaSuccess;
+            std::vector<int> ks;
+            for (int k = 0; k < j; ++k)
+                if (F.rank[slot(j, k)] > 0) ks.push_back(k);
+            size_t pos = 0;
+            while (pos < ks.size()) {
+                std::vector<int> chunk;
+                int Kc = 0;
+                while (pos < ks.size() && (int)chunk.size() < TLR_MAXK_PER_CHUNK &&
+                       Kc + F.rank[slot(j, ks[pos])] <= TLR_KCHUNK) {
+                    Kc += F.rank[slot(j, ks[pos])];
+                    chunk.push_back(ks[pos]);
+                    ++pos;
+                }
+                std::vector<GemmDesc> dm, dp;
+                std::vector<char> has(nt + 1, 0);
+                int off = 0;
+                size_t mused = 0;
+                const size_t mcap = (size_t)T * TLR_MAXK_PER_CHUNK * kmax * kmax;
+                for (size_t ci = 0; ci < chunk.size(); ++ci) {
+                    const int k = chunk[ci];
+                    const size_t sjk = slot(j, k);
+                    const int rjk = F.rank[sjk];
+                    if ((ce = cudaMemcpyAsync(Qc + (size_t)off * nb, Uof(j, k), sizeof(double) * (size_t)nb * rjk,
+                                              cudaMemcpyDeviceToDevice, s)))
+                        return ce;
+                    for (int i : rows) {
+                        // P_ik = U_ik (V_ik' V_jk), the block of columns [off, off + rjk) of P_i
+                        const size_t sik = slot(i, k);
+                        const int rik = F.rank[sik];
+                        if (rik == 0) continue;
+                        has[i - j] = 1;
+                        double *P = Pb + (size_t)(i - j) * nb * TLR_KCHUNK + (size_t)off * nb;
+                        if (F.dense[sjk]) {
+                            // V_jk = I: P = U_ik V_ik' (= U_ik itself when (i, k) is dense too)
+                            if (F.dense[sik]) {
+                                if ((ce = cudaMemcpyAsync(P, Uof(i, k), sizeof(double) * (size_t)nb * rjk,
+                                                          cudaMemcpyDeviceToDevice, s)))
+                                    return ce;
+                            } else {
+                                dp.push_back({mt(i), rjk, rik, 0, 1, Uof(i, k), nb, Vof(i, k), nb, P, nb, 1.0, 0.0});
+                            }
+                        } else if (F.dense[sik]) {
+                            // V_ik = I: P = U_ik V_jk
+                            dp.push_back({mt(i), rjk, mt(k), 0, 0, Uof(i, k), nb, Vof(j, k), nb, P, nb, 1.0, 0.0});
+                        } else {
+                            double *M = Mb + mused;
+                            mused += (size_t)kmax * kmax;
+                            if (mused > mcap) return cudaErrorMemoryAllocation;
+                            dm.push_back({rik, rjk, nb, 1, 0, Vof(i, k), nb, Vof(j, k), nb, M, kmax, 1.0, 0.0});
+                            dp.push_back({mt(i), rjk, rik, 0, 0, Uof(i, k), nb, M, kmax, P, nb, 1.0, 0.0});
+                        }
+                    }
+                    off += rjk;
+                }
+                // rows with something in this chunk: zero the P blocks of the k with rank 0 there
+                for (int i : rows) {
+                    if (!has[i - j]) continue;
+                    int o2 = 0;
+                    for (int k : chunk) {
+                        const int rjk = F.rank[slot(j, k)];
+                        if (F.rank[slot(i, k)] == 0 &&
+                            (ce = cudaMemsetAsync(Pb + (size_t)(i - j) * nb * TLR_KCHUNK + (size_t)o2 * nb, 0,
+                                                  sizeof(double) * (size_t)nb * rjk, s)))
+                            return ce;
+                        o2 += rjk;
                     }
                 }
-                off += rjk;
-            }
-            // tiles with nothing in this chunk still get a zero P block for the stacked product
-            for (int i = j; i < T; ++i) {
-                bool any = false;
-                for (int k : chunk) any = any || F.rank[slot(i, k)] > 0;
-                if (!any) continue;
-                // zero the P_i columns of this chunk for the k with rank 0 in row i
-                int o2 = 0;
-                for (int k : chunk) {
-                    const int rjk = F.rank[slot(j, k)];
-                    if (F.rank[slot(i, k)] == 0)
-                        TCK(cudaMemsetAsync(Pb + (size_t)(i - j) * nb * TLR_KCHUNK + (size_t)o2 * nb, 0,
-                                            sizeof(double) * (size_t)nb * rjk, s));
-                    o2 += rjk;
+                if (!dm.empty()) {
+                    GemmDesc *d1 = push(arena, dm, s, &ce);
+                    if (ce) return ce;
+                    if ((ce = launch_bgemm(d1, (int)dm.size(), gemm_tiles(dm), s, gemm_flops(dm)))) return ce;
                 }
-                dw.push_back({mt(i), mj, Kc, 0, 1, Pb + (size_t)(i - j) * nb * TLR_KCHUNK, nb, Qc, nb,
-                              W + (size_t)(i - j) * nb, ldw, -1.0, 1.0});
+                if (!dp.empty()) {
+                    GemmDesc *d2 = push(arena, dp, s, &ce);
+                    if (ce) return ce;
+                    if ((ce = launch_bgemm(d2, (int)dp.size(), gemm_tiles(dp), s, gemm_flops(dp)))) return ce;
+                }
+                if ((ce = apply(Kc, has))) return ce;
             }
-            if (!dm.empty()) {
-                GemmDesc *d1 = push(arena, dm, s, &e);
-                TCK(e);
-                TCK(launch_bgemm(d1, (int)dm.size(), gemm_tiles(dm), s, gemm_flops(dm)));
-            }
-            if (!dp.empty()) {
-                GemmDesc *d2 = push(arena, dp, s, &e);
-                TCK(e);
-                TCK(launch_bgemm(d2, (int)dp.size(), gemm_tiles(dp), s, gemm_flops(dp)));
-            }
-            if (!dw.empty()) {
-                GemmDesc *d3 = push(arena, dw, s, &e);
-                TCK(e);
-                TCK(launch_bgemm(d3, (int)dw.size(), gemm_tiles(dw), s, gemm_flops(dw)));
-            }
+            return ce;
+        };
+        auto Pof = [&](int i) { return Pb + (size_t)(i - j) * nb * TLR_KCHUNK; };
+        // dense update W_i -= P_i Qc' for the listed tiles
+        auto dense_update = [&](const std::vector<int> &rows, int Kc, const std::vector<char> &has) -> cudaError_t {
+            std::vector<GemmDesc> dw;
+            for (int i : rows)
+                if (has[i - j])
+                    dw.push_back({mt(i), mj, Kc, 0, 1, Pof(i), nb, Qc, nb, W + (size_t)(i - j) * nb, ldw, -1.0, 1.0});
+            if (dw.empty()) return cudaSuccess;
+            cudaError_t ce;
+            GemmDesc *d3 = push(arena, dw, s, &ce);
+            if (ce) return ce;
+            return launch_bgemm(d3, (int)dw.size(), gemm_tiles(dw), s, gemm_flops(dw));
+        };
+        // the Gaussian test matrix of this column and the raw sketches Y_i = Sigma_ij Omega
+        TCK(launch_gaussian(Om, (long long)nb * rmax, 0x5EEDull * (j + 1), s));
+        std::vector<int> all_rows{j}, dense_rows{j}, lr_rows;
+        for (int q = 0; q < nt; ++q) {
+            all_rows.push_back(j + 1 + q);
+            (dense_now[q] ? dense_rows : lr_rows).push_back(j + 1 + q);
         }
+        if (!lr_rows.empty()) {
+            std::vector<GemmDesc> dy0;
+            for (int i : lr_rows)
+                dy0.push_back({mt(i), rmax, mj, 0, 0, W + (size_t)(i - j) * nb, ldw, Om, nb, Ysave(i - j - 1), nb,
+                               1.0, 0.0});
+            GemmDesc *g0 = push(arena, dy0, s, &e);
+            TCK(e);
+            TCK(launch_bgemm(g0, (int)dy0.size(), gemm_tiles(dy0), s, gemm_flops(dy0)));
+        }
+        TCK(chunk_loop(all_rows, [&](int Kc, const std::vector<char> &has) -> cudaError_t {
+            cudaError_t ce = dense_update(dense_rows, Kc, has);
+            if (ce || lr_rows.empty()) return ce;
+            // Z = Qc' Omega, then Y_i -= P_i Z
+            std::vector<GemmDesc> dz{{Kc, rmax, mj, 1, 0, Qc, nb, Om, nb, Zb, TLR_KCHUNK, 1.0, 0.0}};
+            std::vector<GemmDesc> dy;
+            for (int i : lr_rows)
+                if (has[i - j])
+                    dy.push_back({mt(i), rmax, Kc, 0, 0, Pof(i), nb, Zb, TLR_KCHUNK, Ysave(i - j - 1), nb, -1.0, 1.0});
+            GemmDesc *gz = push(arena, dz, s, &ce);
+            if (ce) return ce;
+            if ((ce = launch_bgemm(gz, 1, gemm_tiles(dz), s, gemm_flops(dz)))) return ce;
+            if (dy.empty()) return cudaSuccess;
+            GemmDesc *gy = push(arena, dy, s, &ce);
+            if (ce) return ce;
+            return launch_bgemm(gy, (int)dy.size(), gemm_tiles(dy), s, gemm_flops(dy));
+        }));
         // 3. diagonal tile in FP64
         TCK(chol64_panel(W, ldw, 0, mj, mj, mj, st, s));
         TCK(cudaMemcpy2DAsync(F.D + (size_t)j * nb * nb, sizeof(double) * nb, W, sizeof(double) * ldw,
                               sizeof(double) * mj, mj, cudaMemcpyDeviceToDevice, s));
         if (j == T - 1) break;
         // 4. compress the tiles below: first with a narrow sketch, then the widest one where needed
-        const int nt = T - j - 1;
-        TCK(launch_gaussian(Om, (long long)nb * rmax, 0x5EEDull * (j + 1), s));
-        std::vector<int> todo(nt), rk(nt, -1), rused(nt, 0), rwant(nt);
-        std::iota(todo.begin(), todo.end(), 0);
-        std::vector<std::vector<int>> sel(nt);
-        // sketch width: the rank found at the same distance from the diagonal in the
-        // previous column plus oversampling, rounded up to 32; the widest sketch if that fails
+        std::vector<int> todo;
         for (int q = 0; q < nt; ++q) {
-            const int d = q + 1;
-            const int hint = (j > 0 && d < (int)rank_hint.size()) ? rank_hint[d] : 16;
-            rwant[q] = std::min(rmax, std::max(32, (hint + 16 + 31) / 32 * 32));
+            if (dense_now[q])
+                rk[q] = -1;
+            else
+                todo.push_back(q);
         }
+        std::vector<std::vector<int>> sel(nt);
         for (int pass = 0; pass < 2 && !todo.empty(); ++pass) {
-            std::vector<GemmDesc> dy, db;
+            std::vector<GemmDesc> db;
             std::vector<QrDesc> dq1, dq2;
             std::vector<TlrR2Desc> dr;
             std::vector<SvdDesc> dsv;
+            std::vector<int> rows_b;
             int r = 0;
             for (int q : todo) r = std::max(r, std::min(std::min(pass == 0 ? rwant[q] : rmax, mj), mt(j + 1 + q)));
             for (int q : todo) {
@@ -380,23 +450,42 @@ cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, cons
                 double *Vs = Ms + (size_t)rmax * rmax, *sig = Vs + (size_t)rmax * rmax, *tau = sig + rmax;
                 double *v0 = tau + rmax;
                 double *Wi = W + (size_t)(i - j) * nb;
-                dy.push_back({mi, rr, mj, 0, 0, Wi, ldw, Om, nb, Y, nb, 1.0, 0.0});
+                // the first rr columns of the saved sketch (the QR works in place)
+                TCK(cudaMemcpyAsync(Y, Ysave(q), sizeof(double) * (size_t)nb * rr, cudaMemcpyDeviceToDevice, s));
                 dq1.push_back({mi, rr, Y, nb, Q, nb, tau, v0});
                 db.push_back({mj, rr, mi, 1, 0, Wi, ldw, Q, nb, Bt, nb, 1.0, 0.0});
                 dq2.push_back({mj, rr, Bt, nb, Q2, nb, tau, v0});
                 dr.push_back({rr, Bt, nb, M, rmax});
                 dsv.push_back({rr, M, Vj, rmax, sig, F.tol / 16.0});
                 rused[q] = rr;
+                rows_b.push_back(i);
             }
-            GemmDesc *g1 = push(arena, dy, s, &e);
-            TCK(e);
-            TCK(launch_bgemm(g1, (int)dy.size(), gemm_tiles(dy), s, gemm_flops(dy)));
             QrDesc *q1 = push(arena, dq1, s, &e);
             TCK(e);
             TCK(launch_house_qr(q1, (int)dq1.size(), s, 4.0 * (double)dq1.size() * nb * r * r));
             GemmDesc *g2 = push(arena, db, s, &e);
             TCK(e);
             TCK(launch_bgemm(g2, (int)db.size(), gemm_tiles(db), s, gemm_flops(db)));
+            // B_i' -= Qc (P_i' Q_i)
+            TCK(chunk_loop(rows_b, [&](int Kc, const std::vector<char> &has) -> cudaError_t {
+                std::vector<GemmDesc> dt1, dt2;
+                for (int i : rows_b) {
+                    if (!has[i - j]) continue;
+                    const int q = i - j - 1;
+                    double *Q = tb(q) + (size_t)nb * rmax, *Bt = Q + (size_t)nb * rmax;
+                    double *Tq = Tb + (size_t)q * TLR_KCHUNK * rmax;
+                    dt1.push_back({Kc, rused[q], mt(i), 1, 0, Pof(i), nb, Q, nb, Tq, TLR_KCHUNK, 1.0, 0.0});
+                    dt2.push_back({mj, rused[q], Kc, 0, 0, Qc, nb, Tq, TLR_KCHUNK, Bt, nb, -1.0, 1.0});
+                }
+                if (dt1.empty()) return cudaSuccess;
+                cudaError_t ce;
+                GemmDesc *h1 = push(arena, dt1, s, &ce);
+                if (ce) return ce;
+                if ((ce = launch_bgemm(h1, (int)dt1.size(), gemm_tiles(dt1), s, gemm_flops(dt1)))) return ce;
+                GemmDesc *h2 = push(arena, dt2, s, &ce);
+                if (ce) return ce;
+                return launch_bgemm(h2, (int)dt2.size(), gemm_tiles(dt2), s, gemm_flops(dt2));
+            }));
             QrDesc *q2 = push(arena, dq2, s, &e);
             TCK(e);
             TCK(launch_house_qr(q2, (int)dq2.size(), s, 4.0 * (double)dq2.size() * nb * r * r));
@@ -448,6 +537,16 @@ cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, cons
                 sel[q].assign(idx.begin(), idx.begin() + k);
             }
             todo = next;
+        }
+        // tiles found dense during the compression: form them (W_i -= P_i Qc') before their TRSM
+        {
+            std::vector<int> late;
+            for (int q = 0; q < nt; ++q)
+                if (rk[q] < 0 && !dense_now[q]) late.push_back(j + 1 + q);
+            if (!late.empty())
+                TCK(chunk_loop(late, [&](int Kc, const std::vector<char> &has) -> cudaError_t {
+                    return dense_update(late, Kc, has);
+                }));
         }
         // U = Q (M Vj)[:, sel], V = Q2 Vj[:, sel]
         {
