@@ -242,6 +242,28 @@ def predict(theta: Theta, locs, Z, new_locs, L=None) -> np.ndarray:
     return zhat
 
 
+def predict_var(theta: Theta, locs, new_locs, L=None) -> np.ndarray:
+    """Prediction (cokriging) variances, the diagonal of C(0) - c0' Sigma^-1 c0 at
+    every new location (the mean square error of Eq. 3's predictor under the
+    true model, the E_t term of Eq. 5 before the trace); p m entries, Rep. I."""
+    locs = _f64(locs).reshape(-1, 2)
+    new_locs = _f64(new_locs).reshape(-1, 2)
+    if L is None:
+        L, info = cholesky(covgen(theta, locs))
+        if info:
+            raise ValueError("Sigma not positive definite (info=%d)" % info)
+    p = theta.p
+    out = np.empty(p * new_locs.shape[0])
+    for l in range(new_locs.shape[0]):
+        s0 = new_locs[l:l + 1]
+        c0 = covgen(theta, locs, s0)                 # (p n) x p
+        C0 = covgen(theta, s0)                       # p x p
+        for i in range(p):
+            y = forward(L, c0[:, i])                 # L^-1 c0_i
+            out[p * l + i] = C0[i, i] - float(y @ y)
+    return out
+
+
 def simulate(theta: Theta, locs, e) -> np.ndarray:
     """Z = L e with L L' = Sigma(theta): a draw from N(0, Sigma) given standard normals e."""
     L, info = cholesky(covgen(theta, locs))

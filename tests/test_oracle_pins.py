@@ -439,3 +439,44 @@ def test_mloe_nonnegative_for_misspecified():
     pred = inputs.jittered_grid(5, 123)
     mloe, mmom, loe, mom = oracle.mloe_mmom(th, tha, locs, pred)
     assert np.all(loe >= -1e-12)
+
+
+# ---- prediction variance (diag of C(0) - c0' Sigma^-1 c0) --------------------
+
+def test_predict_var_zero_at_observed_locations_and_bounded():
+    th = oracle.Theta([1.0, 2.0], 0.1, [0.5, 1.0], np.array([[1.0, 0.5], [0.5, 1.0]]))
+    locs = inputs.jittered_grid(60, 5)
+    v_obs = oracle.predict_var(th, locs, locs[[3, 17, 42]])
+    assert np.all(np.abs(v_obs) < 1e-10)   # no nugget: an observed location is known exactly
+    new = inputs.jittered_grid(25, 6)
+    v = oracle.predict_var(th, locs, new)
+    s2 = np.tile([1.0, 2.0], 25)
+    assert np.all(v >= -1e-12) and np.all(v <= s2 + 1e-12)
+
+
+def test_predict_var_far_from_the_data_is_the_prior_variance():
+    th = oracle.Theta([1.3, 0.7], 0.02, [0.5, 1.5], np.array([[1.0, -0.4], [-0.4, 1.0]]))
+    locs = inputs.jittered_grid(40, 7) * 0.2          # all data in [0, 0.2]^2
+    v = oracle.predict_var(th, locs, np.array([[0.95, 0.95]]))
+    # the nearest datum is > 1 away, 50 a: every covariance with it is below e^-50
+    assert v == pytest.approx([1.3, 0.7], abs=1e-15)
+
+
+def test_predict_var_beta_zero_is_univariate_kriging():
+    thb = oracle.Theta([1.0, 2.0], 0.1, [0.5, 1.5], np.eye(2))
+    locs = inputs.jittered_grid(50, 8)
+    new = inputs.jittered_grid(10, 9)
+    v = oracle.predict_var(thb, locs, new)
+    for i, (s2, nu) in enumerate([(1.0, 0.5), (2.0, 1.5)]):
+        th1 = oracle.Theta([s2], 0.1, [nu], np.eye(1))
+        assert v[i::2] == pytest.approx(oracle.predict_var(th1, locs, new), rel=1e-12, abs=1e-14)
+
+
+def test_predict_var_matches_library_solve():
+    th = oracle.Theta([1.0, 1.0], 0.09, [0.5, 1.0], np.array([[1.0, 0.5], [0.5, 1.0]]))
+    locs = inputs.jittered_grid(70, 10)
+    new = inputs.jittered_grid(8, 11)
+    S = oracle.covgen(th, locs)
+    c0 = oracle.covgen(th, locs, new)                     # (2 * 70) x (2 * 8)
+    ref = np.diag(oracle.covgen(th, new)) - np.einsum("ij,ij->j", c0, np.linalg.solve(S, c0))
+    assert oracle.predict_var(th, locs, new) == pytest.approx(ref, rel=1e-9, abs=1e-12)
