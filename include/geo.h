@@ -261,6 +261,18 @@ int geo_loglik_batch(geo_ctx *ctx, int count, const geo_batch_item *items, doubl
                      void *stream);
 
 /*
+ * Prediction (cokriging) variances on a kept factor: the diagonal of
+ * C(0) - c0' Sigma^-1 c0 at each new location s0, i.e. the mean square error
+ * of the Eq. 3 predictor under the model (the E_t term of Eq. 5).
+ *   new_locs_dev  m x 2 (device);  var_dev  p m doubles (device), Representation I
+ * Dense FP64 or mixed factors (GEO_EUNSUPPORTED for tile low-rank ones); cost
+ * N^2 p m flops (a right-side triangular solve of the m cross-covariances).
+ * Synchronises `stream`.
+ */
+int geo_predict_var(geo_ctx *ctx, const geo_factor *factor, const double *new_locs_dev, int m, double *var_dev,
+                    void *stream);
+
+/*
  * Multivariate MLOE / MMOM (Eq. 5 - Eq. 8, Algorithm 1 of Sec. 5.4): how much
  * cokriging with theta_a instead of the true theta_t loses in prediction
  * efficiency (LOE) and misstates the mean square prediction error (MOM),

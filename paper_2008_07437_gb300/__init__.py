@@ -113,6 +113,7 @@ SIGNATURES = {
     "geo_profile_enable": (_I, [_P, _I]),
     "geo_profile_read": (_I, [_P, ctypes.POINTER(geo_kstat)]),
     "geo_server_profile_read": (_I, [_P, ctypes.POINTER(geo_kstat)]),
+    "geo_predict_var": (_I, [_P, _P, _P, _I, _P, _P]),
     "geo_mloe_mmom": (_I, [_P, _P, _I, _P, _I, ctypes.POINTER(geo_theta), ctypes.POINTER(geo_theta), _P, _P, _P, _P,
                            _P, _P]),
     "geo_loglik_noalloc": (_I, [_P, _I, _P, ctypes.POINTER(geo_theta), _I, _P, _P, _P]),
@@ -529,6 +530,14 @@ class Server:
         if self.handle:
             self.lib.geo_server_destroy(self.handle)
             self.handle = None
+
+
+def geo_predict_var(ctx: Context, factor: "Factor", new_locs, out, stream=None):
+    """Prediction variances diag(C(0) - c0' Sigma^-1 c0) at new_locs into out (p m doubles, device)."""
+    import torch
+    ctx.check(ctx.lib.geo_predict_var(ctx.handle, factor.handle, _dev_ptr(new_locs, "new_locs", torch.float64),
+                                      new_locs.shape[0], _dev_ptr(out, "out", torch.float64), _stream(stream)))
+    return out
 
 
 def geo_mloe_mmom(ctx: Context, locs, pred, theta_t: Theta, theta_a: Theta, options: geo_opts | None = None,

@@ -1030,6 +1030,44 @@ int geo_loglik_batch(geo_ctx *ctx, int count, const geo_batch_item *items, doubl
     return GEO_OK;
 }
 
+int geo_predict_var(geo_ctx *ctx, const geo_factor *factor, const double *new_locs_dev, int m, double *var_dev,
+                    void *stream) {
+    if (!ctx || !factor) return GEO_EINVAL;
+    ProfBind pb(&ctx->prof);
+    if (m < 0) return fail(ctx, GEO_EINVAL, "m < 0");
+    if (m == 0) return GEO_OK;
+    if (!new_locs_dev || !var_dev) return fail(ctx, GEO_EINVAL, "NULL pointer");
+    if (factor->tlr) return fail(ctx, GEO_EUNSUPPORTED, "prediction variances need a dense or mixed factor");
+    SetDevice sd(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const geo_factor *f = factor;
+    const int p = f->p, N = f->N, pm = p * m;
+    const long long ldx = round_up(pm, 32);
+    const size_t xbytes = sizeof(double) * (size_t)ldx * N, sbytes = sizeof(double) * pm,
+                 dbytes = sizeof(GemmDesc) * 64;
+    void *px = nullptr, *ps = nullptr, *pd = nullptr;
+    auto done = [&](int code) {
+        cudaStreamSynchronize(s);
+        if (px) dev_free(ctx, px, xbytes);
+        if (ps) dev_free(ctx, ps, sbytes);
+        if (pd) dev_free(ctx, pd, dbytes);
+        return code;
+    };
+    int rc;
+    if ((rc = dev_alloc(ctx, &px, xbytes)) || (rc = dev_alloc(ctx, &ps, sbytes)) || (rc = dev_alloc(ctx, &pd, dbytes)))
+        return done(rc);
+    double c0d[GEO_PMAX];
+    for (int i = 0; i < p; ++i) c0d[i] = f->cp.m[i * p + i].c0;
+    cudaError_t e;
+    // X = c0' (p m x N, the factor's location order), X <- X L^-T = (L^-1 c0)', var = C_ii(0) - |row|^2
+    if ((e = launch_covgen_cross(f->cp, new_locs_dev, m, f->lx, f->ly, f->n, (double *)px, ldx, s)) ||
+        (e = trsm_right_upper_t((double *)px, ldx, pm, f->A, f->ld, N, pd, s)) ||
+        (e = launch_row_sums((double *)px, ldx, nullptr, 0, pm, N, (double *)ps, nullptr, s)) ||
+        (e = launch_var_finish((const double *)ps, pm, p, c0d, var_dev, s)))
+        return done(cuda_fail(ctx, e, "geo_predict_var"));
+    return done(GEO_OK);
+}
+
 int geo_mloe_mmom(geo_ctx *ctx, const double *locs_dev, int n, const double *pred_dev, int m,
                   const geo_theta *theta_t, const geo_theta *theta_a, const geo_opts *opts, double *mloe,
                   double *mmom, double *loe_host, double *mom_host, void *stream) {

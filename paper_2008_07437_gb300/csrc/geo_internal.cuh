@@ -117,6 +117,11 @@ cudaError_t launch_row_sums(const double *X, long long ldx, const double *Y, lon
 // X <- X L^-1 (X: R x N, L lower); arena_dev: 64 GemmDesc of device scratch.
 cudaError_t trsm_right_lower(double *X, long long ldx, int R, const double *L, long long ldl, int N, void *arena_dev,
                              cudaStream_t s);
+// X <- X L^-T (X: R x N, L lower); arena_dev: 64 GemmDesc of device scratch.
+cudaError_t trsm_right_upper_t(double *X, long long ldx, int R, const double *L, long long ldl, int N,
+                               void *arena_dev, cudaStream_t s);
+// var[q] = c0diag[q mod p] - sums[q] (device arrays of R doubles).
+cudaError_t launch_var_finish(const double *sums, int R, int p, const double *c0diag, double *var, cudaStream_t s);
 // V = X L (L lower; the upper parts of its 64 x 64 diagonal blocks are zeroed);
 // arena_dev / arena_host (pinned): ceil(N / 64) GemmDesc each.
 cudaError_t trmm_right_lower(const double *X, long long ldx, int R, double *L, long long ldl, int N, double *V,

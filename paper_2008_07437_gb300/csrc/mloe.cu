@@ -74,6 +74,44 @@ __global__ void __launch_bounds__(128) k_trsm_right_lower_diag(double *X, long l
         if (c < cb) X[(long long)(c0 + c) * ldx + q] = x[c];
 }
 
+// X[:, c0 .. c0 + cb) <- X[:, c0 ..) L[c0 .., c0 ..)^-T: per row,
+// x_c = (b_c - sum_{k < c} x_k L[c, k]) / L[c, c] from the first column; one thread per row.
+__global__ void __launch_bounds__(128) k_trsm_right_upper_diag(double *X, long long ldx, int R, const double *L,
+                                                               long long ldl, int c0, int cb) {
+    __shared__ double Ls[XB][XB + 1];   // Ls[c][k] = L[c0 + c, c0 + k], k <= c
+    for (int e = threadIdx.x; e < XB * XB; e += blockDim.x) {
+        const int k = e / XB, c = e % XB;
+        Ls[c][k] = (k < cb && c < cb && k <= c) ? L[(long long)(c0 + k) * ldl + c0 + c] : 0.0;
+    }
+    __syncthreads();
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= R) return;
+    double x[XB];
+#pragma unroll
+    for (int c = 0; c < XB; ++c) x[c] = (c < cb) ? X[(long long)(c0 + c) * ldx + q] : 0.0;
+#pragma unroll
+    for (int c = 0; c < XB; ++c) {
+        if (c < cb) {
+            double t = x[c];
+#pragma unroll
+            for (int k = 0; k < c; ++k) t -= x[k] * Ls[c][k];
+            x[c] = t / Ls[c][c];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < XB; ++c)
+        if (c < cb) X[(long long)(c0 + c) * ldx + q] = x[c];
+}
+
+// var[q] = C_ii(0) - s[q], i = q mod p.
+__global__ void k_var_finish(const double *s, int R, int p, double c0, double c1, double c2, double c3, double *var) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= R) return;
+    const int i = q % p;
+    const double c = (i == 0) ? c0 : (i == 1) ? c1 : (i == 2) ? c2 : c3;
+    var[q] = c - s[q];
+}
+
 // Zero the strictly upper part of every 64 x 64 diagonal block of L (those
 // entries are never part of the factor), so that block products see a lower
 // triangle.
@@ -130,6 +168,42 @@ cudaError_t trsm_right_lower(double *X, long long ldx, int R, const double *L, l
         }
     }
     return cudaSuccess;
+}
+
+// X <- X L^-T (X: R x N, L lower), by 64-column blocks from the first:
+// X_J <- X_J L_JJ^-T, then X[:, J+1:] -= X_J L[J+1:, J]'.
+cudaError_t trsm_right_upper_t(double *X, long long ldx, int R, const double *L, long long ldl, int N,
+                               void *arena_dev, cudaStream_t s) {
+    if (R <= 0 || N <= 0) return cudaSuccess;
+    GemmDesc *gd = (GemmDesc *)arena_dev;
+    const int nblk = (N + XB - 1) / XB;
+    for (int J = 0; J < nblk; ++J) {
+        const int c0 = J * XB, cb = min(XB, N - c0);
+        {
+            KScope ks(GEO_K_SOLVE, s, (double)R * cb * cb, 8.0 * 2.0 * R * cb);
+            k_trsm_right_upper_diag<<<(R + 127) / 128, 128, 0, s>>>(X, ldx, R, L, ldl, c0, cb);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const int rest = N - c0 - cb;
+        if (rest > 0) {
+            GemmDesc g{R, rest, cb, 0, 1, X + (long long)c0 * ldx, ldx, L + (long long)c0 * ldl + c0 + cb, ldl,
+                       X + (long long)(c0 + cb) * ldx, ldx, -1.0, 1.0};
+            GemmDesc *d = gd + (J % 64);
+            if ((e = cudaMemcpyAsync(d, &g, sizeof(g), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+            if ((e = launch_bgemm(d, 1, ((R + 63) / 64) * ((rest + 63) / 64), s, 2.0 * R * rest * cb)) != cudaSuccess)
+                return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_var_finish(const double *sums, int R, int p, const double *c0diag, double *var, cudaStream_t s) {
+    if (R <= 0) return cudaSuccess;
+    KScope ks(GEO_K_AUX, s);
+    k_var_finish<<<(R + 255) / 256, 256, 0, s>>>(sums, R, p, c0diag[0], p > 1 ? c0diag[1] : 0.0,
+                                                 p > 2 ? c0diag[2] : 0.0, p > 3 ? c0diag[3] : 0.0, var);
+    return cudaGetLastError();
 }
 
 // V = X L (X: R x N, L lower with its diagonal blocks' upper parts zeroed
