@@ -172,6 +172,135 @@ __global__ void __launch_bounds__(LA_THREADS) k_house_qr(const QrDesc *__restric
     }
 }
 
+// ---- the same Householder QR on a cluster of QC CTAs ------------------------
+// Rows are split over the CTAs of a cluster (the block stays in global
+// memory, which L2 holds); per column c the CTAs exchange partial norms, then
+// partial products v'y_j for the trailing columns, through distributed shared
+// memory, every CTA forming alpha, v0, tau and the dots in rank order (so all
+// take the same values), and each updates its own rows.  The thin Q is
+// accumulated the same way.  r <= QR_MAX.
+constexpr int QC = 8, QT = 256, QR_MAX = 256;
+
+size_t house_qr_cl_smem(int m) {
+    const int rs = (m + QC - 1) / QC;
+    return sizeof(double) * ((size_t)rs + 2 * (QR_MAX + 2) + 2 * QR_MAX);
+}
+
+__global__ void __launch_bounds__(QT, 1) k_house_qr_cl(const QrDesc *__restrict__ d, int count) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int tile = blockIdx.x / QC;
+    if (tile >= count) return;   // uniform over the cluster
+    const int rank = (int)cluster.block_rank();
+    const QrDesc q = d[tile];
+    double *Y = q.Y;
+    const long long ld = q.ldy;
+    const int m = q.m, r = q.r;
+    const int rs = (m + QC - 1) / QC;
+    const int row0 = rank * rs, row1 = min(m, row0 + rs);
+    extern __shared__ double qsm[];
+    double *vloc = qsm;                       // reflector on this CTA's rows (row c holds v0)
+    double *P = vloc + rs;                    // [2][QR_MAX + 2]: partial dots, then norm, x_c
+    double *taus = P + 2 * (QR_MAX + 2);      // [QR_MAX]
+    double *v0s = taus + QR_MAX;              // [QR_MAX]
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = QT / 32;
+    int buf = 0;
+    for (int c = 0; c < r; ++c) {
+        double *Pb = P + buf * (QR_MAX + 2);
+        const double *x = Y + (long long)c * ld;
+        // (a) partial |x[c:]|^2 over this CTA's rows; the owner of row c also passes x_c
+        const int i0 = max(c, row0);
+        double t = 0.0;
+        for (int i = i0 + threadIdx.x; i < row1; i += QT) t = fma(x[i], x[i], t);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        __shared__ double red[QT / 32];
+        if (lane == 0) red[warp] = t;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0;
+            for (int w = 0; w < nw; ++w) a += red[w];
+            Pb[QR_MAX] = a;
+            Pb[QR_MAX + 1] = (c >= row0 && c < row1) ? x[c] : 0.0;
+        }
+        cluster.sync();
+        // (b) alpha, v0, tau (the same in every CTA)
+        double nrm2 = 0.0;
+        for (int k = 0; k < QC; ++k) nrm2 += cluster.map_shared_rank(Pb, k)[QR_MAX];
+        const double x0 = cluster.map_shared_rank(Pb, c / rs)[QR_MAX + 1];
+        const double nrm = sqrt(nrm2);
+        double alpha = (x0 >= 0.0) ? -nrm : nrm;
+        double v0 = x0 - alpha, tauc;
+        if (nrm == 0.0) {
+            alpha = 0.0;
+            v0 = 1.0;
+            tauc = 0.0;
+        } else {
+            const double vtv = v0 * v0 + (nrm2 - x0 * x0);
+            tauc = (vtv > 0.0) ? 2.0 / vtv : 0.0;
+        }
+        // the reflector on this CTA's rows
+        for (int i = i0 + threadIdx.x; i < row1; i += QT) vloc[i - row0] = (i == c) ? v0 : x[i];
+        __syncthreads();
+        // (c) partial v'y_j for j > c: warp per column, lanes over rows
+        for (int j = c + 1 + warp; j < r; j += nw) {
+            const double *y = Y + (long long)j * ld;
+            double dot = 0.0;
+            for (int i = i0 + lane; i < row1; i += 32) dot = fma(vloc[i - row0], y[i], dot);
+            for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
+            if (lane == 0) Pb[j] = dot;
+        }
+        cluster.sync();
+        // (d) y_j -= tau (v'y_j) v on this CTA's rows
+        for (int j = c + 1 + warp; j < r; j += nw) {
+            double dot = 0.0;
+            for (int k = 0; k < QC; ++k) dot += cluster.map_shared_rank(Pb, k)[j];
+            dot *= tauc;
+            double *y = Y + (long long)j * ld;
+            for (int i = i0 + lane; i < row1; i += 32) y[i] -= dot * vloc[i - row0];
+        }
+        if (threadIdx.x == 0) {
+            taus[c] = tauc;
+            v0s[c] = v0;
+            if (c >= row0 && c < row1) {
+                Y[(long long)c * ld + c] = alpha;   // R diagonal
+                q.tau[c] = tauc;
+                q.v0[c] = v0;
+            }
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+    // thin Q: [I; 0] on this CTA's rows, then H_c for c = r-1 .. 0
+    double *Q = q.Q;
+    const long long ldq = q.ldq;
+    for (int j = warp; j < r; j += nw)
+        for (int i = row0 + lane; i < row1; i += 32) Q[(long long)j * ldq + i] = (i == j) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int c = r - 1; c >= 0; --c) {
+        double *Pb = P + buf * (QR_MAX + 2);
+        const double *x = Y + (long long)c * ld;
+        const int i0 = max(c, row0);
+        const double v0 = v0s[c], tauc = taus[c];
+        for (int j = c + warp; j < r; j += nw) {
+            const double *y = Q + (long long)j * ldq;
+            double dot = 0.0;
+            for (int i = i0 + lane; i < row1; i += 32) dot = fma((i == c) ? v0 : x[i], y[i], dot);
+            for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
+            if (lane == 0) Pb[j] = dot;
+        }
+        cluster.sync();
+        for (int j = c + warp; j < r; j += nw) {
+            double dot = 0.0;
+            for (int k = 0; k < QC; ++k) dot += cluster.map_shared_rank(Pb, k)[j];
+            dot *= tauc;
+            double *y = Q + (long long)j * ldq;
+            for (int i = i0 + lane; i < row1; i += 32) y[i] -= dot * ((i == c) ? v0 : x[i]);
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+    cluster.sync();   // no CTA leaves while another still reads its shared memory
+}
+
 // ---- one-sided Jacobi SVD of an r x r block M (Hestenes) --------------------
 // Rotates column pairs of M (and accumulates V) until every pair is
 // orthogonal to relative 1e-13 or the sweep budget is spent (pairs whose
@@ -402,11 +531,29 @@ cudaError_t launch_bgemm(const GemmDesc *d_desc, int count, int max_tiles, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_house_qr(const QrDesc *d_desc, int count, cudaStream_t s, double flops) {
+cudaError_t launch_house_qr(const QrDesc *d_desc, int count, int mmax, int rmax, cudaStream_t s, double flops) {
     if (count <= 0) return cudaSuccess;
     KScope ks(GEO_K_TLR, s, flops, 0.0);
-    k_house_qr<<<count, LA_THREADS, 0, s>>>(d_desc, count);
-    return cudaGetLastError();
+    if (rmax > QR_MAX) {
+        k_house_qr<<<count, LA_THREADS, 0, s>>>(d_desc, count);
+        return cudaGetLastError();
+    }
+    const size_t smem = house_qr_cl_smem(mmax);
+    cudaError_t e = cudaFuncSetAttribute(k_house_qr_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)count * QC);
+    cfg.blockDim = dim3(QT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = QC;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_house_qr_cl, d_desc, count);
 }
 
 cudaError_t launch_jacobi_svd(const SvdDesc *d_desc, int count, int max_sweeps, int rmax, cudaStream_t s,

@@ -188,7 +188,8 @@ struct SvdDesc {            // one-sided Jacobi SVD of M (r x r): M <- M V, V, s
     double skip;            // pairs of columns both below this norm are left alone (0 = none)
 };
 cudaError_t launch_bgemm(const GemmDesc *d_desc, int count, int max_tiles, cudaStream_t s, double flops);
-cudaError_t launch_house_qr(const QrDesc *d_desc, int count, cudaStream_t s, double flops);
+// mmax, rmax: the largest m and r of the batch (the cluster kernel serves r <= 256).
+cudaError_t launch_house_qr(const QrDesc *d_desc, int count, int mmax, int rmax, cudaStream_t s, double flops);
 // rmax: the largest r of the batch (the cluster kernel serves r <= 256).
 cudaError_t launch_jacobi_svd(const SvdDesc *d_desc, int count, int max_sweeps, int rmax, cudaStream_t s,
                               double flops);

@@ -462,7 +462,7 @@ cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, cons
             }
             QrDesc *q1 = push(arena, dq1, s, &e);
             TCK(e);
-            TCK(launch_house_qr(q1, (int)dq1.size(), s, 4.0 * (double)dq1.size() * nb * r * r));
+            TCK(launch_house_qr(q1, (int)dq1.size(), nb, r, s, 4.0 * (double)dq1.size() * nb * r * r));
             GemmDesc *g2 = push(arena, db, s, &e);
             TCK(e);
             TCK(launch_bgemm(g2, (int)db.size(), gemm_tiles(db), s, gemm_flops(db)));
@@ -488,7 +488,7 @@ cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, cons
             }));
             QrDesc *q2 = push(arena, dq2, s, &e);
             TCK(e);
-            TCK(launch_house_qr(q2, (int)dq2.size(), s, 4.0 * (double)dq2.size() * nb * r * r));
+            TCK(launch_house_qr(q2, (int)dq2.size(), nb, r, s, 4.0 * (double)dq2.size() * nb * r * r));
             TlrR2Desc *r2 = push(arena, dr, s, &e);
             TCK(e);
             {
