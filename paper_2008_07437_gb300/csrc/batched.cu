@@ -240,13 +240,25 @@ __global__ void __launch_bounds__(QT, 1) k_house_qr_cl(const QrDesc *__restrict_
         // the reflector on this CTA's rows
         for (int i = i0 + threadIdx.x; i < row1; i += QT) vloc[i - row0] = (i == c) ? v0 : x[i];
         __syncthreads();
-        // (c) partial v'y_j for j > c: warp per column, lanes over rows
-        for (int j = c + 1 + warp; j < r; j += nw) {
-            const double *y = Y + (long long)j * ld;
-            double dot = 0.0;
-            for (int i = i0 + lane; i < row1; i += 32) dot = fma(vloc[i - row0], y[i], dot);
-            for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
-            if (lane == 0) Pb[j] = dot;
+        // (c) partial v'y_j for j > c: a warp per pair of columns, lanes over rows
+        for (int j = c + 1 + warp; j < r; j += 2 * nw) {
+            const int j2 = j + nw;
+            const double *y = Y + (long long)j * ld, *y2 = Y + (long long)(j2 < r ? j2 : j) * ld;
+            double dot = 0.0, dot2 = 0.0;
+#pragma unroll 4
+            for (int i = i0 + lane; i < row1; i += 32) {
+                const double v = vloc[i - row0];
+                dot = fma(v, y[i], dot);
+                dot2 = fma(v, y2[i], dot2);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                dot += __shfl_down_sync(0xffffffffu, dot, o);
+                dot2 += __shfl_down_sync(0xffffffffu, dot2, o);
+            }
+            if (lane == 0) {
+                Pb[j] = dot;
+                if (j2 < r) Pb[j2] = dot2;
+            }
         }
         cluster.sync();
         // (d) y_j -= tau (v'y_j) v on this CTA's rows
@@ -280,12 +292,24 @@ __global__ void __launch_bounds__(QT, 1) k_house_qr_cl(const QrDesc *__restrict_
         const double *x = Y + (long long)c * ld;
         const int i0 = max(c, row0);
         const double v0 = v0s[c], tauc = taus[c];
-        for (int j = c + warp; j < r; j += nw) {
-            const double *y = Q + (long long)j * ldq;
-            double dot = 0.0;
-            for (int i = i0 + lane; i < row1; i += 32) dot = fma((i == c) ? v0 : x[i], y[i], dot);
-            for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
-            if (lane == 0) Pb[j] = dot;
+        for (int j = c + warp; j < r; j += 2 * nw) {
+            const int j2 = j + nw;
+            const double *y = Q + (long long)j * ldq, *y2 = Q + (long long)(j2 < r ? j2 : j) * ldq;
+            double dot = 0.0, dot2 = 0.0;
+#pragma unroll 4
+            for (int i = i0 + lane; i < row1; i += 32) {
+                const double v = (i == c) ? v0 : x[i];
+                dot = fma(v, y[i], dot);
+                dot2 = fma(v, y2[i], dot2);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                dot += __shfl_down_sync(0xffffffffu, dot, o);
+                dot2 += __shfl_down_sync(0xffffffffu, dot2, o);
+            }
+            if (lane == 0) {
+                Pb[j] = dot;
+                if (j2 < r) Pb[j2] = dot2;
+            }
         }
         cluster.sync();
         for (int j = c + warp; j < r; j += nw) {
