@@ -93,3 +93,15 @@ def test_batch_reports_not_spd_per_problem(ctx):
                                            (dev(bad_locs), dev(np.zeros(900)), bad_th)])
     assert info[0] == 0 and info[1] > 0
     assert np.isfinite(got[0]) and np.isnan(got[1])
+
+
+def test_batch_with_four_variables(ctx):
+    th4 = geo.Theta((1.0, 0.8, 1.2, 0.6), 0.08, (0.4, 0.9, 1.3, 3.6), (0.3, 0.2, 0.1, 0.25, 0.15, 0.35))
+    probs = _problems([60, 90], seed=50)
+    locs4 = inputs.jittered_grid(70, 55)
+    z4 = oracle.simulate(o_theta(th4), locs4, inputs.normals(56, 280))
+    items = [(dev(l), dev(z), th) for l, z, th in probs] + [(dev(locs4), dev(z4), th4)]
+    got, info = geo.geo_loglik_batch(ctx, items)
+    assert np.all(info == 0)
+    for (locs, z, th), g in zip(probs + [(locs4, z4, th4)], got):
+        assert g == pytest.approx(oracle.loglik(o_theta(th), locs, z).loglik, rel=1e-10)

@@ -61,11 +61,13 @@ def o_theta(t: geo.Theta) -> oracle.Theta:
 TH2 = geo.Theta((1.0, 1.0), 0.09, (0.5, 1.0), 0.5)                 # Fig. 5 theta
 TH2G = geo.Theta((1.3, 0.7), 0.05, (0.35, 1.75), -0.4)              # general orders everywhere
 TH3 = geo.Theta((1.0, 1.0, 1.0), 0.05, (0.5, 1.0, 1.5), (0.5, 0.3, 0.4))
+# p = 4 (the largest p): every K_nu table slot in use, and nu_44 = 3.6 above the tabulated range
+TH4 = geo.Theta((1.0, 0.8, 1.2, 0.6), 0.08, (0.4, 0.9, 1.3, 3.6), (0.3, 0.2, 0.1, 0.25, 0.15, 0.35))
 
 
 # ------------------------------------------------------------------ covgen --
 
-@pytest.mark.parametrize("theta", [TH2, TH2G, TH3], ids=["fig5", "general", "trivariate"])
+@pytest.mark.parametrize("theta", [TH2, TH2G, TH3, TH4], ids=["fig5", "general", "trivariate", "p4"])
 def test_covgen_symmetric_matches_oracle(ctx, theta):
     locs = inputs.jittered_grid(150, 3)
     p = len(theta.sigma2)
@@ -138,8 +140,9 @@ def test_loglik_bivariate_n400(ctx, nb):
     assert got == pytest.approx(ref.loglik, rel=1e-10)
 
 
-@pytest.mark.parametrize("n,theta", [(1, TH2), (31, TH2), (37, TH3), (100, TH3), (513, TH2G)],
-                         ids=["n1", "n31", "n37p3", "n100p3", "n513"])
+@pytest.mark.parametrize("n,theta", [(1, TH2), (31, TH2), (37, TH3), (100, TH3), (513, TH2G), (37, TH4),
+                                     (150, TH4)],
+                         ids=["n1", "n31", "n37p3", "n100p3", "n513", "n37p4", "n150p4"])
 def test_loglik_ragged_sizes(ctx, n, theta):
     locs, Z = _problem(n, theta, seed=n)
     ref = oracle.loglik(o_theta(theta), locs, Z)
@@ -284,3 +287,24 @@ def test_mle_steps_match_oracle_nelder_mead(ctx):
     best, ll = geo.geo_mle_best(st)
     assert ll == pytest.approx(-onm.best[1], rel=1e-10)
     assert ll >= -onm.F[-1]   # the simplex improved on its worst vertex
+
+
+def test_predict_and_variance_p4(ctx):
+    n, m = 150, 20
+    allp = inputs.jittered_grid(n + m, 35)
+    locs, new = allp[:n], allp[n:]
+    Zall = oracle.simulate(o_theta(TH4), allp, inputs.normals(36, 4 * (n + m)))
+    Z = Zall[: 4 * n]
+    ref = oracle.predict(o_theta(TH4), locs, Z, new)
+    ref_var = oracle.predict_var(o_theta(TH4), locs, new)
+    _, fac = geo.geo_loglik(ctx, dev(locs), dev(Z), TH4, geo.opts(nb=128), keep=True)
+    try:
+        zhat = torch.zeros(4 * m, dtype=torch.float64, device="cuda")
+        var = torch.zeros(4 * m, dtype=torch.float64, device="cuda")
+        geo.geo_predict(ctx, fac, dev(new), zhat)
+        geo.geo_predict_var(ctx, fac, dev(new), var)
+        got, got_var = zhat.cpu().numpy(), var.cpu().numpy()
+    finally:
+        fac.free()
+    assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref)
+    assert np.all(np.abs(got_var - ref_var) <= 1e-10 + 1e-8 * np.abs(ref_var))
