@@ -264,6 +264,27 @@ def predict_var(theta: Theta, locs, new_locs, L=None) -> np.ndarray:
     return out
 
 
+def dst_loglik(theta: Theta, locs, Z, nb: int, dst: int) -> float:
+    """Eq. 1 for the Diagonal Super Tile approximation (Sec. 3.4): Sigma in
+    Morton order (Sec. 5.3), cut into nb x nb tiles; the tiles with
+    |I - J| >= dst are set to zero and the rest kept exactly."""
+    locs = _f64(locs).reshape(-1, 2)
+    p = theta.p
+    perm = morton_order(locs)
+    ls = locs[perm]
+    zs = _f64(Z).reshape(-1, p)[perm].ravel()
+    S = covgen(theta, ls)
+    N = S.shape[0]
+    idx = np.arange(N) // nb
+    S[np.abs(idx[:, None] - idx[None, :]) >= dst] = 0.0
+    L, info = cholesky(S)
+    if info:
+        raise ValueError("the DST matrix is not positive definite (info=%d)" % info)
+    y = forward(L, zs)
+    logdet = 2.0 * float(np.sum(np.log(np.diag(L))))
+    return -0.5 * N * math.log(2.0 * math.pi) - 0.5 * logdet - 0.5 * float(y @ y)
+
+
 def simulate(theta: Theta, locs, e) -> np.ndarray:
     """Z = L e with L L' = Sigma(theta): a draw from N(0, Sigma) given standard normals e."""
     L, info = cholesky(covgen(theta, locs))

@@ -480,3 +480,40 @@ def test_predict_var_matches_library_solve():
     c0 = oracle.covgen(th, locs, new)                     # (2 * 70) x (2 * 8)
     ref = np.diag(oracle.covgen(th, new)) - np.einsum("ij,ij->j", c0, np.linalg.solve(S, c0))
     assert oracle.predict_var(th, locs, new) == pytest.approx(ref, rel=1e-9, abs=1e-12)
+
+
+# ---- Diagonal Super Tile (Sec. 3.4) -----------------------------------------
+
+def _dst_problem():
+    th = oracle.Theta([1.0, 1.5], 0.04, [0.5, 1.0], np.array([[1.0, 0.4], [0.4, 1.0]]))
+    locs = inputs.jittered_grid(120, 21)
+    Z = oracle.simulate(th, locs, inputs.normals(22, 240))
+    return th, locs, Z
+
+
+def test_dst_with_every_tile_kept_is_the_exact_likelihood():
+    th, locs, Z = _dst_problem()
+    full = oracle.loglik(th, locs, Z).loglik
+    assert oracle.dst_loglik(th, locs, Z, 48, 5) == pytest.approx(full, rel=1e-12)   # 240 / 48 = 5 tiles
+
+
+def test_dst_one_tile_diagonal_is_a_sum_of_block_likelihoods():
+    th, locs, Z = _dst_problem()
+    perm = oracle.morton_order(locs)
+    ls, zs = locs[perm], Z.reshape(-1, 2)[perm]
+    # nb = 48 rows = 24 locations per tile: independent blocks of consecutive Morton locations
+    ref = sum(oracle.loglik(th, ls[b:b + 24], zs[b:b + 24].ravel()).loglik for b in range(0, 120, 24))
+    assert oracle.dst_loglik(th, locs, Z, 48, 1) == pytest.approx(ref, rel=1e-12)
+
+
+def test_dst_matches_a_direct_numpy_evaluation():
+    th, locs, Z = _dst_problem()
+    perm = oracle.morton_order(locs)
+    S = oracle.covgen(th, locs[perm])
+    idx = np.arange(240) // 40
+    S[np.abs(idx[:, None] - idx[None, :]) >= 3] = 0.0
+    zs = Z.reshape(-1, 2)[perm].ravel()
+    sign, logdet = np.linalg.slogdet(S)
+    ref = -0.5 * 240 * np.log(2 * np.pi) - 0.5 * logdet - 0.5 * zs @ np.linalg.solve(S, zs)
+    assert sign > 0
+    assert oracle.dst_loglik(th, locs, Z, 40, 3) == pytest.approx(ref, rel=1e-10)
