@@ -82,7 +82,10 @@ typedef struct {
     int tlr_kmax;       /* TLR: maximum tile rank (default 200) */
     int morton;         /* 1 = reorder locations by Morton (Z-order) key internally (default 1) */
     int fp64_gemm;      /* FP64 trailing updates: 0 = native FP64 FMA (default) */
-    int reserved[7];
+    int dst;            /* TLR form: > 0 = Diagonal Super Tile (Sec. 3.4), keep the dst tile diagonals
+                           nearest the diagonal (1 = diagonal tiles only) dense and zero the other
+                           tiles (of the Morton-ordered matrix); 0 = off (default) */
+    int reserved[6];
 } geo_opts;
 
 typedef struct geo_ctx geo_ctx;

@@ -40,7 +40,8 @@ class geo_theta(ctypes.Structure):
 class geo_opts(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int), ("prec", ctypes.c_int), ("band", ctypes.c_int), ("lowp", ctypes.c_int),
                 ("refine_iters", ctypes.c_int), ("tlr_tol", ctypes.c_double), ("tlr_kmax", ctypes.c_int),
-                ("morton", ctypes.c_int), ("fp64_gemm", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("morton", ctypes.c_int), ("fp64_gemm", ctypes.c_int), ("dst", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 class geo_factor_stats(ctypes.Structure):

@@ -574,6 +574,7 @@ static int loglik_tlr(geo_ctx *ctx, const double *locs_dev, int n, const double 
     const int N = f->N, p = f->p, nb = o.nb;
     if (nb % p != 0) return bail(fail(ctx, GEO_EINVAL, "TLR needs nb to be a multiple of p"));
     if (!(o.tlr_tol > 0.0) || o.tlr_kmax < 1) return bail(fail(ctx, GEO_EINVAL, "TLR needs tol > 0 and kmax >= 1"));
+    if (o.dst < 0) return bail(fail(ctx, GEO_EINVAL, "dst must be >= 0"));
     TlrFactor *F = new TlrFactor();
     f->tlr = F;
     F->N = N;
@@ -581,6 +582,7 @@ static int loglik_tlr(geo_ctx *ctx, const double *locs_dev, int n, const double 
     F->T = (N + nb - 1) / nb;
     F->kmax = std::min(o.tlr_kmax, nb);
     F->tol = o.tlr_tol;
+    F->dst = o.dst;
     const size_t fbytes = tlr_factor_bytes(N, nb, F->kmax);
     void *pf;
     if ((rc = dev_alloc(ctx, &pf, fbytes))) return bail(rc);

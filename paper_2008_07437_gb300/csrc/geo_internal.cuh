@@ -200,6 +200,7 @@ constexpr int TLR_KCHUNK = 2048;            // stacked rank per update chunk
 constexpr int TLR_MAXK_PER_CHUNK = 16;      // column tiles per update chunk
 constexpr size_t TLR_ARENA_BYTES = 16u << 20;
 struct TlrFactor {
+    int dst = 0;               // > 0: keep only the dst tile diagonals nearest the diagonal, dense
     int N = 0, nb = 0, T = 0, kmax = 0;
     double tol = 0.0;
     double *D = nullptr;                    // T diagonal tiles nb x nb (ld nb), lower = L_tt

@@ -390,7 +390,12 @@ cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, cons
         std::vector<int> all_rows{j}, dense_rows{j}, lr_rows;
         for (int q = 0; q < nt; ++q) {
             all_rows.push_back(j + 1 + q);
-            (dense_now[q] ? dense_rows : lr_rows).push_back(j + 1 + q);
+            if (F.dst > 0) {
+                // Diagonal Super Tile: the tiles within the band are formed densely, the others dropped
+                if (q + 1 < F.dst) dense_rows.push_back(j + 1 + q);
+            } else {
+                (dense_now[q] ? dense_rows : lr_rows).push_back(j + 1 + q);
+            }
         }
         if (!lr_rows.empty()) {
             std::vector<GemmDesc> dy0;
@@ -426,7 +431,9 @@ cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, cons
         // 4. compress the tiles below: first with a narrow sketch, then the widest one where needed
         std::vector<int> todo;
         for (int q = 0; q < nt; ++q) {
-            if (dense_now[q])
+            if (F.dst > 0)
+                rk[q] = (q + 1 < F.dst) ? -1 : 0;   // dense within the band, rank 0 beyond
+            else if (dense_now[q])
                 rk[q] = -1;
             else
                 todo.push_back(q);
@@ -542,7 +549,7 @@ cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, cons
         {
             std::vector<int> late;
             for (int q = 0; q < nt; ++q)
-                if (rk[q] < 0 && !dense_now[q]) late.push_back(j + 1 + q);
+                if (rk[q] < 0 && !dense_now[q] && F.dst == 0) late.push_back(j + 1 + q);
             if (!late.empty())
                 TCK(chunk_loop(late, [&](int Kc, const std::vector<char> &has) -> cudaError_t {
                     return dense_update(late, Kc, has);

@@ -145,3 +145,20 @@ def test_tlr_rejects_tile_not_multiple_of_p(ctx):
     with pytest.raises(geo.GeoError) as ei:
         geo.geo_loglik(ctx, dev(locs), dev(Z), TH3, tlr_opts(100, 1e-9))
     assert ei.value.code == geo.GEO_EINVAL
+
+
+# ---- Diagonal Super Tile (Sec. 3.4): the tiles beyond a band dropped, the band exact ----
+
+@pytest.mark.parametrize("dst", [1, 2, 3, 5])
+def test_dst_matches_oracle(ctx, dst):
+    th = geo.Theta((1.0, 1.5), 0.03, (0.5, 1.0), 0.4)
+    locs, Z = _problem(600, th, seed=61)            # N = 1,200: 5 tiles of 240
+    ref = oracle.dst_loglik(o_theta(th), locs, Z, 240, dst)
+    got, fac = geo.geo_loglik(ctx, dev(locs), dev(Z), th, geo.opts(prec=2, nb=240, dst=dst), keep=True)
+    st = geo.geo_factor_stats_get(fac)
+    fac.free()
+    assert got == pytest.approx(ref, rel=1e-10)
+    assert st.tlr_dense_tiles == sum(5 - d for d in range(1, min(dst, 5)))   # the kept off-diagonal tiles
+    if dst >= 5:
+        dense, _ = geo.geo_loglik(ctx, dev(locs), dev(Z), th, geo.opts(nb=240))
+        assert got == pytest.approx(dense, rel=1e-12)
