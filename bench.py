@@ -55,6 +55,35 @@ def measured_peaks():
         return {}
 
 
+# --------------------------------------------------------------------------
+# replicas under torchrun: one process per GPU, no collective on the data path
+# --------------------------------------------------------------------------
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over the ranks (the timed region is the slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def gather_over_ranks(obj) -> list:
+    """Every rank's obj, in rank order."""
+    import torch.distributed as dist
+    if not dist.is_initialized() or dist.get_world_size() == 1:
+        return [obj]
+    out = [None] * dist.get_world_size()
+    dist.all_gather_object(out, obj)
+    return out
+
+
+def replica_value(units_per_rank: float, seconds: float, world: int) -> float:
+    """Whole-job throughput: the units all ranks processed / the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 # Roofline of each kernel class: (bound, peak, unit, what the peak is).
 def class_roofline(cls):
     mp = measured_peaks()
@@ -363,10 +392,8 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     prof = geo.geo_profile_read(ctx)
     geo.geo_profile_enable(ctx, False)
+    ms = max_over_ranks(ms, dev)
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     zhat = d_zhat.cpu().numpy()
     mspe = float(np.mean(np.sum((zhat - z_true_pred).reshape(-1, p) ** 2, axis=1))) if w.n_pred else None
@@ -395,12 +422,8 @@ def run_ours(args):
                 h_zhat.copy_(d_zhat, non_blocking=True)
             fac.free()
             torch.cuda.synchronize()
-        t_e2e = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([t_e2e], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": world * args.steps / t_e2e, "unit": UNIT,
+        t_e2e = max_over_ranks(time.perf_counter() - t0, dev)
+        e2e = {"value": replica_value(args.steps, t_e2e, world), "unit": UNIT,
                "h2d_bytes_per_step": 8 * (2 * w.n + N + 2 * w.n_pred),
                "d2h_bytes_per_step": 8 * (p * w.n_pred + 1)}
 
@@ -417,7 +440,7 @@ def run_ours(args):
     # (N = 8,000) measured 0.822 x the algorithmic bytes; scaled to this run's
     # average launch (FP64 update kernel only)
     traffic = 0.822 * dk["bytes"] / max(dk["launches"], 1) if dom == "gemm" and not tlr else None
-    out = {"metric": METRIC, "value": world * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+    out = {"metric": METRIC, "value": replica_value(args.steps, ms * 1e-3, world), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": config_json(w, args),
@@ -618,15 +641,11 @@ def run_serving(args):
     escalated = sum(1 for r, x in rows if r.kind == "loglik" and x["prec"] == 0 and args.serving_prec != "fp64")
     failed = sum(1 for _, x in rows if x["status"] != 0)
     lat_k = {k: [x["t_end"] - x["t_submit"] for r, x in rows if r.kind == k] for k in ("loglik", "predict")}
-    if world > 1:
-        allv = [None] * world
-        dist.all_gather_object(allv, {"lat": lat, "span": span, "n": len(rows), "n_ll": n_ll, "launches": launches})
-        lat = [v for a in allv for v in a["lat"]]
-        span = max(a["span"] for a in allv)
-        total, n_ll = sum(a["n"] for a in allv), sum(a["n_ll"] for a in allv)
-        launches = sum(a["launches"] for a in allv)
-    else:
-        total = len(rows)
+    allv = gather_over_ranks({"lat": lat, "span": span, "n": len(rows), "n_ll": n_ll, "launches": launches})
+    lat = [v for a in allv for v in a["lat"]]
+    span = max(a["span"] for a in allv)
+    total, n_ll = sum(a["n"] for a in allv), sum(a["n_ll"] for a in allv)
+    launches = sum(a["launches"] for a in allv)
 
     # accuracy of the served reduced form: |dl| / |l| against FP64 on Z drawn
     # from the model, at the theta and locations of the smallest served likelihoods
@@ -771,10 +790,7 @@ def run_batch(args):
     ms = ev0.elapsed_time(ev1)
     prof = geo.geo_profile_read(ctx)
     geo.geo_profile_enable(ctx, False)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     # the same problems one geo_loglik call at a time (context, not the metric)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -795,15 +811,15 @@ def run_batch(args):
                 dl.copy_(hl, non_blocking=True)
                 dz.copy_(hz, non_blocking=True)
             geo.geo_loglik_batch(ctx, items)   # returns host results (synchronises)
-        t_e2e = time.perf_counter() - t0
-        e2e = {"value": world * args.steps * len(items) / t_e2e, "unit": UNIT,
+        t_e2e = max_over_ranks(time.perf_counter() - t0, dev)
+        e2e = {"value": replica_value(args.steps * len(items), t_e2e, world), "unit": UNIT,
                "h2d_bytes_per_step": sum(8 * 4 * n for n, _, _, _ in probs),
                "d2h_bytes_per_step": 8 * len(items)}
     launches = sum(v["launches"] for v in prof.values())
     dom = max(("gemm", "covgen", "potrf", "trsm"), key=lambda k: prof[k]["ms"])
     bound, peak, peak_src = class_roofline("gemm")
     tflops = (Ntot3 * args.steps) / (ms * 1e-3) / 1e12
-    out = {"metric": METRIC, "value": world * args.steps * len(items) / (ms * 1e-3), "unit": UNIT,
+    out = {"metric": METRIC, "value": replica_value(args.steps * len(items), ms * 1e-3, world), "unit": UNIT,
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",

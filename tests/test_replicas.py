@@ -1,0 +1,65 @@
+"""The multi-GPU path of bench.py is replicas only (independent evaluations,
+no collective on the data path): the timed region is the slowest rank's and
+the value counts the units of all ranks.  Exercised here with two gloo ranks
+on the CPU."""
+import multiprocessing as mp
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank: int, world: int, port: int, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        seconds = bench.max_over_ranks(2.0 + rank, torch.device("cpu"))          # rank 1 is the slowest
+        gathered = bench.gather_over_ranks({"rank": rank, "lat": [0.1 * (rank + 1)] * (rank + 2)})
+        value = bench.replica_value(3, seconds, world)
+        q.put((rank, seconds, gathered, value))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_aggregate_like_the_bench():
+    pytest.importorskip("torch")
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, seconds, gathered, value in out:
+        assert seconds == 3.0                                     # max over the ranks
+        assert [g["rank"] for g in gathered] == [0, 1]            # rank order
+        assert sum(len(g["lat"]) for g in gathered) == 5
+        assert value == pytest.approx(2 * 3 / 3.0)                # units of both ranks / slowest time
+
+
+def test_single_process_is_the_identity():
+    pytest.importorskip("torch")
+    sys.path.insert(0, ROOT)
+    import torch
+
+    import bench
+    assert bench.max_over_ranks(1.5, torch.device("cpu")) == 1.5
+    assert bench.gather_over_ranks({"a": 1}) == [{"a": 1}]
+    assert bench.replica_value(4, 2.0, 1) == 2.0
