@@ -53,11 +53,10 @@ __global__ void __launch_bounds__(256) k_b_covgen(BatchDesc *d) {
     const CovParams &cp = q.cp;
     const double x = (l == r) ? 0.0 : sqrt(dx * dx + dy * dy) * cp.inv_a;
     const int p = cp.p;
+    double v[GEO_PMAX_DEV * GEO_PMAX_DEV];
+    matern_block(x, cp, v);
     for (int i = 0; i < p; ++i)
-        for (int j = 0; j < p; ++j) {
-            const double v = matern_cov(x, cp.m[(i <= j) ? i * p + j : j * p + i], cp.tab);
-            q.A[(long long)(p * r + j) * q.ld + p * l + i] = v;
-        }
+        for (int j = 0; j < p; ++j) q.A[(long long)(p * r + j) * q.ld + p * l + i] = v[i * GEO_PMAX_DEV + j];
 }
 
 __global__ void k_b_gather(BatchDesc *d) {

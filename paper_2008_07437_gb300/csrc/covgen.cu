@@ -14,15 +14,7 @@ constexpr int TR = 4;    // locations r (columns) per CTA
 
 // The p x p block of C at distance h for one location pair.
 __device__ __forceinline__ void cov_block(const CovParams &cp, double h, double *v) {
-    const double x = h * cp.inv_a;
-    const int p = cp.p;
-    for (int i = 0; i < p; ++i) {
-        for (int j = i; j < p; ++j) {
-            const double c = matern_cov(x, cp.m[i * p + j], cp.tab);
-            v[i * GEO_PMAX_DEV + j] = c;
-            v[j * GEO_PMAX_DEV + i] = c;
-        }
-    }
+    matern_block(h * cp.inv_a, cp, v);
 }
 
 // K_nu tables of one theta (cheb_build_block, matern.cuh): block (q, k).

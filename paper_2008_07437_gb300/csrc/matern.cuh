@@ -35,16 +35,16 @@
 // Those two methods are the reference evaluator.  The covariance kernels use
 // a per-theta table built from it on the device (k_cheb_build): for each
 // order nu_ij <= 3 that is not a half-integer,
-//   H(x) = e^x sqrt(x) K_nu(x)
+//   F(x) = e^x x^nu K_nu(x)
 // is interpolated on every dyadic interval [2^k, 2^(k+1)), k = -2 .. 9, by the
 // Chebyshev polynomial of degree 23 through the 24 Chebyshev nodes of the
-// interval.  H is analytic except at x = 0, which lies three half-widths from
+// interval.  F is analytic except at x = 0, which lies three half-widths from
 // the centre of every such interval, so the interpolation error falls like
-// (3 + sqrt 8)^-24: below 1e-16 relative up to nu = 3 (checked against
-// arbitrary-precision K_nu).  Then
-//   x^nu K_nu(x) = exp((nu - 1/2) ln x - x) H(x),
-// one Clenshaw sum, one logarithm and one exponential, instead of a
-// recurrence of up to ~90 terms with two divisions each.  Below x = 1/4
+// (3 + sqrt 8)^-24: below 1e-19 relative up to nu = 3 (checked against
+// arbitrary-precision K_nu).  Then x^nu K_nu(x) = e^-x F(x): one Clenshaw sum
+// per order, and one exponential per location pair shared by all the orders
+// (and the half-integer closed forms), instead of a recurrence of up to ~90
+// terms with two divisions each.  Below x = 1/4
 // Temme's series is used with the reciprocals 1/(k^2 - mu^2), 1/(k -+ mu), 1/k
 // taken from the table (no divisions in the loop); at x >= 1024 the
 // covariance underflows to 0.
@@ -168,17 +168,18 @@ GEO_DEV double xnu_besselk(double x, const MaternConst &c) {
     return exp(c.nu * log(x)) * kv;
 }
 
-// H(x) = e^x sqrt(x) K_nu(x), reference methods (table construction).
-GEO_DEV double besselk_h_ref(double x, const MaternConst &c) {
+// F(x) = e^x x^nu K_nu(x), reference methods (table construction).
+GEO_DEV double besselk_f_ref(double x, const MaternConst &c) {
     bool scaled;
     const double kv = besselk_ref(x, c, &scaled);
-    return scaled ? sqrt(x) * kv : exp(x) * sqrt(x) * kv;
+    const double xnu = exp(c.nu * log(x));
+    return scaled ? xnu * kv : exp(x) * xnu * kv;
 }
 
 // One block of 32 threads of the table construction for order q = i p + j
 // (i <= j) and interval k (k = GEO_CHEB_NI: the reciprocals), from the
-// reference evaluator.  Node values H(x_t) at x_t = mid + half cos(pi (t + 1/2) / n),
-// coefficients c_m = (2 - [m = 0]) / n sum_t H(x_t) cos(pi m (t + 1/2) / n),
+// reference evaluator.  Node values F(x_t) at x_t = mid + half cos(pi (t + 1/2) / n),
+// coefficients c_m = (2 - [m = 0]) / n sum_t F(x_t) cos(pi m (t + 1/2) / n),
 // each summed in a fixed order.  hv: GEO_CHEB_N doubles of shared memory.
 __device__ __forceinline__ void cheb_build_block(const CovParams &cp, double *tab, int q, int k, double *hv) {
     const int p = cp.p;
@@ -201,7 +202,7 @@ __device__ __forceinline__ void cheb_build_block(const CovParams &cp, double *ta
     const double lo = ldexp(1.0, GEO_CHEB_K0 + k);
     if (t < GEO_CHEB_N) {
         const double xt = 1.5 * lo + 0.5 * lo * cospi((t + 0.5) / GEO_CHEB_N);
-        hv[t] = besselk_h_ref(xt, c);
+        hv[t] = besselk_f_ref(xt, c);
     }
     __syncthreads();
     if (t < GEO_CHEB_N) {
@@ -259,8 +260,8 @@ GEO_DEV double xnu_besselk_small(double x, const MaternConst &c, const double *r
     return exp(c.nu * (0.6931471805599453 - lx)) * kv;   // ln x = ln 2 - ln(2/x)
 }
 
-// x^nu K_nu(x) for 1/4 <= x < 1024 from the Chebyshev table of the order.
-GEO_DEV double xnu_besselk_table(double x, const MaternConst &c, const double *tab) {
+// F(x) = e^x x^nu K_nu(x) for 1/4 <= x < 1024 from the Chebyshev table of the order.
+GEO_DEV double cheb_f(double x, const double *tab) {
     const int e = ilogb(x);                              // x in [2^e, 2^(e+1))
     const double *cf = tab + (e - GEO_CHEB_K0) * GEO_CHEB_N;
     const double t = ldexp(x, 1 - e) - 3.0;              // exact map to [-1, 1)
@@ -272,8 +273,7 @@ GEO_DEV double xnu_besselk_table(double x, const MaternConst &c, const double *t
         b2 = b1;
         b1 = b0;
     }
-    const double h = fma(t, b1, cf[0]) - b2;
-    return exp((c.nu - 0.5) * log(x) - x) * h;
+    return fma(t, b1, cf[0]) - b2;
 }
 
 // C_ij(h) of Eq. 2 given x = h / a (x >= 0), reference methods only.
@@ -287,18 +287,36 @@ GEO_DEV double matern_cov_ref(double x, const MaternConst &c) {
     }
 }
 
-// C_ij(h) of Eq. 2 given x = h / a (x >= 0); tab: the theta's tables.
-GEO_DEV double matern_cov(double x, const MaternConst &c, const double *tab) {
-    if (x == 0.0) return c.c0;
+// C_ij(h) of Eq. 2 given x = h / a > 0 and emx = e^-x; tab: the theta's tables.
+GEO_DEV double matern_cov_e(double x, double emx, const MaternConst &c, const double *tab) {
     switch (c.kind) {
-        case 1: return c.c0 * exp(-x);
-        case 2: return c.c0 * (1.0 + x) * exp(-x);
-        case 3: return c.c0 * (1.0 + x + x * x * (1.0 / 3.0)) * exp(-x);
+        case 1: return c.c0 * emx;
+        case 2: return c.c0 * (1.0 + x) * emx;
+        case 3: return c.c0 * (1.0 + x + x * x * (1.0 / 3.0)) * emx;
         default:
             if (c.toff < 0 || !tab) return c.pre * xnu_besselk(x, c);
             if (x >= 1024.0) return 0.0;
-            if (x < 0.25)
-                return c.pre * xnu_besselk_small(x, c, tab + c.toff + GEO_CHEB_NI * GEO_CHEB_N);
-            return c.pre * xnu_besselk_table(x, c, tab + c.toff);
+            if (x < 0.25) return c.pre * xnu_besselk_small(x, c, tab + c.toff + GEO_CHEB_NI * GEO_CHEB_N);
+            return c.pre * emx * cheb_f(x, tab + c.toff);
     }
+}
+
+// C_ij(h) of Eq. 2 given x = h / a (x >= 0); tab: the theta's tables.
+GEO_DEV double matern_cov(double x, const MaternConst &c, const double *tab) {
+    if (x == 0.0) return c.c0;
+    return matern_cov_e(x, exp(-x), c, tab);
+}
+
+// The p x p block of C at x = h / a: v[i * GEO_PMAX_DEV + j], each distinct
+// (i, j) evaluated once, one exponential shared by all of them.
+GEO_DEV void matern_block(double x, const CovParams &cp, double *v) {
+    const int p = cp.p;
+    const double emx = exp(-x);
+    for (int i = 0; i < p; ++i)
+        for (int j = i; j < p; ++j) {
+            const MaternConst &c = cp.m[i * p + j];
+            const double val = (x == 0.0) ? c.c0 : matern_cov_e(x, emx, c, cp.tab);
+            v[i * GEO_PMAX_DEV + j] = val;
+            v[j * GEO_PMAX_DEV + i] = val;
+        }
 }

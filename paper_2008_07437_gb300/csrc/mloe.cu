@@ -21,11 +21,10 @@ __global__ void __launch_bounds__(256) k_covgen_cross(const CovParams cp, const 
     const double dx = s0[2 * q] - lx[r], dy = s0[2 * q + 1] - ly[r];
     const double x = sqrt(dx * dx + dy * dy) * cp.inv_a;
     const int p = cp.p;
+    double v[GEO_PMAX_DEV * GEO_PMAX_DEV];
+    matern_block(x, cp, v);
     for (int i = 0; i < p; ++i)
-        for (int j = 0; j < p; ++j) {
-            const double v = matern_cov(x, cp.m[(i <= j) ? i * p + j : j * p + i], cp.tab);
-            out[(long long)(p * r + j) * ld + (long long)p * q + i] = v;
-        }
+        for (int j = 0; j < p; ++j) out[(long long)(p * r + j) * ld + (long long)p * q + i] = v[i * GEO_PMAX_DEV + j];
 }
 
 // For rows q < R of X (column-major, ldx, N columns): s[q] = sum_c X[q, c]^2

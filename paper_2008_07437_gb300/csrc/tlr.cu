@@ -39,11 +39,10 @@ __global__ void __launch_bounds__(256) k_covgen_block(const CovParams cp, const 
     const double dx = lx[l] - lx[r], dy = ly[l] - ly[r];
     const double x = (l == r) ? 0.0 : sqrt(dx * dx + dy * dy) * cp.inv_a;
     const int p = cp.p;
+    double v[GEO_PMAX_DEV * GEO_PMAX_DEV];
+    matern_block(x, cp, v);
     for (int i = 0; i < p; ++i)
-        for (int j = 0; j < p; ++j) {
-            const double v = matern_cov(x, cp.m[(i <= j) ? i * p + j : j * p + i], cp.tab);
-            out[(long long)(p * (r - r0) + j) * ld + p * (l - l0) + i] = v;
-        }
+        for (int j = 0; j < p; ++j) out[(long long)(p * (r - r0) + j) * ld + p * (l - l0) + i] = v[i * GEO_PMAX_DEV + j];
 }
 
 // M (r x r) = transpose of the upper triangle of B (r x r leading block, ld ldb).
