@@ -21,6 +21,9 @@ Contents and the passage each part follows:
   at an absolute accuracy threshold (Sec. 5.3, Fig. 5).
 * ``mloe_mmom``: the multivariate MLOE/MMOM criteria, Eq. 5 - Eq. 8 and
   Algorithm 1 (Sec. 5.4).
+* ``sigma2_hat`` / ``profile_loglik`` / ``profile_objective``: the profile
+  likelihood of Sec. 4.2 (marginal variances from each variable's own
+  correlation matrix, plugged into Eq. 1).
 
 Pins that tie this oracle to the paper and to mathematics (not to itself) live
 in ``tests/test_oracle_pins.py``.
@@ -471,6 +474,65 @@ def mle_objective(locs, Z, p: int):
         if r.info:
             return math.inf
         return -r.loglik
+    return f
+
+
+# ----------------------------------------------------------------------------
+# Profile likelihood (Sec. 4.2): the marginal variances leave the optimisation
+# ----------------------------------------------------------------------------
+
+def sigma2_hat(theta: Theta, locs, Z) -> np.ndarray:
+    """Sec. 4.2: sigma^2_ii = n^-1 Z_i' R_ii^-1 Z_i for i = 1..p, where Z_i holds
+    the n values of variable i (every p-th entry of Representation I, from i)
+    and R_ii is the correlation matrix of variable i alone: the Matern of
+    Eq. 2 with i = j, sigma^2_ii = 1, smoothness nu_ii and range a.  sigma^2 and
+    beta of ``theta`` are not used."""
+    locs = _f64(locs).reshape(-1, 2)
+    Z = _f64(Z)
+    p, n = theta.p, locs.shape[0]
+    out = np.empty(p)
+    for i in range(p):
+        Rii = covgen(Theta([1.0], theta.a, [theta.nu[i]], np.eye(1)), locs)
+        L, info = cholesky(Rii)
+        if info:
+            raise np.linalg.LinAlgError(f"R_{i + 1}{i + 1} is not positive definite (column {info})")
+        y = forward(L, Z[i::p])
+        out[i] = float(y @ y) / n
+    return out
+
+
+def profile_loglik(theta: Theta, locs, Z) -> tuple[float, np.ndarray]:
+    """Profile log-likelihood (Sec. 4.2): Eq. 1 at theta with its marginal
+    variances replaced by sigma2_hat(theta).  Returns (l, sigma2_hat)."""
+    s2 = sigma2_hat(theta, locs, Z)
+    r = loglik(Theta(s2, theta.a, theta.nu, theta.beta), locs, Z)
+    return r.loglik, s2
+
+
+def profile_theta_to_x(theta: Theta) -> np.ndarray:
+    """Profile coordinates: (log a, log nu_i, beta_ij for i<j), the sigma^2 dropped."""
+    return theta_to_x(theta)[theta.p:].copy()
+
+
+def profile_x_to_theta(x, p: int) -> Theta:
+    """Inverse of profile_theta_to_x with sigma^2 = 1 (replaced by sigma2_hat when evaluated)."""
+    return x_to_theta(np.concatenate([np.zeros(p), np.asarray(x, dtype=np.float64)]), p)
+
+
+def profile_objective(locs, Z, p: int):
+    """f(x) = -l_profile(theta(x)) over the profile coordinates, +inf outside the
+    feasible set (beta not PD, a Cholesky failure)."""
+    def f(x):
+        th = profile_x_to_theta(x, p)
+        if not beta_is_pd(th.beta):
+            return math.inf
+        try:
+            ll, _ = profile_loglik(th, locs, Z)
+        except np.linalg.LinAlgError:
+            return math.inf
+        if not math.isfinite(ll):
+            return math.inf
+        return -ll
     return f
 
 

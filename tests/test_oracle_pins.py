@@ -517,3 +517,77 @@ def test_dst_matches_a_direct_numpy_evaluation():
     ref = -0.5 * 240 * np.log(2 * np.pi) - 0.5 * logdet - 0.5 * zs @ np.linalg.solve(S, zs)
     assert sign > 0
     assert oracle.dst_loglik(th, locs, Z, 40, 3) == pytest.approx(ref, rel=1e-10)
+
+
+# ------------------------------------------------ profile likelihood -------
+
+def _profile_problem(p, beta, nu, seed):
+    th = oracle.Theta([1.3, 0.7, 2.0][:p], 0.08, nu, beta)
+    locs = inputs.jittered_grid(90, seed)
+    Z = oracle.simulate(th, locs, inputs.normals(seed + 1, p * 90))
+    return th, locs, Z
+
+
+def test_profile_p1_is_the_maximum_over_sigma2():
+    # p = 1: sigma2_hat is the exact maximiser of Eq. 1 over sigma^2 (Sec. 4.2),
+    # found here by a bounded scalar search on the full likelihood
+    optimize = pytest.importorskip("scipy.optimize")
+    th, locs, Z = _profile_problem(1, np.eye(1), [0.8], 61)
+    f = lambda ls: -oracle.loglik(oracle.Theta([math.exp(ls)], th.a, th.nu, th.beta), locs, Z).loglik
+    r = optimize.minimize_scalar(f, bounds=(-5, 5), method="bounded", options={"xatol": 1e-10})
+    ll, s2 = oracle.profile_loglik(th, locs, Z)
+    assert s2[0] == pytest.approx(math.exp(r.x), rel=1e-7)
+    assert ll == pytest.approx(-r.fun, rel=1e-12)
+
+
+def test_profile_beta_zero_maximises_each_variance():
+    # beta = 0: Sigma is block diagonal by variable, Eq. 1 splits into p
+    # univariate likelihoods and the joint maximiser over sigma^2 is sigma2_hat
+    optimize = pytest.importorskip("scipy.optimize")
+    th, locs, Z = _profile_problem(2, np.eye(2), [0.5, 1.3], 63)
+
+    def f(ls):
+        return -oracle.loglik(oracle.Theta(np.exp(ls), th.a, th.nu, th.beta), locs, Z).loglik
+
+    r = optimize.minimize(f, np.zeros(2), method="Nelder-Mead",
+                          options={"xatol": 1e-10, "fatol": 1e-13, "maxiter": 4000})
+    ll, s2 = oracle.profile_loglik(th, locs, Z)
+    np.testing.assert_allclose(s2, np.exp(r.x), rtol=1e-6)
+    assert ll == pytest.approx(-r.fun, rel=1e-11)
+
+
+def test_sigma2_hat_closed_form_correlations():
+    # nu = 1/2 and 3/2 have closed-form Matern correlations, exp(-t) and (1 + t) exp(-t),
+    # t = h / a; sigma2_hat by a dense numpy solve with them (beta does not enter)
+    th, locs, Z = _profile_problem(2, np.array([[1.0, 0.6], [0.6, 1.0]]), [0.5, 1.5], 65)
+    t = np.linalg.norm(locs[:, None, :] - locs[None, :, :], axis=2) / th.a
+    R = [np.exp(-t), (1 + t) * np.exp(-t)]
+    ref = [Z[i::2] @ np.linalg.solve(R[i], Z[i::2]) / 90 for i in range(2)]
+    np.testing.assert_allclose(oracle.sigma2_hat(th, locs, Z), ref, rtol=1e-12)
+
+
+def test_profile_scale_equivariance_and_joint_bound():
+    # Z -> c Z: sigma2_hat -> c^2 sigma2_hat and l_profile -> l_profile - N log c;
+    # the plug-in value never exceeds the joint maximum of Eq. 1 over sigma^2
+    optimize = pytest.importorskip("scipy.optimize")
+    th, locs, Z = _profile_problem(3, np.array([[1.0, 0.5, 0.2], [0.5, 1.0, 0.3], [0.2, 0.3, 1.0]]),
+                                   [0.5, 1.0, 1.5], 67)
+    ll, s2 = oracle.profile_loglik(th, locs, Z)
+    c = 3.0
+    ll_c, s2_c = oracle.profile_loglik(th, locs, c * Z)
+    np.testing.assert_allclose(s2_c, c * c * s2, rtol=1e-12)
+    assert ll_c == pytest.approx(ll - 270 * math.log(c), rel=1e-12)
+    f = lambda ls: -oracle.loglik(oracle.Theta(np.exp(ls), th.a, th.nu, th.beta), locs, Z).loglik
+    r = optimize.minimize(f, np.log(s2), method="Nelder-Mead", options={"xatol": 1e-9, "fatol": 1e-12})
+    assert ll <= -r.fun + 1e-9
+
+
+def test_profile_coordinates_roundtrip():
+    th = oracle.Theta([2.0, 3.0], 0.07, [0.4, 1.7], 0.35)
+    x = oracle.profile_theta_to_x(th)
+    assert x.shape == (4,)
+    back = oracle.profile_x_to_theta(x, 2)
+    assert back.a == pytest.approx(0.07, rel=1e-15)
+    np.testing.assert_allclose(back.nu, [0.4, 1.7], rtol=1e-15)
+    assert back.beta[0, 1] == 0.35 and back.beta[1, 0] == 0.35
+    np.testing.assert_array_equal(back.sigma2, [1.0, 1.0])
