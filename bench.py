@@ -114,7 +114,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bivariate-n20000",
-                    choices=sorted(inputs.WORKLOADS) + ["serving", "batch", "mloe"])
+                    choices=sorted(inputs.WORKLOADS) + ["serving", "batch", "mloe", "estimation"])
     ap.add_argument("--n", type=int, default=0, help="override n (profiling runs on small cases only)")
     ap.add_argument("--n-pred", type=int, default=-1)
     ap.add_argument("--nb", type=int, default=0)
@@ -130,8 +130,17 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="serving: skip the tile-size autotuner")
     ap.add_argument("--batch-count", type=int, default=512, help="batch: problems per call")
     ap.add_argument("--mle", type=int, default=0, help="run this many Nelder-Mead steps instead of evaluations")
+    ap.add_argument("--profile-lik", action="store_true",
+                    help="mle: optimise the profile likelihood (marginal variances estimated, Sec. 4.2)")
     ap.add_argument("--mloe-m", type=int, default=100, help="mloe: prediction locations")
     ap.add_argument("--tlr-tol", type=float, default=0.0, help="tile low-rank accuracy (default: the workload's)")
+    ap.add_argument("--est-a", default="0.03,0.09,0.2", help="estimation: range parameters (weak, moderate, strong)")
+    ap.add_argument("--replicates", type=int, default=2, help="estimation: simulated fields per range")
+    ap.add_argument("--est-full", action="store_true", help="estimation: full likelihood instead of the profile one")
+    ap.add_argument("--est-budget-s", type=float, default=600.0,
+                    help="estimation: start no new MLE run after this many seconds")
+    ap.add_argument("--dst", type=int, default=0,
+                    help="tile low-rank workloads: Diagonal Super Tile, keep this many tile diagonals (Sec. 3.4)")
     return ap.parse_args()
 
 
@@ -147,6 +156,9 @@ def workload(args):
     if args.tlr_tol > 0 and w.extra.get("prec") == 2:
         w = inputs.Workload(w.name + "-tol%g" % args.tlr_tol, w.n, w.theta, n_pred=w.n_pred, nb=w.nb,
                             loc_seed=w.loc_seed, z_seed=w.z_seed, extra=dict(w.extra, tlr_tol=args.tlr_tol))
+    if args.dst > 0 and w.extra.get("prec") == 2:
+        w = inputs.Workload(w.name + "-dst%d" % args.dst, w.n, w.theta, n_pred=w.n_pred, nb=w.nb,
+                            loc_seed=w.loc_seed, z_seed=w.z_seed, extra=dict(w.extra, dst=args.dst))
     return w
 
 
@@ -287,6 +299,9 @@ def config_json(w, args):
     if w.extra.get("prec") == 2:
         form = ("tile low-rank: dense FP64 diagonal tiles, off-diagonal tiles U V' at absolute accuracy %g, "
                 "rank <= %d (dense beyond)" % (w.extra.get("tlr_tol", 1e-9), w.extra.get("tlr_kmax", 200)))
+        if w.extra.get("dst"):
+            form = ("Diagonal Super Tile: the %d tile diagonals nearest the diagonal kept dense, the other tiles "
+                    "dropped" % w.extra["dst"])
     if w.extra.get("prec") == 1:
         form = ("mixed: FP64 diagonal tiles, FP32 band of %d tiles, %s tensor cores beyond, %d FP64 refinement sweeps"
                 % (w.extra.get("band", 4), "BF16" if w.extra.get("lowp") else "FP16x2", w.extra.get("refine_iters", 2)))
@@ -698,6 +713,18 @@ def run_serving(args):
 # --------------------------------------------------------------------------
 # MLE: Nelder-Mead steps (Sec. 5.1) on the workload's data and form
 # --------------------------------------------------------------------------
+def theta_rel_error(best, spec):
+    """|estimate - truth| / |truth| per parameter (beta: absolute error)."""
+    p = spec.p
+    bt = np.asarray(best.beta, dtype=np.float64).reshape(p, p)
+    true_b = list(spec.beta) if p > 1 else []
+    est_b = [float(bt[i, j]) for i in range(p) for j in range(i + 1, p)]
+    return {"sigma2": [abs(e - t) / t for e, t in zip(best.sigma2, spec.sigma2)],
+            "a": abs(best.a - spec.a) / spec.a,
+            "nu": [abs(e - t) / t for e, t in zip(best.nu, spec.nu)],
+            "beta_abs": [abs(e - t) for e, t in zip(est_b, true_b)]}
+
+
 def run_mle(args, w, ctx, d_locs, d_z, theta, o, dev):
     import torch
 
@@ -706,7 +733,7 @@ def run_mle(args, w, ctx, d_locs, d_z, theta, o, dev):
     # start: a x 1.3, nu x 0.9, sigma^2 x 1.1, beta x 0.8
     th0 = geo.Theta(tuple(1.1 * v for v in spec.sigma2), 1.3 * spec.a, tuple(0.9 * v for v in spec.nu),
                     tuple(0.8 * v for v in spec.beta) if spec.p > 1 else None)
-    st = geo.geo_mle_init(th0)
+    st = geo.geo_mle_init(th0, profile=args.profile_lik)
     ll_true, _ = geo.geo_loglik(ctx, d_locs, d_z, theta, o)
     torch.cuda.synchronize()
     clocks = ClockSampler(dev.index)
@@ -728,6 +755,8 @@ def run_mle(args, w, ctx, d_locs, d_z, theta, o, dev):
            "best_theta": {"sigma2": list(best.sigma2), "a": best.a, "nu": list(best.nu),
                           "beta": [float(b) for b in np.asarray(best.beta).ravel()]},
            "start_theta": {"sigma2": list(th0.sigma2), "a": th0.a, "nu": list(th0.nu)},
+           "objective": "profile" if args.profile_lik else "full",
+           "theta_rel_error": theta_rel_error(best, spec),
            "clocks": clk}
     print(json.dumps(out), flush=True)
     ctx.close()
@@ -923,6 +952,128 @@ def run_mloe(args):
     return 0
 
 
+# --------------------------------------------------------------------------
+# estimation: parameter recovery of exact, TLR and DST fits (Sec. 6, Experiment 2)
+# --------------------------------------------------------------------------
+EST_METHODS = [("exact", {}), ("TLR5", {"tol": 1e-5}), ("TLR7", {"tol": 1e-7}), ("TLR9", {"tol": 1e-9}),
+               ("DST 40/60", {"keep": 0.4}), ("DST 70/30", {"keep": 0.7})]
+
+
+def dst_band(T: int, keep: float) -> int:
+    """Tile diagonals d whose share of the T x T tiles of Sigma, (T + 2 sum_{k<d} (T - k)) / T^2, is closest
+    to ``keep`` (DST 40/60 keeps 40 % of the tiles nearest the diagonal)."""
+    best, best_err = 1, 2.0
+    for d in range(1, T + 1):
+        kept = T + 2 * sum(T - k for k in range(1, d))
+        if abs(kept / T / T - keep) < best_err:
+            best, best_err = d, abs(kept / T / T - keep)
+    return best
+
+
+def est_opts(geo, method, N, nb):
+    kind = dict(EST_METHODS)[method]
+    if "tol" in kind:
+        return geo.opts(prec=geo.GEO_PREC_TLR, nb=nb, tlr_tol=kind["tol"], tlr_kmax=nb // 4)
+    if "keep" in kind:
+        return geo.opts(prec=geo.GEO_PREC_TLR, nb=nb, tlr_tol=1e-9, tlr_kmax=nb // 4,
+                        dst=dst_band((N + nb - 1) // nb, kind["keep"]))
+    return geo.opts(nb=nb)
+
+
+def nm_converged(st, ftol=1e-6, xtol=1e-5):
+    q = st.q
+    if not st.initialized:
+        return False
+    fs = [st.f[v] for v in range(q + 1)]
+    if not all(math.isfinite(f) for f in fs) or fs[-1] - fs[0] > ftol:
+        return False
+    return max(abs(st.x[v][d] - st.x[0][d]) for v in range(1, q + 1) for d in range(q)) < xtol
+
+
+def run_estimation(args):
+    import torch
+
+    import paper_2008_07437_gb300 as geo
+    from paper_2008_07437_gb300 import build as gbuild
+    torch.cuda.set_device(0)
+    gbuild.build()
+    dev = torch.device("cuda", 0)
+    n = args.n or 1600
+    p = 2
+    N = p * n
+    nb = args.nb or 2 * ((N // 10 + 1) // 2)          # ten tile rows, nb a multiple of p
+    max_iter = args.mle or 400
+    ranges = [float(v) for v in args.est_a.split(",")]
+    ctx = geo.geo_create(0)
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    t_start = time.perf_counter()
+    results, runs, skipped = {}, 0, 0
+    for a in ranges:
+        truth = inputs.ThetaSpec((1.0, 1.0), a, (0.5, 1.0), (0.5,))
+        th_true = geo.Theta.from_spec(truth)
+        per = {m: [] for m, _ in EST_METHODS}
+        for r in range(args.replicates):
+            locs = inputs.jittered_grid(n, 3000 + r)
+            dl = torch.as_tensor(locs, device=dev).contiguous()
+            de = torch.as_tensor(inputs.normals(4000 + r, N), device=dev)
+            dz = torch.empty(N, dtype=torch.float64, device=dev)
+            geo.geo_simulate(ctx, dl, de, th_true, dz, geo.opts(nb=nb))
+            start = geo.Theta((1.2, 0.8), 1.3 * a, (0.6, 0.9), 0.3)
+            for m, _ in EST_METHODS:
+                if time.perf_counter() - t_start > args.est_budget_s:
+                    skipped += 1
+                    continue
+                o = est_opts(geo, m, N, nb)
+                st = geo.geo_mle_init(start, 0.1, profile=not args.est_full)
+                t0 = time.perf_counter()
+                it = 0
+                while it < max_iter and not nm_converged(st):
+                    geo.geo_mle_step(ctx, st, dl, dz, o)
+                    it += 1
+                dt = time.perf_counter() - t0
+                best, ll = geo.geo_mle_best(st)
+                per[m].append({"sigma2": list(best.sigma2), "a": best.a, "nu": list(best.nu),
+                               "beta": float(np.asarray(best.beta).reshape(2, 2)[0, 1]), "loglik": ll,
+                               "iters": st.iter, "evals": st.evals, "converged": nm_converged(st), "s": dt})
+                runs += 1
+                print("a=%g r=%d %-9s %3d it %4d ev %6.1f s  a=%.4f nu=(%.3f, %.3f) beta=%.3f s2=(%.3f, %.3f)" % (
+                    a, r, m, st.iter, st.evals, dt, best.a, best.nu[0], best.nu[1], per[m][-1]["beta"],
+                    best.sigma2[0], best.sigma2[1]), file=sys.stderr, flush=True)
+        summary = {}
+        tv = {"sigma2_1": 1.0, "sigma2_2": 1.0, "a": a, "nu_1": 0.5, "nu_2": 1.0, "beta": 0.5}
+        for m, est in per.items():
+            if not est:
+                continue
+            vals = {"sigma2_1": [e["sigma2"][0] for e in est], "sigma2_2": [e["sigma2"][1] for e in est],
+                    "a": [e["a"] for e in est], "nu_1": [e["nu"][0] for e in est],
+                    "nu_2": [e["nu"][1] for e in est], "beta": [e["beta"] for e in est]}
+            summary[m] = {"median": {k: float(np.median(v)) for k, v in vals.items()},
+                          "std": {k: float(np.std(v)) for k, v in vals.items()},
+                          "median_rel_err": {k: float(np.median([abs(x - tv[k]) / abs(tv[k]) for x in v]))
+                                             for k, v in vals.items()},
+                          "runs": est}
+        results["a=%g" % a] = summary
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t_start
+    clk = clocks.stop()
+    out = {"metric": "estimation study wall time", "value": t, "unit": "s", "n_gpus": 1, "steps": runs,
+           "warmup": 0, "ms_per_step": 1e3 * t / max(runs, 1), "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "estimation", "n": n, "p": p, "N": N, "nb": nb, "tiles": (N + nb - 1) // nb,
+                      "truth": {"sigma2": [1.0, 1.0], "nu": [0.5, 1.0], "beta": 0.5, "a": ranges},
+                      "replicates": args.replicates, "objective": "full" if args.est_full else "profile",
+                      "start": "sigma2 (1.2, 0.8), a x 1.3, nu (0.6, 0.9), beta 0.3; simplex step 0.1",
+                      "stop": "f spread <= 1e-6 and vertex spread <= 1e-5, or %d iterations" % max_iter,
+                      "tlr_kmax": nb // 4,
+                      "dst_bands": {m: dst_band((N + nb - 1) // nb, k["keep"]) for m, k in EST_METHODS
+                                    if "keep" in k}},
+           "results": results, "runs_skipped_for_time": skipped, "clocks": clk}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_serving_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -950,6 +1101,11 @@ def main():
             print(json.dumps({"impl": "reference", "unavailable": "mloe mode: the oracle time is this mode's cpu_baseline"}))
             return 0
         return run_mloe(args)
+    if args.workload == "estimation":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "estimation mode: a study of fits, not a timed path"}))
+            return 0
+        return run_estimation(args)
     if args.workload == "batch":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "batch mode: use the default workload's reference arm"}))

@@ -140,6 +140,31 @@ int geo_loglik(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev,
                const geo_opts *opts, double *loglik_host, geo_factor **keep, int *info, void *stream);
 
 /*
+ * Marginal variances of the profile likelihood (Sec. 4.2):
+ *   sigma2_host[i] = n^-1 Z_i' R_ii^-1 Z_i,  i = 0 .. p-1,
+ * Z_i the n values of variable i (z_dev[l*p + i], Representation I) and R_ii
+ * the correlation matrix of variable i alone (Eq. 2 with i = j,
+ * sigma^2_ii = 1, smoothness nu_ii, range a).  theta->sigma2 and theta->beta
+ * are not read.  Each R_ii is factored in the form opts selects (as
+ * geo_loglik with p = 1); in the tile-low-rank form (and its DST variant) with
+ * tiles of nb / p rows, so that they cover the same blocks of locations as the
+ * tiles of Sigma.  sigma2_host: p doubles (host).  info as in
+ * geo_loglik, for the first R_ii that is not positive definite.
+ * Synchronises `stream`.
+ */
+int geo_sigma2_hat(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev, const geo_theta *theta,
+                   const geo_opts *opts, double *sigma2_host, int *info, void *stream);
+
+/*
+ * Profile log-likelihood (Sec. 4.2): Eq. 1 at theta with its marginal
+ * variances replaced by geo_sigma2_hat.  The cost is one likelihood of size
+ * p n and p of size n.  loglik_host, sigma2_host (p doubles): host, either may
+ * be NULL.  Errors as geo_loglik.  Synchronises `stream`.
+ */
+int geo_loglik_profile(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev, const geo_theta *theta,
+                       const geo_opts *opts, double *loglik_host, double *sigma2_host, int *info, void *stream);
+
+/*
  * Cokriging predictor, Eq. 3 / Eq. 4 (Sec. 4.3): for each of the m new
  * locations s0, Zhat(s0) = c0' Sigma^-1 Z, c0 the (p n) x p cross-covariance
  * between Z(s0) and the observed locations.  Every new location misses all p
@@ -220,10 +245,20 @@ typedef struct {
     double x[GEO_MLE_QMAX + 1][GEO_MLE_QMAX];  /* vertices, ordered best first once initialized */
     double f[GEO_MLE_QMAX + 1];                /* -l at each vertex */
     double last_f;                             /* -l of the last evaluation */
+    int profile;                               /* 1 = profile likelihood (geo_mle_init_profile) */
+    double s2[GEO_MLE_QMAX + 1][GEO_PMAX];     /* profile: sigma^2 estimate at each vertex */
 } geo_mle_state;
 
 /* Start a simplex at theta0 (host) with x0 + step * e_k as the other vertices. */
 int geo_mle_init(geo_mle_state *state, const geo_theta *theta0, double step);
+
+/*
+ * The same over the profile likelihood (Sec. 4.2): coordinates
+ * x = (log a, log nu_i, beta_ij for i < j), every evaluation is
+ * geo_loglik_profile, and the marginal variances of a vertex are the
+ * geo_sigma2_hat values at it (theta0->sigma2 is not read; it may be NULL).
+ */
+int geo_mle_init_profile(geo_mle_state *state, const geo_theta *theta0, double step);
 
 /*
  * One unit of work: the q + 1 initial evaluations on the first call, one
@@ -233,7 +268,8 @@ int geo_mle_init(geo_mle_state *state, const geo_theta *theta0, double step);
 int geo_mle_step(geo_ctx *ctx, geo_mle_state *state, const double *locs_dev, int n, const double *z_dev,
                  const geo_opts *opts, void *stream);
 
-/* Best vertex as theta: sigma2[p], a, nu[p], beta[p*p] (host; beta may be NULL). */
+/* Best vertex as theta: sigma2[p], a, nu[p], beta[p*p] (host; beta may be NULL).  For a
+   profile run sigma2 is the sigma^2 estimate at the best vertex. */
 int geo_mle_best(const geo_mle_state *state, double *sigma2, double *a, double *nu, double *beta,
                  double *loglik);
 

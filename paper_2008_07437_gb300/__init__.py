@@ -56,7 +56,8 @@ class geo_mle_state(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("q", ctypes.c_int), ("iter", ctypes.c_int), ("evals", ctypes.c_int),
                 ("initialized", ctypes.c_int), ("step", ctypes.c_double),
                 ("x", (ctypes.c_double * GEO_MLE_QMAX) * (GEO_MLE_QMAX + 1)),
-                ("f", ctypes.c_double * (GEO_MLE_QMAX + 1)), ("last_f", ctypes.c_double)]
+                ("f", ctypes.c_double * (GEO_MLE_QMAX + 1)), ("last_f", ctypes.c_double),
+                ("profile", ctypes.c_int), ("s2", (ctypes.c_double * GEO_PMAX) * (GEO_MLE_QMAX + 1))]
 
 
 GEO_K_NAMES = ["covgen", "potrf", "trsm", "gemm", "reduce", "solve", "predict", "aux", "tcgemm", "sgemm", "tlr"]
@@ -109,6 +110,11 @@ SIGNATURES = {
     "geo_factor_free": (None, [_P]),
     "geo_morton_order": (_I, [_P, _I, _P]),
     "geo_mle_init": (_I, [ctypes.POINTER(geo_mle_state), ctypes.POINTER(geo_theta), _D]),
+    "geo_mle_init_profile": (_I, [ctypes.POINTER(geo_mle_state), ctypes.POINTER(geo_theta), _D]),
+    "geo_sigma2_hat": (_I, [_P, _P, _I, _P, ctypes.POINTER(geo_theta), ctypes.POINTER(geo_opts), _P,
+                            ctypes.POINTER(_I), _P]),
+    "geo_loglik_profile": (_I, [_P, _P, _I, _P, ctypes.POINTER(geo_theta), ctypes.POINTER(geo_opts), _P, _P,
+                                ctypes.POINTER(_I), _P]),
     "geo_mle_step": (_I, [_P, ctypes.POINTER(geo_mle_state), _P, _I, _P, ctypes.POINTER(geo_opts), _P]),
     "geo_mle_best": (_I, [ctypes.POINTER(geo_mle_state), _P, _P, _P, _P, _P]),
     "geo_profile_enable": (_I, [_P, _I]),
@@ -301,6 +307,43 @@ def geo_loglik(ctx: Context, locs, z, theta: Theta, options: geo_opts | None = N
     return val.value, (Factor(ctx, fac) if keep else None)
 
 
+def _raise_info(ctx: Context, rc: int, info: ctypes.c_int):
+    if rc == GEO_ENOTSPD:
+        err = GeoError(rc, ctx.lib.geo_last_error(ctx.handle).decode())
+        err.info = info.value
+        raise err
+    ctx.check(rc)
+
+
+def geo_sigma2_hat(ctx: Context, locs, z, theta: Theta, options: geo_opts | None = None, stream=None) -> np.ndarray:
+    """Sec. 4.2 marginal variances n^-1 Z_i' R_ii^-1 Z_i (theta's sigma^2 and beta unused)."""
+    import torch
+    th, _keep = theta.to_c()
+    out = np.zeros(len(theta.sigma2))
+    info = ctypes.c_int()
+    rc = ctx.lib.geo_sigma2_hat(ctx.handle, _dev_ptr(locs, "locs", torch.float64), locs.shape[0],
+                                _dev_ptr(z, "z", torch.float64), ctypes.byref(th),
+                                ctypes.byref(options) if options is not None else None,
+                                out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(info), _stream(stream))
+    _raise_info(ctx, rc, info)
+    return out
+
+
+def geo_loglik_profile(ctx: Context, locs, z, theta: Theta, options: geo_opts | None = None, stream=None):
+    """Profile log-likelihood (Sec. 4.2).  Returns (loglik, sigma2_hat)."""
+    import torch
+    th, _keep = theta.to_c()
+    val = ctypes.c_double()
+    s2 = np.zeros(len(theta.sigma2))
+    info = ctypes.c_int()
+    rc = ctx.lib.geo_loglik_profile(ctx.handle, _dev_ptr(locs, "locs", torch.float64), locs.shape[0],
+                                    _dev_ptr(z, "z", torch.float64), ctypes.byref(th),
+                                    ctypes.byref(options) if options is not None else None, ctypes.byref(val),
+                                    s2.ctypes.data_as(ctypes.c_void_p), ctypes.byref(info), _stream(stream))
+    _raise_info(ctx, rc, info)
+    return val.value, s2
+
+
 def geo_predict(ctx: Context, factor: Factor, new_locs, zhat, stream=None):
     """Eq. 3 / Eq. 4 cokriging at ``new_locs`` into ``zhat`` (p*m, Rep. I)."""
     import torch
@@ -352,12 +395,14 @@ def geo_morton_order(locs) -> np.ndarray:
     return perm[:n].astype(np.int64)
 
 
-def geo_mle_init(theta0: Theta, step: float = 0.1) -> geo_mle_state:
+def geo_mle_init(theta0: Theta, step: float = 0.1, profile: bool = False) -> geo_mle_state:
+    """Nelder-Mead state at theta0; ``profile`` runs it over the profile likelihood (Sec. 4.2)."""
     st = geo_mle_state()
     th, _keep = theta0.to_c()
-    rc = load_library().geo_mle_init(ctypes.byref(st), ctypes.byref(th), float(step))
+    name = "geo_mle_init_profile" if profile else "geo_mle_init"
+    rc = getattr(load_library(), name)(ctypes.byref(st), ctypes.byref(th), float(step))
     if rc != GEO_OK:
-        raise GeoError(rc, "geo_mle_init")
+        raise GeoError(rc, name)
     return st
 
 

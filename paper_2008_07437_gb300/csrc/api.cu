@@ -766,6 +766,64 @@ int geo_loglik(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev,
     return GEO_OK;
 }
 
+// Sec. 4.2: sigma^2_ii = n^-1 Z_i' R_ii^-1 Z_i.  Z_i is copied out of the
+// Representation I vector with one strided copy and each R_ii is a p = 1
+// likelihood (sigma^2 = 1, nu_ii, a) in the requested form; Z_i' R_ii^-1 Z_i is
+// that likelihood's data term.
+int geo_sigma2_hat(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev, const geo_theta *theta,
+                   const geo_opts *opts, double *sigma2_host, int *info, void *stream) {
+    if (!ctx) return GEO_EINVAL;
+    if (info) *info = 0;
+    if (!theta || theta->p < 1 || theta->p > GEO_PMAX || !theta->nu || !sigma2_host || n <= 0 || !locs_dev ||
+        !z_dev)
+        return fail(ctx, GEO_EINVAL, "geo_sigma2_hat: bad arguments");
+    SetDevice sd(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int p = theta->p;
+    void *pz;
+    int rc;
+    if ((rc = dev_alloc(ctx, &pz, sizeof(double) * n))) return rc;
+    double *zi = (double *)pz;
+    const double one = 1.0;
+    // tile-low-rank / DST: marginal tiles of nb / p rows cover the same location blocks as Sigma's tiles
+    geo_opts om;
+    const geo_opts *mo = opts;
+    if (opts && opts->prec == GEO_PREC_TLR && opts->nb > 0) {
+        om = *opts;
+        om.nb = opts->nb / p;
+        mo = &om;
+    }
+    for (int i = 0; i < p && rc == GEO_OK; ++i) {
+        cudaError_t e = cudaMemcpy2DAsync(zi, sizeof(double), z_dev + i, sizeof(double) * p, sizeof(double), n,
+                                          cudaMemcpyDeviceToDevice, s);
+        if (e) {
+            rc = cuda_fail(ctx, e, "geo_sigma2_hat");
+            break;
+        }
+        geo_theta ti{1, &one, theta->nu + i, nullptr, theta->a};
+        double ll;
+        rc = geo_loglik(ctx, locs_dev, n, zi, &ti, mo, &ll, nullptr, info, stream);
+        if (rc == GEO_OK) sigma2_host[i] = ctx->h_res->quad / n;
+    }
+    cudaStreamSynchronize(s);
+    dev_free(ctx, zi, sizeof(double) * n);
+    return rc;
+}
+
+int geo_loglik_profile(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev, const geo_theta *theta,
+                       const geo_opts *opts, double *loglik_host, double *sigma2_host, int *info, void *stream) {
+    if (!ctx) return GEO_EINVAL;
+    if (!theta || theta->p < 1 || theta->p > GEO_PMAX) return fail(ctx, GEO_EINVAL, "geo_loglik_profile: bad theta");
+    double s2[GEO_PMAX];
+    int rc = geo_sigma2_hat(ctx, locs_dev, n, z_dev, theta, opts, s2, info, stream);
+    if (rc) return rc;
+    if (sigma2_host)
+        for (int i = 0; i < theta->p; ++i) sigma2_host[i] = s2[i];
+    geo_theta t = *theta;
+    t.sigma2 = s2;
+    return geo_loglik(ctx, locs_dev, n, z_dev, &t, opts, loglik_host, nullptr, info, stream);
+}
+
 int geo_predict(geo_ctx *ctx, const geo_factor *factor, const double *new_locs_dev, int m, double *zhat_dev,
                 void *stream) {
     if (!ctx || !factor) return GEO_EINVAL;

@@ -75,6 +75,21 @@ def test_mle_init_simplex(lib):
         assert np.array_equal(row, expect)
 
 
+def test_mle_init_profile_simplex(lib):
+    # profile coordinates (log a, log nu_i, beta_ij): the sigma^2 leave the simplex (Sec. 4.2)
+    th = geo.Theta((1.0, 2.0, 3.0), 0.09, (0.5, 1.0, 1.5), (0.5, 0.2, 0.1))
+    st = geo.geo_mle_init(th, 0.05, profile=True)
+    assert st.p == 3 and st.q == 7 and st.profile == 1 and st.initialized == 0
+    x0 = oracle.profile_theta_to_x(oracle.Theta([1.0, 2.0, 3.0], 0.09, [0.5, 1.0, 1.5], [0.5, 0.2, 0.1]))
+    for v in range(8):
+        row = np.array([st.x[v][d] for d in range(7)])
+        expect = x0.copy()
+        if v:
+            expect[v - 1] += 0.05
+        assert np.array_equal(row, expect)
+    assert geo.geo_mle_init(th, 0.05).profile == 0
+
+
 def test_create_without_gpu_reports_error(lib):
     import torch
     if torch.cuda.is_available():
