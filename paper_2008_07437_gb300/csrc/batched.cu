@@ -14,7 +14,86 @@ namespace cg = cooperative_groups;
 namespace {
 
 // ---- batched GEMM: C = alpha op(A) op(B) + beta C (column-major) ----------
+// One CTA per 64 x 64 output tile of one problem, 4 x 4 outputs per thread
+// (rows ty + 16 i, columns tx + 16 j).  The FP64 pipe is the limit (a few DFMA
+// per clock per SM), so work on padding is the waste to avoid: a tile whose
+// rows (columns) end inside it runs only the IM (JM) sixteen-row (-column)
+// strips that hold outputs, and the last K slice runs only its valid depth.
+// Ranks and sketch widths (the skinny side of most products here) are rarely
+// multiples of 64.
 constexpr int BT = 64, BKK = 16;
+
+template <int IM, int JM>
+__device__ __forceinline__ void bgemm_tile(const GemmDesc &g, int tm, int tn, double (*As)[BT + 2],
+                                           double (*Bs)[BT + 2]) {
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[IM][JM];
+#pragma unroll
+    for (int i = 0; i < IM; ++i)
+#pragma unroll
+        for (int j = 0; j < JM; ++j) acc[i][j] = 0.0;
+    for (int k0 = 0; k0 < g.k; k0 += BKK) {
+        // consecutive threads walk the operand's contiguous index: rows for a
+        // row-contiguous slice, K for a K-contiguous one (transposed A, plain B)
+        for (int t = threadIdx.x; t < BKK * 16 * IM; t += 256) {
+            const int kk = g.ta ? t % BKK : t / (16 * IM), r = g.ta ? t / BKK : t % (16 * IM);
+            const int kg = k0 + kk;
+            double a = 0.0;
+            if (kg < g.k && tm + r < g.m)
+                a = g.ta ? g.A[(long long)(tm + r) * g.lda + kg] : g.A[(long long)kg * g.lda + tm + r];
+            As[kk][r] = a;
+        }
+        for (int t = threadIdx.x; t < BKK * 16 * JM; t += 256) {
+            const int kk = g.tb ? t / (16 * JM) : t % BKK, r = g.tb ? t % (16 * JM) : t / BKK;
+            const int kg = k0 + kk;
+            double b = 0.0;
+            if (kg < g.k && tn + r < g.n)
+                b = g.tb ? g.B[(long long)kg * g.ldb + tn + r] : g.B[(long long)(tn + r) * g.ldb + kg];
+            Bs[kk][r] = b;
+        }
+        __syncthreads();
+        const int kc = min(BKK, g.k - k0);   // uniform over the CTA
+        if (kc == BKK) {
+#pragma unroll
+            for (int kk = 0; kk < BKK; ++kk) {
+                double a[IM], b[JM];
+#pragma unroll
+                for (int i = 0; i < IM; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < JM; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < IM; ++i)
+#pragma unroll
+                    for (int j = 0; j < JM; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
+        } else {
+            for (int kk = 0; kk < kc; ++kk) {
+                double a[IM], b[JM];
+#pragma unroll
+                for (int i = 0; i < IM; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < JM; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < IM; ++i)
+#pragma unroll
+                    for (int j = 0; j < JM; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < JM; ++j) {
+        const int c = tn + tx + 16 * j;
+        if (c >= g.n) continue;
+#pragma unroll
+        for (int i = 0; i < IM; ++i) {
+            const int r = tm + ty + 16 * i;
+            if (r >= g.m) continue;
+            double *p = g.C + (long long)c * g.ldc + r;
+            *p = g.alpha * acc[i][j] + (g.beta == 0.0 ? 0.0 : g.beta * *p);
+        }
+    }
+}
 
 __global__ void __launch_bounds__(256) k_bgemm(const GemmDesc *__restrict__ d, int count) {
     __shared__ double As[BKK][BT + 2];
@@ -26,57 +105,16 @@ __global__ void __launch_bounds__(256) k_bgemm(const GemmDesc *__restrict__ d, i
     const int tiles_n = (g.n + BT - 1) / BT;
     if ((int)blockIdx.x >= tiles_m * tiles_n) return;
     const int tm = (blockIdx.x % tiles_m) * BT, tn = (blockIdx.x / tiles_m) * BT;
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    double acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-    for (int k0 = 0; k0 < g.k; k0 += BKK) {
-        // consecutive threads walk the operand's contiguous index: rows for a
-        // row-contiguous slice, K for a K-contiguous one (transposed A, plain B)
-        for (int t = threadIdx.x; t < BKK * BT; t += 256) {
-            const int kk = g.ta ? t % BKK : t / BT, r = g.ta ? t / BKK : t % BT;
-            const int kg = k0 + kk;
-            double a = 0.0;
-            if (kg < g.k && tm + r < g.m)
-                a = g.ta ? g.A[(long long)(tm + r) * g.lda + kg] : g.A[(long long)kg * g.lda + tm + r];
-            As[kk][r] = a;
-        }
-        for (int t = threadIdx.x; t < BKK * BT; t += 256) {
-            const int kk = g.tb ? t / BT : t % BKK, r = g.tb ? t % BT : t / BKK;
-            const int kg = k0 + kk;
-            double b = 0.0;
-            if (kg < g.k && tn + r < g.n)
-                b = g.tb ? g.B[(long long)kg * g.ldb + tn + r] : g.B[(long long)(tn + r) * g.ldb + kg];
-            Bs[kk][r] = b;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BKK; ++kk) {
-            double a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int c = tn + tx + 16 * j;
-        if (c >= g.n) continue;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int r = tm + ty + 16 * i;
-            if (r >= g.m) continue;
-            double *p = g.C + (long long)c * g.ldc + r;
-            *p = g.alpha * acc[i][j] + (g.beta == 0.0 ? 0.0 : g.beta * *p);
-        }
+    const int im = min(4, (g.m - tm + 15) / 16), jm = min(4, (g.n - tn + 15) / 16);
+    switch ((im - 1) * 4 + (jm - 1)) {
+#define GEO_BGEMM_CASE(I, J) \
+    case (I - 1) * 4 + (J - 1): bgemm_tile<I, J>(g, tm, tn, As, Bs); break;
+        GEO_BGEMM_CASE(1, 1) GEO_BGEMM_CASE(1, 2) GEO_BGEMM_CASE(1, 3) GEO_BGEMM_CASE(1, 4)
+        GEO_BGEMM_CASE(2, 1) GEO_BGEMM_CASE(2, 2) GEO_BGEMM_CASE(2, 3) GEO_BGEMM_CASE(2, 4)
+        GEO_BGEMM_CASE(3, 1) GEO_BGEMM_CASE(3, 2) GEO_BGEMM_CASE(3, 3) GEO_BGEMM_CASE(3, 4)
+        GEO_BGEMM_CASE(4, 1) GEO_BGEMM_CASE(4, 2) GEO_BGEMM_CASE(4, 3) GEO_BGEMM_CASE(4, 4)
+#undef GEO_BGEMM_CASE
+        default: break;
     }
 }
 
