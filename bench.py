@@ -137,6 +137,8 @@ def parse():
     ap.add_argument("--est-a", default="0.03,0.09,0.2", help="estimation: range parameters (weak, moderate, strong)")
     ap.add_argument("--replicates", type=int, default=2, help="estimation: simulated fields per range")
     ap.add_argument("--est-full", action="store_true", help="estimation: full likelihood instead of the profile one")
+    ap.add_argument("--est-methods", default="exact,TLR5,TLR7,TLR9,DST 40/60,DST 70/30",
+                    help="estimation: comma-separated subset of the fits")
     ap.add_argument("--est-budget-s", type=float, default=600.0,
                     help="estimation: start no new MLE run after this many seconds")
     ap.add_argument("--dst", type=int, default=0,
@@ -1004,6 +1006,10 @@ def run_estimation(args):
     nb = args.nb or 2 * ((N // 10 + 1) // 2)          # ten tile rows, nb a multiple of p
     max_iter = args.mle or 400
     ranges = [float(v) for v in args.est_a.split(",")]
+    methods = [m.strip() for m in args.est_methods.split(",")]
+    unknown = [m for m in methods if m not in dict(EST_METHODS)]
+    if unknown:
+        raise SystemExit("unknown estimation methods: %s" % unknown)
     ctx = geo.geo_create(0)
     clocks = ClockSampler(dev.index)
     clocks.start()
@@ -1012,7 +1018,7 @@ def run_estimation(args):
     for a in ranges:
         truth = inputs.ThetaSpec((1.0, 1.0), a, (0.5, 1.0), (0.5,))
         th_true = geo.Theta.from_spec(truth)
-        per = {m: [] for m, _ in EST_METHODS}
+        per = {m: [] for m in methods}
         for r in range(args.replicates):
             locs = inputs.jittered_grid(n, 3000 + r)
             dl = torch.as_tensor(locs, device=dev).contiguous()
@@ -1020,7 +1026,7 @@ def run_estimation(args):
             dz = torch.empty(N, dtype=torch.float64, device=dev)
             geo.geo_simulate(ctx, dl, de, th_true, dz, geo.opts(nb=nb))
             start = geo.Theta((1.2, 0.8), 1.3 * a, (0.6, 0.9), 0.3)
-            for m, _ in EST_METHODS:
+            for m in methods:
                 if time.perf_counter() - t_start > args.est_budget_s:
                     skipped += 1
                     continue
@@ -1028,14 +1034,19 @@ def run_estimation(args):
                 st = geo.geo_mle_init(start, 0.1, profile=not args.est_full)
                 t0 = time.perf_counter()
                 it = 0
+                infeasible = False
                 while it < max_iter and not nm_converged(st):
                     geo.geo_mle_step(ctx, st, dl, dz, o)
                     it += 1
+                    if it == 1 and all(math.isinf(st.f[v]) for v in range(st.q + 1)):
+                        infeasible = True    # no vertex of the initial simplex has a positive definite matrix
+                        break
                 dt = time.perf_counter() - t0
                 best, ll = geo.geo_mle_best(st)
                 per[m].append({"sigma2": list(best.sigma2), "a": best.a, "nu": list(best.nu),
                                "beta": float(np.asarray(best.beta).reshape(2, 2)[0, 1]), "loglik": ll,
-                               "iters": st.iter, "evals": st.evals, "converged": nm_converged(st), "s": dt})
+                               "iters": st.iter, "evals": st.evals, "converged": nm_converged(st), "s": dt,
+                               "infeasible": infeasible})
                 runs += 1
                 print("a=%g r=%d %-9s %3d it %4d ev %6.1f s  a=%.4f nu=(%.3f, %.3f) beta=%.3f s2=(%.3f, %.3f)" % (
                     a, r, m, st.iter, st.evals, dt, best.a, best.nu[0], best.nu[1], per[m][-1]["beta"],
@@ -1045,6 +1056,11 @@ def run_estimation(args):
         for m, est in per.items():
             if not est:
                 continue
+            if all(e["infeasible"] for e in est):
+                summary[m] = {"infeasible": "the matrix (or a marginal R_ii) with the dropped tiles is not positive "
+                                            "definite at any vertex of the initial simplex", "runs": est}
+                continue
+            est = [e for e in est if not e["infeasible"]]
             vals = {"sigma2_1": [e["sigma2"][0] for e in est], "sigma2_2": [e["sigma2"][1] for e in est],
                     "a": [e["a"] for e in est], "nu_1": [e["nu"][0] for e in est],
                     "nu_2": [e["nu"][1] for e in est], "beta": [e["beta"] for e in est]}
