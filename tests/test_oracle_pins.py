@@ -591,3 +591,25 @@ def test_profile_coordinates_roundtrip():
     np.testing.assert_allclose(back.nu, [0.4, 1.7], rtol=1e-15)
     assert back.beta[0, 1] == 0.35 and back.beta[1, 0] == 0.35
     np.testing.assert_array_equal(back.sigma2, [1.0, 1.0])
+
+
+def test_profile_mle_reaches_the_full_mle_at_p1():
+    # p = 1: the profile likelihood is exact (Sec. 4.2), so Nelder-Mead over (log a, log nu)
+    # on it and over (log sigma^2, log a, log nu) on Eq. 1 reach the same maximum
+    th = oracle.Theta([1.5], 0.15, [0.9], np.eye(1))
+    locs = inputs.jittered_grid(64, 71)
+    Z = oracle.simulate(th, locs, inputs.normals(72, 64))
+
+    def run(nm, iters):
+        for _ in range(iters):
+            nm.step()
+        return nm.best
+
+    full = oracle.NelderMead(oracle.mle_objective(locs, Z, 1), oracle.theta_to_x(th), step=0.2)
+    prof = oracle.NelderMead(oracle.profile_objective(locs, Z, 1), oracle.profile_theta_to_x(th), step=0.2)
+    xf, ff = run(full, 300)
+    xp, fp = run(prof, 200)
+    assert fp == pytest.approx(ff, abs=1e-6)
+    np.testing.assert_allclose(xp, xf[1:], atol=2e-3)                 # log a, log nu
+    s2 = oracle.sigma2_hat(oracle.profile_x_to_theta(xp, 1), locs, Z)
+    assert math.log(s2[0]) == pytest.approx(xf[0], abs=2e-3)          # log sigma^2
