@@ -304,9 +304,10 @@ int geo_loglik_batch(geo_ctx *ctx, int count, const geo_batch_item *items, doubl
  * C(0) - c0' Sigma^-1 c0 at each new location s0, i.e. the mean square error
  * of the Eq. 3 predictor under the model (the E_t term of Eq. 5).
  *   new_locs_dev  m x 2 (device);  var_dev  p m doubles (device), Representation I
- * Dense FP64 or mixed factors (GEO_EUNSUPPORTED for tile low-rank ones); cost
- * N^2 p m flops (a right-side triangular solve of the m cross-covariances).
- * Synchronises `stream`.
+ * Dense FP64 or mixed factors: N^2 p m flops (a right-side triangular solve
+ * of the m cross-covariances).  Tile-low-rank factors (and their DST form): one
+ * TLR forward solve per column of c0, p m in all, with a stream synchronisation
+ * after each.  Synchronises `stream`.
  */
 int geo_predict_var(geo_ctx *ctx, const geo_factor *factor, const double *new_locs_dev, int m, double *var_dev,
                     void *stream);

@@ -824,6 +824,56 @@ int geo_loglik_profile(geo_ctx *ctx, const double *locs_dev, int n, const double
     return geo_loglik(ctx, locs_dev, n, z_dev, &t, opts, loglik_host, nullptr, info, stream);
 }
 
+// The device workspace and pinned descriptor arena of tlr_solve (the
+// workspace is released when a serving context is trimmed).
+static int tlr_solve_buffers(geo_ctx *ctx, const TlrFactor &F, cudaStream_t s) {
+    if (!ctx->tarena || ctx->tarena_bytes < TLR_ARENA_BYTES)
+        return fail(ctx, GEO_EINVAL, "the tile-low-rank factor belongs to another context");
+    return ensure_buffer(ctx, &ctx->tws, &ctx->tws_bytes, tlr_solve_workspace_bytes(F.N, F.nb, F.kmax), s);
+}
+
+// Sec. 4.3 variances on a tile-low-rank factor: c0 (N x p m, the factor's
+// order) is formed transposed by the cross-covariance kernel, transposed to
+// one contiguous column per right-hand side, solved column by column with the
+// TLR forward solve, and var = C_ii(0) - |L^-1 c0|^2 per column.
+static int predict_var_tlr(geo_ctx *ctx, const geo_factor *f, const double *new_locs_dev, int m, double *var_dev,
+                           cudaStream_t s) {
+    const int p = f->p, N = f->N, pm = p * m;
+    const long long ldx = round_up(pm, 32);
+    const size_t xbytes = sizeof(double) * (size_t)ldx * N, ybytes = sizeof(double) * (size_t)N * pm,
+                 sbytes = sizeof(double) * pm;
+    void *px = nullptr, *py = nullptr, *ps = nullptr;
+    auto done = [&](int code) {
+        cudaStreamSynchronize(s);
+        if (px) dev_free(ctx, px, xbytes);
+        if (py) dev_free(ctx, py, ybytes);
+        if (ps) dev_free(ctx, ps, sbytes);
+        return code;
+    };
+    int rc;
+    cudaStreamSynchronize(s);   // no earlier descriptor copy may still read the pinned arena
+    if ((rc = tlr_solve_buffers(ctx, *f->tlr, s)) || (rc = dev_alloc(ctx, &px, xbytes)) ||
+        (rc = dev_alloc(ctx, &py, ybytes)) || (rc = dev_alloc(ctx, &ps, sbytes)))
+        return done(rc);
+    double c0d[GEO_PMAX];
+    for (int i = 0; i < p; ++i) c0d[i] = f->cp.m[i * p + i].c0;
+    double *X = (double *)px, *Y = (double *)py;
+    cudaError_t e;
+    if ((e = launch_covgen_cross(f->cp, new_locs_dev, m, f->lx, f->ly, f->n, X, ldx, s)) ||
+        (e = launch_transpose(X, ldx, pm, N, Y, N, s)))
+        return done(cuda_fail(ctx, e, "geo_predict_var"));
+    for (int q = 0; q < pm; ++q) {
+        // each solve stages its descriptors in the same pinned arena: wait before the next one refills it
+        if ((e = tlr_solve(*f->tlr, Y + (size_t)q * N, false, ctx->tws, ctx->tarena, s)) ||
+            (e = cudaStreamSynchronize(s)))
+            return done(cuda_fail(ctx, e, "geo_predict_var (TLR solve)"));
+    }
+    if ((e = launch_col_sumsq(Y, N, N, pm, (double *)ps, s)) ||
+        (e = launch_var_finish((const double *)ps, pm, p, c0d, var_dev, s)))
+        return done(cuda_fail(ctx, e, "geo_predict_var"));
+    return done(GEO_OK);
+}
+
 int geo_predict(geo_ctx *ctx, const geo_factor *factor, const double *new_locs_dev, int m, double *zhat_dev,
                 void *stream) {
     if (!ctx || !factor) return GEO_EINVAL;
@@ -835,13 +885,15 @@ int geo_predict(geo_ctx *ctx, const geo_factor *factor, const double *new_locs_d
     cudaStream_t s = (cudaStream_t)stream;
     geo_factor *f = const_cast<geo_factor *>(factor);
     if (!f->w) {
+        int rc;
+        if (f->tlr && (rc = tlr_solve_buffers(ctx, *f->tlr, s))) return rc;
         void *pw;
-        int rc = dev_alloc(ctx, &pw, sizeof(double) * f->N);
-        if (rc) return rc;
+        if ((rc = dev_alloc(ctx, &pw, sizeof(double) * f->N))) return rc;
         f->w = (double *)pw;
         if (f->tlr) {
             CK(cudaMemcpyAsync(f->w, f->ybuf, sizeof(double) * f->N, cudaMemcpyDeviceToDevice, s));
             CK(tlr_solve(*f->tlr, f->w, true, ctx->tws, ctx->tarena, s));
+            CK(cudaStreamSynchronize(s));   // the solve's descriptors sit in the shared pinned arena
         } else {
             CK(backward_solve(f->A, f->ld, f->N, f->A + f->N, f->ld, f->w, ctx->sync, &ctx->st->timeout, s));
         }
@@ -1097,9 +1149,9 @@ int geo_predict_var(geo_ctx *ctx, const geo_factor *factor, const double *new_lo
     if (m < 0) return fail(ctx, GEO_EINVAL, "m < 0");
     if (m == 0) return GEO_OK;
     if (!new_locs_dev || !var_dev) return fail(ctx, GEO_EINVAL, "NULL pointer");
-    if (factor->tlr) return fail(ctx, GEO_EUNSUPPORTED, "prediction variances need a dense or mixed factor");
     SetDevice sd(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
+    if (factor->tlr) return predict_var_tlr(ctx, factor, new_locs_dev, m, var_dev, s);
     const geo_factor *f = factor;
     const int p = f->p, N = f->N, pm = p * m;
     const long long ldx = round_up(pm, 32);

@@ -120,6 +120,10 @@ cudaError_t trsm_right_lower(double *X, long long ldx, int R, const double *L, l
 // X <- X L^-T (X: R x N, L lower); arena_dev: 64 GemmDesc of device scratch.
 cudaError_t trsm_right_upper_t(double *X, long long ldx, int R, const double *L, long long ldl, int N,
                                void *arena_dev, cudaStream_t s);
+// Y = X' (X: R x C column-major, ldx; Y: C x R column-major, ldy).
+cudaError_t launch_transpose(const double *X, long long ldx, int R, int C, double *Y, long long ldy, cudaStream_t s);
+// sums[q] = sum_{c < N} Y[q * ldy + c]^2, q < R (columns of a column-major Y).
+cudaError_t launch_col_sumsq(const double *Y, long long ldy, int N, int R, double *sums, cudaStream_t s);
 // var[q] = c0diag[q mod p] - sums[q] (device arrays of R doubles).
 cudaError_t launch_var_finish(const double *sums, int R, int p, const double *c0diag, double *var, cudaStream_t s);
 // V = X L (L lower; the upper parts of its 64 x 64 diagonal blocks are zeroed);

@@ -111,6 +111,38 @@ __global__ void k_var_finish(const double *s, int R, int p, double c0, double c1
     var[q] = c - s[q];
 }
 
+// Y = X' through a 32 x 32 shared-memory tile: X is R x C (column-major, ldx),
+// Y is C x R (column-major, ldy); reads and writes both run along columns.
+__global__ void __launch_bounds__(256) k_transpose(const double *__restrict__ X, long long ldx, int R, int C,
+                                                   double *__restrict__ Y, long long ldy) {
+    __shared__ double t[32][33];
+    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int r = r0 + threadIdx.x, c = c0 + j;
+        if (r < R && c < C) t[j][threadIdx.x] = X[(long long)c * ldx + r];
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int c = c0 + threadIdx.x, r = r0 + j;
+        if (r < R && c < C) Y[(long long)r * ldy + c] = t[threadIdx.x][j];
+    }
+}
+
+// s[q] = sum_{c < N} Y[q * ldy + c]^2 for q < R: one warp per column, lanes
+// striding the column, then a fixed shuffle tree.
+__global__ void __launch_bounds__(256) k_col_sumsq(const double *__restrict__ Y, long long ldy, int N, int R,
+                                                   double *s) {
+    const int q = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (q >= R) return;   // uniform over the warp
+    double a = 0.0;
+    for (int c = lane; c < N; c += 32) {
+        const double y = Y[(long long)q * ldy + c];
+        a = fma(y, y, a);
+    }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) s[q] = a;
+}
+
 // Zero the strictly upper part of every 64 x 64 diagonal block of L (those
 // entries are never part of the factor), so that block products see a lower
 // triangle.
@@ -195,6 +227,20 @@ cudaError_t trsm_right_upper_t(double *X, long long ldx, int R, const double *L,
         }
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_transpose(const double *X, long long ldx, int R, int C, double *Y, long long ldy, cudaStream_t s) {
+    if (R <= 0 || C <= 0) return cudaSuccess;
+    KScope ks(GEO_K_AUX, s);
+    k_transpose<<<dim3((R + 31) / 32, (C + 31) / 32), dim3(32, 8), 0, s>>>(X, ldx, R, C, Y, ldy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_col_sumsq(const double *Y, long long ldy, int N, int R, double *sums, cudaStream_t s) {
+    if (R <= 0) return cudaSuccess;
+    KScope ks(GEO_K_REDUCE, s, 2.0 * N * R, 8.0 * N * R);
+    k_col_sumsq<<<(R + 7) / 8, 256, 0, s>>>(Y, ldy, N, R, sums);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_var_finish(const double *sums, int R, int p, const double *c0diag, double *var, cudaStream_t s) {

@@ -1,5 +1,7 @@
 """Prediction (cokriging) variances on a kept factor against the oracle:
-diag(C(0) - c0' Sigma^-1 c0).  Bound: 1e-10 absolute + 1e-8 relative."""
+diag(C(0) - c0' Sigma^-1 c0).  Bound: 1e-10 absolute + 1e-8 relative for dense
+factors; 1e-9 absolute + 1e-7 relative for tile-low-rank factors at tile
+accuracy 1e-12."""
 import numpy as np
 import pytest
 
@@ -60,13 +62,27 @@ def test_predict_var_zero_at_observed_locations(ctx):
     assert np.all(np.abs(got) < 1e-9)
 
 
-def test_predict_var_unsupported_on_tile_low_rank(ctx):
-    th = geo.Theta((1.0, 1.0, 1.0), 0.1, (0.5, 1.0, 1.5), (0.5, 0.3, 0.4))
-    locs = inputs.jittered_grid(600, 91)
-    z = torch.zeros(1800, dtype=torch.float64, device="cuda")
-    _, fac = geo.geo_loglik(ctx, dev(locs), z, th, geo.opts(prec=2, nb=600, tlr_tol=1e-9, tlr_kmax=200), keep=True)
-    out = torch.empty(6, dtype=torch.float64, device="cuda")
-    with pytest.raises(geo.GeoError) as ei:
-        geo.geo_predict_var(ctx, fac, dev(inputs.jittered_grid(2, 92)), out)
-    assert ei.value.code == geo.GEO_EUNSUPPORTED
+@pytest.mark.parametrize("th,n,m,nb", [
+    (geo.Theta((1.0, 1.0, 1.0), 0.1, (0.5, 1.0, 1.5), (0.5, 0.3, 0.4)), 200, 15, 120),
+    (geo.Theta((1.0, 1.0), 0.09, (0.5, 1.0), 0.5), 384, 20, 128),
+])
+def test_predict_var_tile_low_rank_matches_oracle(ctx, th, n, m, nb):
+    # tile accuracy 1e-12: a CPU model (tiles truncated by exact SVD at that threshold, solved
+    # exactly) moves the variances by 2.4e-15 at the first case, well inside the bound
+    allp = inputs.jittered_grid(n + m, 93 + n)
+    locs, new = allp[:n], allp[n:]
+    got = _var(ctx, th, locs, new, geo.opts(prec=geo.GEO_PREC_TLR, nb=nb, tlr_tol=1e-12, tlr_kmax=nb))
+    ref = oracle.predict_var(o_theta(th), locs, new)
+    assert np.all(np.abs(got - ref) <= 1e-9 + 1e-7 * np.abs(ref)), np.max(np.abs(got - ref))
+    # prediction on the same kind of factor after the variances (the solve's arena is shared)
+    z = torch.as_tensor(inputs.normals(95, len(th.sigma2) * n), dtype=torch.float64, device="cuda")
+    _, fac = geo.geo_loglik(ctx, dev(locs), z, th, geo.opts(prec=geo.GEO_PREC_TLR, nb=nb, tlr_tol=1e-12,
+                                                            tlr_kmax=nb), keep=True)
+    out = torch.empty(len(th.sigma2) * m, dtype=torch.float64, device="cuda")
+    geo.geo_predict_var(ctx, fac, dev(new), out)
+    zhat = torch.empty_like(out)
+    geo.geo_predict(ctx, fac, dev(new), zhat)
     fac.free()
+    zref = oracle.predict(o_theta(th), locs, z.cpu().numpy(), new)
+    assert np.linalg.norm(zhat.cpu().numpy() - zref) <= 1e-7 * np.linalg.norm(zref)
+    assert np.all(np.abs(out.cpu().numpy() - ref) <= 1e-9 + 1e-7 * np.abs(ref))
