@@ -118,6 +118,33 @@ __global__ void __launch_bounds__(256) k_bgemm(const GemmDesc *__restrict__ d, i
     }
 }
 
+// The same strips on 32 x 32 (S = 2) or 16 x 16 (S = 1) output tiles: for
+// launches whose 64 x 64 tiles would leave most SMs idle (few output tiles,
+// long K, e.g. the r x r cores V_ik' V_jk with K = nb), 4x or 16x more CTAs
+// share the K loops' FP64 work.
+template <int S>
+__global__ void __launch_bounds__(256) k_bgemm_small(const GemmDesc *__restrict__ d, int count) {
+    __shared__ double As[BKK][BT + 2];
+    __shared__ double Bs[BKK][BT + 2];
+    const int pi = blockIdx.y;
+    if (pi >= count) return;
+    const GemmDesc g = d[pi];
+    constexpr int W = 16 * S;
+    const int tiles_m = (g.m + W - 1) / W;
+    const int tiles_n = (g.n + W - 1) / W;
+    if ((int)blockIdx.x >= tiles_m * tiles_n) return;
+    const int tm = (blockIdx.x % tiles_m) * W, tn = (blockIdx.x / tiles_m) * W;
+    const int im = min(S, (g.m - tm + 15) / 16), jm = min(S, (g.n - tn + 15) / 16);
+    if (S == 1 || (im == 1 && jm == 1))
+        bgemm_tile<1, 1>(g, tm, tn, As, Bs);
+    else if (im == 1)
+        bgemm_tile<1, S == 1 ? 1 : 2>(g, tm, tn, As, Bs);
+    else if (jm == 1)
+        bgemm_tile<S == 1 ? 1 : 2, 1>(g, tm, tn, As, Bs);
+    else
+        bgemm_tile<S == 1 ? 1 : 2, S == 1 ? 1 : 2>(g, tm, tn, As, Bs);
+}
+
 // ---- Householder QR of an m x r block (m >= r), in place -------------------
 // Column c: v = x - alpha e1 with alpha = -sign(x_0) |x|, stored below the
 // diagonal (v_0 kept in tau-scaled form), R on and above the diagonal; then
@@ -586,10 +613,28 @@ __global__ void k_gaussian(double *O, long long n, unsigned long long seed) {
 
 }  // namespace
 
+static int device_sms() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        n <= 0)
+        return 1;
+    return n;
+}
+
+// max_tiles: the largest number of 64 x 64 output tiles of one problem.  A
+// problem has at most 4x (16x) as many 32 x 32 (16 x 16) tiles; the surplus
+// CTAs of the smaller-tile grids return at once.
 cudaError_t launch_bgemm(const GemmDesc *d_desc, int count, int max_tiles, cudaStream_t s, double flops) {
     if (count <= 0 || max_tiles <= 0) return cudaSuccess;
     KScope ks(GEO_K_GEMM, s, flops, 0.0);
-    k_bgemm<<<dim3(max_tiles, count), 256, 0, s>>>(d_desc, count);
+    const long long ctas = (long long)max_tiles * count;
+    const long long sms = device_sms();
+    if (ctas >= sms)
+        k_bgemm<<<dim3(max_tiles, count), 256, 0, s>>>(d_desc, count);
+    else if (4 * ctas >= sms)
+        k_bgemm_small<2><<<dim3(4 * max_tiles, count), 256, 0, s>>>(d_desc, count);
+    else
+        k_bgemm_small<1><<<dim3(16 * max_tiles, count), 256, 0, s>>>(d_desc, count);
     return cudaGetLastError();
 }
 
