@@ -269,7 +269,8 @@ int geo_mle_step(geo_ctx *ctx, geo_mle_state *state, const double *locs_dev, int
                  const geo_opts *opts, void *stream);
 
 /* Best vertex as theta: sigma2[p], a, nu[p], beta[p*p] (host; beta may be NULL).  For a
-   profile run sigma2 is the sigma^2 estimate at the best vertex. */
+   profile run sigma2 is the sigma^2 estimate at the best vertex (NaN before the first
+   geo_mle_step); loglik is NaN before the first step. */
 int geo_mle_best(const geo_mle_state *state, double *sigma2, double *a, double *nu, double *beta,
                  double *loglik);
 

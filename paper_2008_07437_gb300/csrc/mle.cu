@@ -243,7 +243,7 @@ int geo_mle_best(const geo_mle_state *s, double *sigma2, double *a, double *nu, 
     ThetaBuf t;
     x_to_theta(s->x[0], s->p, s->profile != 0, &t);
     for (int i = 0; i < s->p; ++i) {
-        if (sigma2) sigma2[i] = s->profile ? s->s2[0][i] : t.sigma2[i];
+        if (sigma2) sigma2[i] = s->profile ? (s->initialized ? s->s2[0][i] : nan("")) : t.sigma2[i];
         if (nu) nu[i] = t.nu[i];
     }
     if (a) *a = t.th.a;

@@ -90,6 +90,23 @@ def test_mle_init_profile_simplex(lib):
     assert geo.geo_mle_init(th, 0.05).profile == 0
 
 
+def test_mle_init_rejects_bad_theta_and_best_before_steps(lib):
+    for bad in (geo.Theta((1.0, 1.0), -0.1, (0.5, 1.0), 0.5), geo.Theta((1.0, 1.0), 0.1, (0.0, 1.0), 0.5)):
+        for profile in (False, True):
+            with pytest.raises(geo.GeoError):
+                geo.geo_mle_init(bad, 0.1, profile=profile)
+    with pytest.raises(geo.GeoError):
+        geo.geo_mle_init(geo.Theta((-1.0, 1.0), 0.1, (0.5, 1.0), 0.5), 0.1)     # sigma^2 <= 0 (full run)
+    # the profile run does not read sigma^2
+    geo.geo_mle_init(geo.Theta((-1.0, 1.0), 0.1, (0.5, 1.0), 0.5), 0.1, profile=True)
+    th = geo.Theta((1.5, 2.5), 0.09, (0.5, 1.0), 0.4)
+    best, ll = geo.geo_mle_best(geo.geo_mle_init(th, 0.1))
+    assert np.isnan(ll) and best.sigma2 == pytest.approx((1.5, 2.5)) and best.a == pytest.approx(0.09)
+    best, ll = geo.geo_mle_best(geo.geo_mle_init(th, 0.1, profile=True))
+    assert np.isnan(ll) and all(np.isnan(best.sigma2))
+    assert best.nu == pytest.approx((0.5, 1.0)) and best.beta[0][1] == pytest.approx(0.4)
+
+
 def test_create_without_gpu_reports_error(lib):
     import torch
     if torch.cuda.is_available():
