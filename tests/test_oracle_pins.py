@@ -432,6 +432,93 @@ def test_mloe_mmom_zero_at_true_parameters():
     assert abs(mloe) < 1e-10 and abs(mmom) < 1e-10
 
 
+def test_mloe_mmom_one_observation_hand_computed():
+    # p = 1, nu = 1/2 (C(h) = sigma^2 e^(-h/a)), one observed location and one
+    # prediction location 0.1 apart.  S = sigma^2, c = C(h) and C(0) = sigma^2
+    # are scalars, so Eq. 5 - Eq. 7 are scalar algebra:
+    #   E_t = s_t - c_t^2 / s_t,  E_ta = s_t - 2 c_t c_a / s_a + c_a^2 s_t / s_a^2,
+    #   E_a = s_a - c_a^2 / s_a  (C(0; theta_a) = s_a: Algorithm 1's E_a).
+    # With s_t = 1, a_t = 0.1, s_a = 2, a_a = 0.2: c_t = e^-1, c_a = 2 e^-1/2, so
+    #   E_t = 1 - e^-2, E_ta = 1 - 2 e^-3/2 + e^-1, E_a = 2 - 2 e^-1.
+    th_t = oracle.Theta([1.0], 0.1, [0.5], np.eye(1))
+    th_a = oracle.Theta([2.0], 0.2, [0.5], np.eye(1))
+    locs = np.array([[0.3, 0.4]])
+    pred = np.array([[0.3, 0.5]])
+    Et = 1.0 - math.exp(-2.0)
+    Eta = 1.0 - 2.0 * math.exp(-1.5) + math.exp(-1.0)
+    Ea = 2.0 - 2.0 * math.exp(-1.0)
+    mloe, mmom, loe, mom = oracle.mloe_mmom(th_t, th_a, locs, pred)
+    assert loe[0] == pytest.approx(Eta / Et - 1.0, rel=1e-12)
+    assert mom[0] == pytest.approx(Ea / Eta - 1.0, rel=1e-12)
+    assert (mloe, mmom) == (loe[0], mom[0])
+    # the three energies are distinct here, so E_a with C(0; theta_t) (= 1 - 2 e^-1) would not pass
+    assert abs(Ea - (1.0 - 2.0 * math.exp(-1.0))) > 0.5 and abs(Ea - Eta) > 0.1 and abs(Eta - Et) > 0.01
+
+
+def _matern_half_integer(h, a, nu):
+    x = h / a
+    if nu == 0.5:
+        return math.exp(-x)
+    if nu == 1.5:
+        return (1.0 + x) * math.exp(-x)
+    if nu == 2.5:
+        return (1.0 + x + x * x / 3.0) * math.exp(-x)
+    raise ValueError(nu)
+
+
+def _block(theta_s2, a, nus, beta, h):
+    """2 x 2 Eq. 2 block at distance h from the half-integer closed forms, rho_12 = beta sqrt(nu1 nu2) / nu12."""
+    nu12 = 0.5 * (nus[0] + nus[1])
+    rho = beta * math.sqrt(nus[0] * nus[1]) / nu12
+    s1, s2 = math.sqrt(theta_s2[0]), math.sqrt(theta_s2[1])
+    c11 = theta_s2[0] * _matern_half_integer(h, a, nus[0])
+    c22 = theta_s2[1] * _matern_half_integer(h, a, nus[1])
+    c12 = rho * s1 * s2 * _matern_half_integer(h, a, nu12)
+    return np.array([[c11, c12], [c12, c22]])
+
+
+def test_mloe_mmom_bivariate_one_observation_closed_forms():
+    # p = 2 with nu = (1/2, 5/2), so nu_12 = 3/2: every entry of S (the colocated
+    # block), c and C(0) has a closed form; E_t, E_ta and E_a are 2 x 2 algebra.
+    nus = (0.5, 2.5)
+    tt = ((1.0, 1.5), 0.12, 0.6)   # (sigma^2, a, beta)
+    ta = ((0.7, 2.0), 0.2, -0.3)
+    h = 0.15
+    locs = np.array([[0.5, 0.5]])
+    pred = np.array([[0.5 + h, 0.5]])
+    St, Sa = _block(tt[0], tt[1], nus, tt[2], 0.0), _block(ta[0], ta[1], nus, ta[2], 0.0)
+    ct, ca = _block(tt[0], tt[1], nus, tt[2], h), _block(ta[0], ta[1], nus, ta[2], h)
+    Sai = np.linalg.inv(Sa)
+    Et = np.trace(St - ct.T @ np.linalg.inv(St) @ ct)
+    Eta = np.trace(St - 2.0 * ct.T @ Sai @ ca + ca.T @ Sai @ St @ Sai @ ca)
+    Ea = np.trace(Sa - ca.T @ Sai @ ca)
+    th_t = oracle.Theta(list(tt[0]), tt[1], list(nus), tt[2])
+    th_a = oracle.Theta(list(ta[0]), ta[1], list(nus), ta[2])
+    _, _, loe, mom = oracle.mloe_mmom(th_t, th_a, locs, pred)
+    assert loe[0] == pytest.approx(Eta / Et - 1.0, rel=1e-11)
+    assert mom[0] == pytest.approx(Ea / Eta - 1.0, rel=1e-11)
+    assert abs(Ea - np.trace(St - ca.T @ Sai @ ca)) > 0.1   # C(0; theta_t) in E_a would differ
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_mloe_mmom_variance_scale_only(p):
+    # theta_a = theta_t except every sigma^2 times c: Sigma_a = c Sigma_t, c_a = c c_t,
+    # so S_a^-1 c_a = S_t^-1 c_t, E_ta = E_t (LOE = 0) and E_a = c E_t (MOM = c - 1) exactly.
+    cfac = 1.7
+    if p == 1:
+        th_t = oracle.Theta([0.8], 0.09, [1.0], np.eye(1))
+        th_a = oracle.Theta([0.8 * cfac], 0.09, [1.0], np.eye(1))
+    else:
+        th_t = oracle.Theta([1.0, 1.3], 0.09, [0.5, 1.0], 0.5)
+        th_a = oracle.Theta([1.0 * cfac, 1.3 * cfac], 0.09, [0.5, 1.0], 0.5)
+    locs = inputs.jittered_grid(40, 7)
+    pred = inputs.jittered_grid(5, 123)
+    mloe, mmom, loe, mom = oracle.mloe_mmom(th_t, th_a, locs, pred)
+    np.testing.assert_allclose(loe, 0.0, atol=1e-10)
+    np.testing.assert_allclose(mom, cfac - 1.0, rtol=1e-10)
+    assert mmom == pytest.approx(cfac - 1.0, rel=1e-10)
+
+
 def test_mloe_nonnegative_for_misspecified():
     # E_ta >= E_t since the true-parameter cokriging predictor is the BLUP.
     th, locs = _small_problem(40)
