@@ -81,11 +81,19 @@ typedef struct {
     double tlr_tol;     /* TLR: absolute accuracy of each compressed tile (default 1e-9) */
     int tlr_kmax;       /* TLR: maximum tile rank (default 200) */
     int morton;         /* 1 = reorder locations by Morton (Z-order) key internally (default 1) */
-    int fp64_gemm;      /* FP64 trailing updates: 0 = native FP64 FMA (default) */
+    int fp64_gemm;      /* FP64 form, trailing updates (the SYRK / GEMM tasks of Sec. 5.1):
+                           0 = native FP64 FMA (default); 1 = emulated on the BF16 tensor cores
+                           (Ozaki scheme: each panel row split into oz_slices 7-bit integer digits
+                           with a power-of-two row scale, digit products accumulated exactly in
+                           FP32, recombined in 64-bit integers and FP64); POTRF, TRSM and every
+                           other step stay native FP64.  nb must be a multiple of 64 (default 512). */
     int dst;            /* TLR form: > 0 = Diagonal Super Tile (Sec. 3.4), keep the dst tile diagonals
                            nearest the diagonal (1 = diagonal tiles only) dense and zero the other
                            tiles (of the Morton-ordered matrix); 0 = off (default) */
-    int reserved[6];
+    int oz_slices;      /* fp64_gemm = 1: digits per operand, 3..8 (0 = 8).  An update then carries a
+                           relative error of about 2^(-7 oz_slices) of max|a_r| max|b_c| per product
+                           term (8 slices: below FP64's 2^-53 rounding; 5 slices: ~2^-35) */
+    int reserved[5];
 } geo_opts;
 
 typedef struct geo_ctx geo_ctx;
@@ -408,6 +416,25 @@ int geo_autotune_nb(geo_ctx *ctx, const double *locs_dev, int n, const double *z
                     void *stream);
 
 /*
+ * FP64-accurate matrix product on the tensor cores (the emulated trailing
+ * update of fp64_gemm = 1 as a standalone operation; the paper's GEMM tile task
+ * of Sec. 5.1 computes C -= A B' in FP64):
+ *   C -= A B',  A m x k, B n x k, C m x n, all column-major FP64 device memory
+ *   (caller-owned; lda >= m, ldb >= n, ldc >= m).
+ * Each row of A and of B is split into `slices` (3..8, 0 = 8) BF16 digits of 7
+ * bits under a power-of-two row scale; digit products are accumulated without
+ * rounding on the tensor cores in chunks of k <= 4096 / slices and recombined
+ * exactly in 64-bit integers, then added to C in FP64.  The error of each
+ * entry is at most about (k + 1) 2^(1 - 7 slices) max_i |A[r, i]| max_i |B[c, i]|
+ * (2^-53-class for 8 slices) plus the rounding of the FP64 additions to C.
+ * Uses a workspace of the context (S (m + n) k 2 bytes).  Synchronises `stream`.
+ * GEO_EINVAL for bad sizes or slices, GEO_ETIMEOUT if a bounded device wait
+ * expired.
+ */
+int geo_gemm_f64e(geo_ctx *ctx, int m, int n, int k, const double *A_dev, long long lda, const double *B_dev,
+                  long long ldb, double *C_dev, long long ldc, int slices, void *stream);
+
+/*
  * Device-time profile per kernel class, measured with CUDA events recorded
  * on the stream each kernel is launched on (no paper counterpart: the
  * paper's timing is wall-clock per phase, Sec. 6.1 / Sec. 6.3).
@@ -426,7 +453,8 @@ enum {
     GEO_K_SOLVE = 5,    /* backward substitution L' w = y */
     GEO_K_PREDICT = 6,  /* fused cross-covariance + GEMV of Eq. 3 */
     GEO_K_AUX = 7,      /* gathers, scatters, conversions */
-    GEO_K_TCGEMM = 8,   /* tensor-core (tcgen05) updates of far tiles, mixed precision */
+    GEO_K_TCGEMM = 8,   /* tensor-core (tcgen05) updates: far tiles of the mixed form, and every
+                           trailing update of the emulated FP64 form (flops counted as FP64 flops) */
     GEO_K_SGEMM = 9,    /* FP32 SIMT updates (mixed precision: diagonal and band tiles, panel) */
     GEO_K_TLR = 10,     /* TLR compression: Householder QR and Jacobi SVD of sketched tiles */
     GEO_K_COUNT = 11
@@ -457,8 +485,8 @@ int geo_server_profile_read(geo_server *server, geo_kstat *out);
  * loop that cannot afford cudaMalloc / cudaFree, which may synchronise the
  * device and may fail at unpredictable times.  This entry point allocates
  * nothing and needs no context: every intermediate (the covariance matrix and
- * its factor, the reordered locations, the K_nu tables of theta, the status
- * words) lives in one fixed-size array in device global memory owned by the
+ * its factor, the locations in SoA form in the caller's order, the K_nu tables
+ * of theta, the status words) lives in one fixed-size array in device global memory owned by the
  * library, about GEO_NOALLOC_SCRATCH_DOUBLES * 8 bytes (34 MB), which every
  * GPU that loads the library holds until the process exits.
  *
@@ -469,6 +497,9 @@ int geo_server_profile_read(geo_server *server, geo_kstat *out);
  *   out_dev   3 doubles (device, caller-owned): l(theta), log|Sigma|, Z' Sigma^-1 Z;
  *             l is NaN when Sigma is not positive definite
  *   info_dev  NULL or one int (device): 0, or the 1-based failing row
+ * Every buffer must be device memory of the current device (the call has no
+ * context of its own and does not switch devices); other pointers are refused
+ * with GEO_EINVAL before anything is enqueued.
  * The work is only enqueued on `stream`: synchronise it before reading the
  * outputs.  Returns GEO_ESCRATCH when p*n > GEO_NOALLOC_MAX_N (the scratch is
  * too small), GEO_EINVAL for other bad arguments, GEO_ECUDA if a launch or the
@@ -477,7 +508,9 @@ int geo_server_profile_read(geo_server *server, geo_kstat *out);
  * current); make that first call before any stream capture.  All calls share
  * the one array, which keeps the previous call's contents (the status words are
  * cleared at the start of each call): calls that overlap on the GPU race, so
- * serialise them (one stream, one thread).
+ * serialise them (one stream, one thread).  The address is cached for the
+ * life of the process: a call after cudaDeviceReset on that device is not
+ * supported.
  */
 #define GEO_NOALLOC_MAX_N 2048
 #define GEO_NOALLOC_SCRATCH_DOUBLES 4267778LL

@@ -41,7 +41,7 @@ class geo_opts(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int), ("prec", ctypes.c_int), ("band", ctypes.c_int), ("lowp", ctypes.c_int),
                 ("refine_iters", ctypes.c_int), ("tlr_tol", ctypes.c_double), ("tlr_kmax", ctypes.c_int),
                 ("morton", ctypes.c_int), ("fp64_gemm", ctypes.c_int), ("dst", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("oz_slices", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class geo_factor_stats(ctypes.Structure):
@@ -125,6 +125,7 @@ SIGNATURES = {
                            _P, _P]),
     "geo_loglik_noalloc": (_I, [_P, _I, _P, ctypes.POINTER(geo_theta), _I, _P, _P, _P]),
     "geo_loglik_batch": (_I, [_P, _I, _P, _P, _P, _P]),
+    "geo_gemm_f64e": (_I, [_P, _I, _I, _I, _P, _LL, _P, _LL, _P, _LL, _I, _P]),
     "geo_server_create": (_I, [ctypes.POINTER(_P), _I, ctypes.c_size_t, _I]),
     "geo_server_submit": (_I, [_P, _P, _P, ctypes.POINTER(_LL)]),
     "geo_server_poll": (_I, [_P, _P, _I, ctypes.POINTER(_I), _I]),
@@ -442,16 +443,73 @@ def geo_profile_read(ctx: Context) -> dict:
                                  bytes=arr[k].bytes, timed=arr[k].timed) for k in range(GEO_K_COUNT)}
 
 
+def _check_noalloc_args(locs, z, theta: Theta, out, info) -> int:
+    """Shapes, dtypes and placement of geo_loglik_noalloc's tensors (raises before anything runs)."""
+    import torch
+    p = len(theta.sigma2)
+    named = [("locs", locs, torch.float64), ("z", z, torch.float64), ("out", out, torch.float64)]
+    if info is not None:
+        named.append(("info", info, torch.int32))
+    for name, t, dt in named:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError("%s must be a torch tensor" % name)
+        if t.dtype != dt:
+            raise TypeError("%s must be %s" % (name, dt))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+    if locs.dim() != 2 or locs.shape[1] != 2:
+        raise ValueError("locs must be n x 2")
+    n = locs.shape[0]
+    if z.numel() != p * n:
+        raise ValueError("z must hold p * n = %d values" % (p * n))
+    if out.numel() < 3:
+        raise ValueError("out must hold 3 doubles")
+    if info is not None and info.numel() < 1:
+        raise ValueError("info must hold one int")
+    if len({t.device for _, t, _ in named}) != 1:
+        raise ValueError("locs, z, out and info must be on one device")
+    if not locs.is_cuda:
+        raise TypeError("geo_loglik_noalloc needs CUDA tensors")
+    return n
+
+
 def geo_loglik_noalloc(locs, z, theta: Theta, out, info=None, nb: int = 960, stream=None) -> int:
     """Eq. 1 without any device allocation (fixed library-owned scratch, p*n <= GEO_NOALLOC_MAX_N).
     ``out`` (3 doubles) and ``info`` (1 int32, optional) are device tensors written asynchronously on
-    the stream; returns the status code (GEO_OK, GEO_ESCRATCH, ...) without raising."""
+    the stream; returns the status code (GEO_OK, GEO_ESCRATCH, ...) without raising.  The tensors must
+    share one device; the call runs with that device current."""
     import torch
+    n = _check_noalloc_args(locs, z, theta, out, info)
     th, _keep = theta.to_c()
-    return load_library().geo_loglik_noalloc(
-        _dev_ptr(locs, "locs", torch.float64), locs.shape[0], _dev_ptr(z, "z", torch.float64), ctypes.byref(th),
-        int(nb), _dev_ptr(out, "out", torch.float64),
-        _dev_ptr(info, "info", torch.int32) if info is not None else None, _stream(stream))
+    with torch.cuda.device(locs.device):
+        return load_library().geo_loglik_noalloc(
+            ctypes.c_void_p(locs.data_ptr()), n, ctypes.c_void_p(z.data_ptr()), ctypes.byref(th), int(nb),
+            ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(info.data_ptr()) if info is not None else None,
+            _stream(stream))
+
+
+def geo_gemm_f64e(ctx: Context, A, B, C, slices: int = 0, stream=None):
+    """C -= A @ B.T on the tensor cores with FP64-class accuracy (``slices`` 7-bit digits per operand).
+    A (m x k), B (n x k), C (m x n): float64 CUDA tensors in column-major storage, i.e. the
+    transposes ``X.t()`` of contiguous row-major tensors are passed as ``X``."""
+    import torch
+    for name, t in (("A", A), ("B", B), ("C", C)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or t.dim() != 2:
+            raise TypeError("%s must be a 2-D float64 CUDA tensor" % name)
+        if t.stride(0) != 1 or t.stride(1) < max(1, t.shape[0]):
+            raise ValueError("%s must be column-major (stride(0) == 1)" % name)
+        if t.device != A.device:
+            raise ValueError("A, B and C must be on one device")
+    m, k = A.shape
+    n = B.shape[0]
+    if B.shape[1] != k or tuple(C.shape) != (m, n):
+        raise ValueError("shapes: A (m, k), B (n, k), C (m, n)")
+    with torch.cuda.device(A.device):
+        ctx.check(ctx.lib.geo_gemm_f64e(ctx.handle, m, n, k, ctypes.c_void_p(A.data_ptr()), max(1, A.stride(1)),
+                                        ctypes.c_void_p(B.data_ptr()), max(1, B.stride(1)),
+                                        ctypes.c_void_p(C.data_ptr()), max(1, C.stride(1)), int(slices),
+                                        _stream(stream)))
+    return C
 
 
 def geo_tlr_tile(factor: Factor, i: int, j: int, which: str = "U") -> np.ndarray:

@@ -38,6 +38,9 @@ struct geo_ctx {
     // workspace of the mixed-precision factorisation (panel copies)
     void *mws = nullptr;
     size_t mws_bytes = 0;
+    // digit slices of the tensor-core FP64 emulation (fp64_gemm = 1)
+    void *ows = nullptr;
+    size_t ows_bytes = 0;
     // iterative refinement: copy of Sigma, sorted Z, partial sums
     void *sws = nullptr, *zws = nullptr, *rws = nullptr;
     size_t sws_bytes = 0, zws_bytes = 0, rws_bytes = 0;
@@ -192,12 +195,19 @@ int order_bucket(int N) {
     return b;
 }
 
-int resolve_nb(int device, int prec, int N) {
+// Form key of the tuned-tile cache: the precision mode, or FORM_F64E for the
+// FP64 form with tensor-core emulated updates (a different best tile size).
+constexpr int FORM_F64E = 16;
+int form_of(const geo_opts &o) { return (o.prec == GEO_PREC_FP64 && o.fp64_gemm == 1) ? FORM_F64E : o.prec; }
+
+int resolve_nb(int device, int form, int N) {
     std::lock_guard<std::mutex> lk(g_tuned_mu);
-    auto it = g_tuned_nb.find(std::make_tuple(device, prec, order_bucket(N)));
+    auto it = g_tuned_nb.find(std::make_tuple(device, form, order_bucket(N)));
     if (it != g_tuned_nb.end()) return it->second;
-    return prec == GEO_PREC_MIXED ? 1024 : 960;
+    return form == GEO_PREC_MIXED ? 1024 : form == FORM_F64E ? 512 : 960;
 }
+
+int oz_slices_of(const geo_opts &o) { return o.oz_slices > 0 ? o.oz_slices : 8; }
 
 // Grow a context-cached device buffer to at least `need` bytes.
 int ensure_buffer(geo_ctx *ctx, void **buf, size_t *have, size_t need, cudaStream_t s) {
@@ -419,6 +429,7 @@ int geo_destroy(geo_ctx *ctx) {
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
     if (ctx->ws) dev_free(ctx, ctx->ws, ctx->ws_bytes);
     if (ctx->mws) dev_free(ctx, ctx->mws, ctx->mws_bytes);
+    if (ctx->ows) dev_free(ctx, ctx->ows, ctx->ows_bytes);
     if (ctx->sws) dev_free(ctx, ctx->sws, ctx->sws_bytes);
     if (ctx->zws) dev_free(ctx, ctx->zws, ctx->zws_bytes);
     if (ctx->rws) dev_free(ctx, ctx->rws, ctx->rws_bytes);
@@ -467,6 +478,32 @@ int geo_covgen(geo_ctx *ctx, const double *locs1_dev, int n1, const double *locs
 }
 
 // Shared front half of loglik / simulate: order locations, generate Sigma.
+// Checks of the dense-form options shared by the entry points.
+static int check_dense_opts(geo_ctx *ctx, const geo_opts &o) {
+    if (o.fp64_gemm != 0 && o.fp64_gemm != 1) return fail(ctx, GEO_EINVAL, "fp64_gemm must be 0 or 1");
+    if (o.fp64_gemm == 1 && (o.oz_slices != 0 && (o.oz_slices < 3 || o.oz_slices > 8)))
+        return fail(ctx, GEO_EINVAL, "oz_slices must be 0 (default 8) or 3..8");
+    if (o.fp64_gemm == 1 && o.nb % 64 != 0) return fail(ctx, GEO_EINVAL, "fp64_gemm = 1 needs nb a multiple of 64");
+    return GEO_OK;
+}
+
+// Dense FP64 factorisation in the form the options select: native FP64 FMA
+// updates (chol64_factor) or tensor-core emulated ones (chol_oz_factor, with
+// the context's slice workspace grown as needed).
+static int dense_factor(geo_ctx *ctx, double *A, long long ld, int N, int nrows, const geo_opts &o, cudaStream_t s,
+                        cudaError_t *err) {
+    *err = cudaSuccess;
+    if (o.fp64_gemm != 1) {
+        *err = chol64_factor(A, ld, N, nrows, o.nb, ctx->st, s);
+        return GEO_OK;
+    }
+    const int S = oz_slices_of(o);
+    int rc = ensure_buffer(ctx, &ctx->ows, &ctx->ows_bytes, oz_chol_workspace_bytes(nrows, o.nb, S), s);
+    if (rc) return rc;
+    *err = chol_oz_factor(A, ld, N, nrows, o.nb, S, ctx->ows, ctx->ows_bytes, ctx->st, s);
+    return GEO_OK;
+}
+
 static int prepare_matrix(geo_ctx *ctx, const double *locs_dev, int n, const geo_theta *theta,
                           const geo_opts *o, int extra_rows, geo_factor *f, cudaStream_t s, bool with_matrix = true) {
     std::string err;
@@ -672,8 +709,9 @@ int geo_loglik(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev,
     else
         geo_opts_default(&o);
     if (n <= 0 || !locs_dev || !z_dev) return fail(ctx, GEO_EINVAL, "n must be > 0 and pointers non-NULL");
-    if (o.nb == 0 && theta) o.nb = resolve_nb(ctx->device, o.prec, theta->p * n);
+    if (o.nb == 0 && theta) o.nb = resolve_nb(ctx->device, form_of(o), theta->p * n);
     if (o.nb < 64) return fail(ctx, GEO_EINVAL, "nb must be >= 64");
+    if (int rc0 = check_dense_opts(ctx, o)) return rc0;
     if (o.prec != GEO_PREC_FP64 && o.prec != GEO_PREC_MIXED && o.prec != GEO_PREC_TLR)
         return fail(ctx, GEO_EUNSUPPORTED, "precision mode not built");
     if (o.prec == GEO_PREC_MIXED && (o.nb % 128 != 0 || o.band < 0))
@@ -723,7 +761,16 @@ int geo_loglik(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev,
             f->w = (double *)pw;
         }
     }
+    if (!mixed && o.fp64_gemm == 1 &&
+        (rc = ensure_buffer(ctx, &ctx->ows, &ctx->ows_bytes, oz_chol_workspace_bytes(N + 1, o.nb, oz_slices_of(o)),
+                            s))) {
+        dev_free(ctx, d_perm, sizeof(int) * n);
+        release_factor_buffers(ctx, f, true);
+        delete f;
+        return rc;
+    }
     double *Scopy = (double *)ctx->sws, *zsorted = (double *)ctx->zws;
+    cudaError_t e_fac = cudaSuccess;
     if ((e = cudaMemcpyAsync(d_perm, f->perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s)) ||
         (e = launch_gather_vec(z_dev, d_perm, n, f->p, f->A + N, f->ld, s)) ||
         (refine && (e = launch_gather_vec(z_dev, d_perm, n, f->p, zsorted, 1, s))) ||
@@ -731,7 +778,7 @@ int geo_loglik(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev,
                                         cudaMemcpyDeviceToDevice, s))) ||
         (e = mixed ? chol_mixed_factor(f->A, f->ld, N, N + 1, o.nb, o.band, o.lowp, ctx->mws, ctx->mws_bytes,
                                        ctx->st, s)
-                   : chol64_factor(f->A, f->ld, N, N + 1, o.nb, ctx->st, s)) ||
+                   : (dense_factor(ctx, f->A, f->ld, N, N + 1, o, s, &e_fac), e_fac)) ||
         (e = refine ? refine_solve(Scopy, f->A, f->ld, N, zsorted, f->A + N, f->ld, o.refine_iters, f->w, ctx->rws,
                                    ctx->st, ctx->res, s)
                     : launch_loglik_reduce(f->A, f->ld, N, f->A + N, f->ld, ctx->st, ctx->res, s)) ||
@@ -913,6 +960,9 @@ int geo_simulate(geo_ctx *ctx, const double *locs_dev, int n, const double *e_de
     else
         geo_opts_default(&o);
     if (n <= 0 || !locs_dev || !e_dev || !z_dev) return fail(ctx, GEO_EINVAL, "bad arguments");
+    if (o.nb == 0 && theta) o.nb = resolve_nb(ctx->device, form_of(o), theta->p * n);
+    if (o.nb < 64) return fail(ctx, GEO_EINVAL, "nb must be >= 64");
+    if (int rc0 = check_dense_opts(ctx, o)) return rc0;
     SetDevice sd(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     geo_factor f;
@@ -944,8 +994,15 @@ int geo_simulate(geo_ctx *ctx, const double *locs_dev, int n, const double *e_de
         release_factor_buffers(ctx, &f, true);
         return rc ? rc : fail(ctx, GEO_EINVAL, "mixed precision needs nb a multiple of 128");
     }
+    cudaError_t e_fac = cudaSuccess;
+    if (!mixed && (rc = dense_factor(ctx, f.A, f.ld, N, N, o, s, &e_fac))) {
+        dev_free(ctx, zs, sizeof(double) * N);
+        dev_free(ctx, d_perm, sizeof(int) * n);
+        release_factor_buffers(ctx, &f, true);
+        return rc;
+    }
     if ((e = mixed ? chol_mixed_factor(f.A, f.ld, N, N, o.nb, o.band, o.lowp, ctx->mws, ctx->mws_bytes, ctx->st, s)
-                   : chol64_factor(f.A, f.ld, N, N, o.nb, ctx->st, s)) ||
+                   : e_fac) ||
         (e = launch_trmv_lower(f.A, f.ld, N, e_dev, zs, s)) ||
         (e = cudaMemcpyAsync(d_perm, f.perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s)) ||
         (e = launch_scatter_vec(zs, 1, d_perm, n, f.p, z_dev, s)) ||
@@ -1196,8 +1253,9 @@ int geo_mloe_mmom(geo_ctx *ctx, const double *locs_dev, int n, const double *pre
         geo_opts_default(&o);
     o.prec = GEO_PREC_FP64;
     const int p = theta_t->p, N = p * n, pm = p * m;
-    if (o.nb == 0) o.nb = resolve_nb(ctx->device, GEO_PREC_FP64, N);
+    if (o.nb == 0) o.nb = resolve_nb(ctx->device, form_of(o), N);
     if (o.nb < 64) return fail(ctx, GEO_EINVAL, "nb must be >= 64");
+    if (int rc0 = check_dense_opts(ctx, o)) return rc0;
     SetDevice sd(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     geo_factor *ft = new geo_factor(), *fa = new geo_factor();
@@ -1232,13 +1290,17 @@ int geo_mloe_mmom(geo_ctx *ctx, const double *locs_dev, int n, const double *pre
         return done(fail(ctx, GEO_ENOMEM, "pinned descriptor buffer"));
     }
     double *sum_t = (double *)psum, *sum_a = sum_t + pm, *cross = sum_a + pm, *sum_v = cross + pm;
-    cudaError_t e;
+    cudaError_t e, e_ft = cudaSuccess, e_fa = cudaSuccess;
+    if (o.fp64_gemm == 1 &&
+        (rc = ensure_buffer(ctx, &ctx->ows, &ctx->ows_bytes,
+                            oz_chol_workspace_bytes(N + 2 * pm, o.nb, oz_slices_of(o)), s)))
+        return done(rc);
     if ((e = launch_covgen_cross(ft->cp, pred_dev, m, ft->lx, ft->ly, n, ft->A + N, ft->ld, s)) ||
         (e = launch_covgen_cross(fa->cp, pred_dev, m, fa->lx, fa->ly, n, fa->A + N, fa->ld, s)) ||
         (e = launch_covgen_cross(ft->cp, pred_dev, m, fa->lx, fa->ly, n, fa->A + N + pm, fa->ld, s)) ||
         // factorisations: the rows below become (L^-1 c)'
-        (e = chol64_factor(ft->A, ft->ld, N, N + pm, o.nb, ctx->st, s)) ||
-        (e = chol64_factor(fa->A, fa->ld, N, N + 2 * pm, o.nb, ctx->st, s)) ||
+        (dense_factor(ctx, ft->A, ft->ld, N, N + pm, o, s, &e_ft), e = e_ft) ||
+        (dense_factor(ctx, fa->A, fa->ld, N, N + 2 * pm, o, s, &e_fa), e = e_fa) ||
         // |L_t^-1 c_t|^2, |L_a^-1 c_a|^2, (L_a^-1 c_t) . (L_a^-1 c_a)
         (e = launch_row_sums(ft->A + N, ft->ld, nullptr, 0, pm, N, sum_t, nullptr, s)) ||
         (e = launch_row_sums(fa->A + N, fa->ld, fa->A + N + pm, fa->ld, pm, N, sum_a, cross, s)) ||
@@ -1323,10 +1385,32 @@ int geo_autotune_nb(geo_ctx *ctx, const double *locs_dev, int n, const double *z
     if (best < 0) return fail(ctx, GEO_EINVAL, "no valid tile-size candidate");
     {
         std::lock_guard<std::mutex> lk(g_tuned_mu);
-        g_tuned_nb[std::make_tuple(ctx->device, o.prec, order_bucket(theta->p * n))] = best;
+        g_tuned_nb[std::make_tuple(ctx->device, form_of(o), order_bucket(theta->p * n))] = best;
     }
     if (best_nb) *best_nb = best;
     if (best_ms) *best_ms = bms;
+    return GEO_OK;
+}
+
+int geo_gemm_f64e(geo_ctx *ctx, int m, int n, int k, const double *A_dev, long long lda, const double *B_dev,
+                  long long ldb, double *C_dev, long long ldc, int slices, void *stream) {
+    if (!ctx) return GEO_EINVAL;
+    ProfBind pb(&ctx->prof);
+    if (m < 0 || n < 0 || k < 0) return fail(ctx, GEO_EINVAL, "m, n, k must be >= 0");
+    if (m == 0 || n == 0 || k == 0) return GEO_OK;
+    if (!A_dev || !B_dev || !C_dev) return fail(ctx, GEO_EINVAL, "NULL operand");
+    if (lda < m || ldb < n || ldc < m) return fail(ctx, GEO_EINVAL, "leading dimension below the row count");
+    if (slices == 0) slices = 8;
+    if (slices < 3 || slices > 8) return fail(ctx, GEO_EINVAL, "slices must be 0 (default 8) or 3..8");
+    SetDevice sd(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ensure_buffer(ctx, &ctx->ows, &ctx->ows_bytes, oz_gemm_workspace_bytes(m, n, k, slices), s);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(ctx->st, 0, sizeof(DevStatus), s));
+    CK(oz_gemm(m, n, k, A_dev, lda, B_dev, ldb, C_dev, ldc, slices, ctx->ows, ctx->st, s));
+    CK(cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (ctx->h_st->timeout) return fail(ctx, GEO_ETIMEOUT, "a bounded device wait expired");
     return GEO_OK;
 }
 
@@ -1373,10 +1457,10 @@ size_t ctx_trim(geo_ctx *ctx, cudaStream_t s) {
     SetDevice sd(ctx->device);
     cudaStreamSynchronize(s);
     const size_t before = ctx->used;
-    void **bufs[] = {(void **)&ctx->ws, &ctx->mws, &ctx->sws, &ctx->zws, &ctx->rws, &ctx->tws, &ctx->bws};
+    void **bufs[] = {(void **)&ctx->ws, &ctx->mws, &ctx->sws, &ctx->zws, &ctx->rws, &ctx->tws, &ctx->bws, &ctx->ows};
     size_t *sizes[] = {&ctx->ws_bytes, &ctx->mws_bytes, &ctx->sws_bytes, &ctx->zws_bytes,
-                       &ctx->rws_bytes, &ctx->tws_bytes, &ctx->bws_bytes};
-    for (int k = 0; k < 7; ++k) {
+                       &ctx->rws_bytes, &ctx->tws_bytes, &ctx->bws_bytes, &ctx->ows_bytes};
+    for (int k = 0; k < 8; ++k) {
         dev_free(ctx, *bufs[k], *sizes[k]);
         *bufs[k] = nullptr;
         *sizes[k] = 0;
@@ -1394,7 +1478,7 @@ size_t loglik_device_bytes(int device, int n, int p, const geo_opts *opts) {
     else
         geo_opts_default(&o);
     const size_t N = (size_t)p * n;
-    if (o.nb == 0) o.nb = resolve_nb(device, o.prec, (int)N);
+    if (o.nb == 0) o.nb = resolve_nb(device, form_of(o), (int)N);
     const size_t nb = (size_t)std::max(o.nb, 64);
     size_t b = sizeof(double) * (2 * (size_t)n + GEO_TAB_DOUBLES) + sizeof(int) * 2 * n + sizeof(double) * N;
     if (o.prec == GEO_PREC_TLR) {
@@ -1407,6 +1491,7 @@ size_t loglik_device_bytes(int device, int n, int p, const geo_opts *opts) {
     }
     const size_t ld = (size_t)round_up((long long)N + 1, 32);
     b += sizeof(double) * ld * N;
+    if (o.prec == GEO_PREC_FP64 && o.fp64_gemm == 1) b += oz_chol_workspace_bytes((int)N + 1, (int)nb, oz_slices_of(o));
     if (o.prec == GEO_PREC_MIXED) {
         b += mixed_workspace_bytes((int)N, (int)nb);
         if (o.refine_iters > 0) b += sizeof(double) * ld * N + sizeof(double) * N + refine_workspace_bytes((int)N);

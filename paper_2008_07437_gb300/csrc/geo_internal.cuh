@@ -106,6 +106,37 @@ cudaError_t chol_mixed_factor(double *A, long long ld, int N, int nrows, int nb,
                               size_t ws_bytes, DevStatus *st, cudaStream_t s);
 
 
+// ---- ozaki.cu -------------------------------------------------------------
+// FP64-accurate products on the BF16 tensor cores: the rows of an operand
+// as S BF16 digit slices with a power-of-two exponent per row and K chunk.
+struct OzSlices {
+    void *d;                  // S slices of rows x Kp BF16 digits (row-major, K contiguous)
+    int *e;                   // row exponents, nchunk x rows
+    int S, K, Kp, kchunk, nchunk;
+    long long rows;           // capacity: row stride of the exponent array
+    long long valid;          // rows holding data (extent of the tensor maps)
+    long long slice_stride;   // elements between slices
+};
+// Depth of one exact-accumulation launch: S * kmax * 2^12 <= 2^24.
+int oz_kmax(int S);
+size_t oz_slices_bytes(long long rows, int K, int S);
+OzSlices oz_slices_carve(void *ws, long long rows, int K, int S);
+// Slices of rows [0, R) of the column-major panel P (ld), columns [0, o.K).
+cudaError_t oz_slice(const double *P, long long ld, int R, const OzSlices &o, const DevStatus *st, cudaStream_t s);
+// C[r0 + i, c0 + j] -= sum_k A[a_off + i, k] B[b_off + j, k] for i < rows, j < cols, written only
+// where the global row < m_end and col < n_end (and row >= col when tri); grid_cap persistent CTAs.
+cudaError_t oz_update(const OzSlices &A, const OzSlices &B, double *C, long long ldc, int r0, int c0, int rows,
+                      int cols, int m_end, int n_end, int a_off, int b_off, int tri, int grid_cap, DevStatus *st,
+                      cudaStream_t s);
+size_t oz_chol_workspace_bytes(int nrows, int nb, int S);
+// Dense Cholesky as chol64_factor, trailing updates on the tensor cores with S slices.
+cudaError_t chol_oz_factor(double *A, long long ld, int N, int nrows, int nb, int S, void *ws, size_t ws_bytes,
+                           DevStatus *st, cudaStream_t s);
+size_t oz_gemm_workspace_bytes(int m, int n, int k, int S);
+// C (m x n) -= A (m x k) B (n x k)', column-major FP64, S slices.
+cudaError_t oz_gemm(int m, int n, int k, const double *A, long long lda, const double *B, long long ldb, double *C,
+                    long long ldc, int S, void *ws, DevStatus *st, cudaStream_t s);
+
 // ---- mloe.cu --------------------------------------------------------------
 // Rows = prediction locations (AoS s0, m), cols = observed locations (SoA, n):
 // out[(p r + j) * ld + (p q + i)] = C_ij(|s0_q - s_r|).
