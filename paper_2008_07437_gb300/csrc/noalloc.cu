@@ -14,7 +14,8 @@
 // doubles (about 34 MB), present on every GPU that loads the library until
 // the process exits.  It holds the matrix (order N = p*n <= GEO_NOALLOC_MAX_N,
 // leading dimension round_up(N + 1, 32), the extra row carrying Z / L^-1 Z),
-// the SoA locations, the K_nu tables of theta and the status words.  In host code the array's name is
+// the locations in SoA form (caller's order), the K_nu tables of theta and
+// the status words.  In host code the array's name is
 // only a host-side stand-in, so its device address is looked up once per
 // device with cudaGetSymbolAddress (with that device current) and cached;
 // that look-up happens during the first call on each device, which should
@@ -22,7 +23,9 @@
 // it keeps the last call's contents: the status words are cleared at the start
 // of each call, everything else is overwritten before it is read.  Calls whose
 // work overlaps on the GPU (other streams, other host threads) race on the
-// array and must be serialised by the caller.
+// array and must be serialised by the caller.  The cached address belongs to
+// the device's primary context as it was at the look-up: calling again after
+// cudaDeviceReset on that device is not supported.
 //
 // The entry point reuses the kernels of geo_loglik unchanged, in the caller's
 // location order (no Morton reordering: the ordering needs a host buffer, and
@@ -63,6 +66,18 @@ cudaError_t scratch_address(double **out) {
     return cudaSuccess;
 }
 
+// The call has no context that could switch devices: every buffer must be
+// device (or managed) memory of the current device.  A pointer of another GPU
+// or plain host memory is refused before anything is enqueued.
+bool on_device(const void *p, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+
 }  // namespace
 
 static_assert(kScratchDoubles == GEO_NOALLOC_SCRATCH_DOUBLES, "scratch size in geo.h out of date");
@@ -76,6 +91,14 @@ extern "C" int geo_loglik_noalloc(const double *locs_dev, int n, const double *z
     CovParams cp;
     std::string err;
     if (theta_to_params(theta, &cp, &err) != GEO_OK) return GEO_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return GEO_ECUDA;
+    }
+    if (!on_device(locs_dev, dev) || !on_device(z_dev, dev) || !on_device(out_dev, dev) ||
+        (info_dev && !on_device(info_dev, dev)))
+        return GEO_EINVAL;
     double *scratch = nullptr;
     if (scratch_address(&scratch) != cudaSuccess) {
         cudaGetLastError();

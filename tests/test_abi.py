@@ -113,3 +113,25 @@ def test_create_without_gpu_reports_error(lib):
         pytest.skip("a GPU is present")
     h = ctypes.c_void_p()
     assert lib.geo_create(ctypes.byref(h), 0, 0) == geo.GEO_ECUDA
+
+
+def test_noalloc_wrapper_checks_shapes_before_any_launch():
+    # the binding refuses mismatched buffers before it touches the library or a device
+    torch = pytest.importorskip("torch")
+    th = geo.Theta((1.0, 1.0), 0.09, (0.5, 1.0), 0.5)
+    locs = torch.zeros((10, 2), dtype=torch.float64)
+    z = torch.zeros(20, dtype=torch.float64)
+    out = torch.zeros(3, dtype=torch.float64)
+    info = torch.zeros(1, dtype=torch.int32)
+    with pytest.raises(ValueError, match="p \\* n"):
+        geo.geo_loglik_noalloc(locs, torch.zeros(19, dtype=torch.float64), th, out, info)
+    with pytest.raises(ValueError, match="n x 2"):
+        geo.geo_loglik_noalloc(torch.zeros((10, 3), dtype=torch.float64), z, th, out, info)
+    with pytest.raises(ValueError, match="3 doubles"):
+        geo.geo_loglik_noalloc(locs, z, th, torch.zeros(2, dtype=torch.float64), info)
+    with pytest.raises(ValueError, match="one int"):
+        geo.geo_loglik_noalloc(locs, z, th, out, torch.zeros(0, dtype=torch.int32))
+    with pytest.raises(TypeError):
+        geo.geo_loglik_noalloc(locs, z, th, out, torch.zeros(1, dtype=torch.int64))
+    with pytest.raises(TypeError, match="CUDA"):
+        geo.geo_loglik_noalloc(locs, z, th, out, info)

@@ -8,8 +8,14 @@ smaller one, so leftovers of the first call in the shared scratch must not
 leak into the second -- and checks each result against geo_loglik within the
 FP64 tolerance of the other parity tests (1e-10 relative on l, log|Sigma| and
 the quadratic form).  It also checks that the second call leaves the device's
-free memory unchanged and that oversized problems are refused.
+free memory unchanged, that oversized problems are refused, that a Sigma that
+is not positive definite gives NaN outputs and a failing row while the next
+good call reports info = 0 again (the status words live in the shared scratch
+and are cleared per call), and that buffers which are not device memory of
+the current device are refused before anything runs.
 This file is named to be collected last."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -81,3 +87,36 @@ def test_noalloc_rejects_problems_beyond_the_scratch(ctx):
     assert geo.geo_loglik_noalloc(locs, z, th, out, nb=256) == geo.GEO_OK
     torch.cuda.synchronize()
     np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=RTOL)
+
+
+def test_noalloc_not_positive_definite_then_recovers(ctx):
+    th = geo.Theta((1.0, 1.0), 0.09, (0.5, 1.0), 0.5)
+    base = inputs.jittered_grid(200, 21)
+    dup = np.concatenate([base, base[:1]])          # a repeated location: Sigma is singular
+    locs = torch.as_tensor(dup, device="cuda")
+    z = torch.as_tensor(inputs.normals(22, 2 * 201), device="cuda")
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert geo.geo_loglik_noalloc(locs, z, th, out, info, nb=128) == geo.GEO_OK
+    torch.cuda.synchronize()
+    assert np.all(np.isnan(out.cpu().numpy()))
+    assert int(info.cpu()[0]) > 0
+    locs2, z2 = _case(200, th, 23)
+    ref = _reference(ctx, locs2, z2, th, 128)
+    assert geo.geo_loglik_noalloc(locs2, z2, th, out, info, nb=128) == geo.GEO_OK
+    torch.cuda.synchronize()
+    assert int(info.cpu()[0]) == 0
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=RTOL)
+
+
+def test_noalloc_refuses_host_buffers(ctx):
+    # a host pointer in place of a device buffer is refused by the C entry point itself
+    th = geo.Theta((1.0, 1.0), 0.09, (0.5, 1.0), 0.5)
+    locs, z = _case(50, th, 31)
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    host_z = np.asarray(inputs.normals(32, 100), dtype=np.float64)
+    thc, _keep = th.to_c()
+    lib = geo.load_library()
+    rc = lib.geo_loglik_noalloc(ctypes.c_void_p(locs.data_ptr()), 50, host_z.ctypes.data_as(ctypes.c_void_p),
+                                ctypes.byref(thc), 128, ctypes.c_void_p(out.data_ptr()), None, None)
+    assert rc == geo.GEO_EINVAL
