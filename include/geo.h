@@ -85,8 +85,11 @@ typedef struct {
                            0 = native FP64 FMA (default); 1 = emulated on the BF16 tensor cores
                            (Ozaki scheme: each panel row split into oz_slices 7-bit integer digits
                            with a power-of-two row scale, digit products accumulated exactly in
-                           FP32, recombined in 64-bit integers and FP64); POTRF, TRSM and every
-                           other step stay native FP64.  nb must be a multiple of 64 (default 512). */
+                           FP32, recombined in 64-bit integers and FP64).  The rows below each
+                           diagonal tile are solved the same way, as the product with the inverse
+                           of the diagonal tile; POTRF and the inversion of the diagonal tiles, the
+                           last panel and every other step stay native FP64.  nb must be a
+                           multiple of 64 and at most 1024 (default 512). */
     int dst;            /* TLR form: > 0 = Diagonal Super Tile (Sec. 3.4), keep the dst tile diagonals
                            nearest the diagonal (1 = diagonal tiles only) dense and zero the other
                            tiles (of the Morton-ordered matrix); 0 = off (default) */
@@ -433,6 +436,23 @@ int geo_autotune_nb(geo_ctx *ctx, const double *locs_dev, int n, const double *z
  */
 int geo_gemm_f64e(geo_ctx *ctx, int m, int n, int k, const double *A_dev, long long lda, const double *B_dev,
                   long long ldb, double *C_dev, long long ldc, int slices, void *stream);
+
+/*
+ * Self-test of the bounded device waits (no paper counterpart; failure
+ * handling).  Every spin-wait of the library's kernels on another block's
+ * progress is bounded: when its clock budget runs out the kernel records the
+ * wait site in the context's status word, raises an abort word so that the
+ * other waiters give up too, and returns, leaving the context usable.  This
+ * entry point makes that happen on purpose: it runs the one-launch forward
+ * triangular solve on an identity factor of order 64 n_blocks with the first
+ * block withheld (the ticket counter starts past it, so the completion the
+ * second block waits for is never published) and a wait budget of
+ * wait_cycles clock cycles (1 .. 4e9).  Returns GEO_ETIMEOUT with *site = 3
+ * (the forward solve's wait) when the waits gave up as designed, GEO_OK if no
+ * wait expired (which would mean the dependency was not withheld).  The
+ * context's status words are cleared afterwards.  Synchronises `stream`.
+ */
+int geo_selftest_bounded_wait(geo_ctx *ctx, int n_blocks, long long wait_cycles, int *site, void *stream);
 
 /*
  * Device-time profile per kernel class, measured with CUDA events recorded

@@ -126,6 +126,7 @@ SIGNATURES = {
     "geo_loglik_noalloc": (_I, [_P, _I, _P, ctypes.POINTER(geo_theta), _I, _P, _P, _P]),
     "geo_loglik_batch": (_I, [_P, _I, _P, _P, _P, _P]),
     "geo_gemm_f64e": (_I, [_P, _I, _I, _I, _P, _LL, _P, _LL, _P, _LL, _I, _P]),
+    "geo_selftest_bounded_wait": (_I, [_P, _I, _LL, ctypes.POINTER(_I), _P]),
     "geo_server_create": (_I, [ctypes.POINTER(_P), _I, ctypes.c_size_t, _I]),
     "geo_server_submit": (_I, [_P, _P, _P, ctypes.POINTER(_LL)]),
     "geo_server_poll": (_I, [_P, _P, _I, ctypes.POINTER(_I), _I]),
@@ -510,6 +511,15 @@ def geo_gemm_f64e(ctx: Context, A, B, C, slices: int = 0, stream=None):
                                         ctypes.c_void_p(C.data_ptr()), max(1, C.stride(1)), int(slices),
                                         _stream(stream)))
     return C
+
+
+def geo_selftest_bounded_wait(ctx: Context, n_blocks: int = 8, wait_cycles: int = 2_000_000, stream=None):
+    """Run the forward solve with a withheld dependency and a short wait budget.
+    Returns (status code, wait site); GEO_ETIMEOUT with site 3 is the expected outcome."""
+    site = ctypes.c_int()
+    rc = ctx.lib.geo_selftest_bounded_wait(ctx.handle, int(n_blocks), int(wait_cycles), ctypes.byref(site),
+                                           _stream(stream))
+    return rc, site.value
 
 
 def geo_tlr_tile(factor: Factor, i: int, j: int, which: str = "U") -> np.ndarray:

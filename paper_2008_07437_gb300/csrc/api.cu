@@ -483,7 +483,8 @@ static int check_dense_opts(geo_ctx *ctx, const geo_opts &o) {
     if (o.fp64_gemm != 0 && o.fp64_gemm != 1) return fail(ctx, GEO_EINVAL, "fp64_gemm must be 0 or 1");
     if (o.fp64_gemm == 1 && (o.oz_slices != 0 && (o.oz_slices < 3 || o.oz_slices > 8)))
         return fail(ctx, GEO_EINVAL, "oz_slices must be 0 (default 8) or 3..8");
-    if (o.fp64_gemm == 1 && o.nb % 64 != 0) return fail(ctx, GEO_EINVAL, "fp64_gemm = 1 needs nb a multiple of 64");
+    if (o.fp64_gemm == 1 && (o.nb % 64 != 0 || o.nb > 1024))
+        return fail(ctx, GEO_EINVAL, "fp64_gemm = 1 needs nb a multiple of 64, at most 1024");
     return GEO_OK;
 }
 
@@ -1411,6 +1412,50 @@ int geo_gemm_f64e(geo_ctx *ctx, int m, int n, int k, const double *A_dev, long l
     CK(cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (ctx->h_st->timeout) return fail(ctx, GEO_ETIMEOUT, "a bounded device wait expired");
+    return GEO_OK;
+}
+
+namespace {
+__global__ void k_identity(double *A, int N) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < (long long)N * N) A[t] = (t % N == t / N) ? 1.0 : 0.0;
+}
+}  // namespace
+
+int geo_selftest_bounded_wait(geo_ctx *ctx, int n_blocks, long long wait_cycles, int *site, void *stream) {
+    if (!ctx) return GEO_EINVAL;
+    if (site) *site = 0;
+    if (n_blocks < 2 || n_blocks > 64 || wait_cycles <= 0 || wait_cycles > 4000000000LL)
+        return fail(ctx, GEO_EINVAL, "n_blocks must be in 2..64 and wait_cycles in 1..4e9");
+    SetDevice sd(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int N = 64 * n_blocks;
+    void *p = nullptr;
+    int rc = dev_alloc(ctx, &p, sizeof(double) * ((size_t)N * N + N));
+    if (rc) return rc;
+    double *A = (double *)p, *x = A + (size_t)N * N;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(ctx->st, 0, sizeof(DevStatus), s)) ||
+        (e = cudaMemsetAsync(x, 0, sizeof(double) * N, s))) {
+        dev_free(ctx, p, sizeof(double) * ((size_t)N * N + N));
+        return cuda_fail(ctx, e, "geo_selftest_bounded_wait");
+    }
+    k_identity<<<(unsigned)(((long long)N * N + 255) / 256), 256, 0, s>>>(A, N);
+    if ((e = cudaGetLastError()) ||
+        (e = forward_solve_withheld(A, N, N, x, ctx->sync, &ctx->st->timeout, wait_cycles, s)) ||
+        (e = cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s))) {
+        cudaStreamSynchronize(s);
+        dev_free(ctx, p, sizeof(double) * ((size_t)N * N + N));
+        return cuda_fail(ctx, e, "geo_selftest_bounded_wait");
+    }
+    dev_free(ctx, p, sizeof(double) * ((size_t)N * N + N));
+    const int code = ctx->h_st->timeout;
+    if (site) *site = code;
+    if (cudaMemsetAsync(ctx->st, 0, sizeof(DevStatus), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        return cuda_fail(ctx, cudaGetLastError(), "geo_selftest_bounded_wait");
+    if (code) return fail(ctx, GEO_ETIMEOUT, "the withheld dependency made the bounded wait give up (site " +
+                                                 std::to_string(code) + ")");
     return GEO_OK;
 }
 

@@ -125,11 +125,13 @@ OzSlices oz_slices_carve(void *ws, long long rows, int K, int S);
 cudaError_t oz_slice(const double *P, long long ld, int R, const OzSlices &o, const DevStatus *st, cudaStream_t s);
 // C[r0 + i, c0 + j] -= sum_k A[a_off + i, k] B[b_off + j, k] for i < rows, j < cols, written only
 // where the global row < m_end and col < n_end (and row >= col when tri); grid_cap persistent CTAs.
+// overwrite = 1: C = -sum (C is not read).
 cudaError_t oz_update(const OzSlices &A, const OzSlices &B, double *C, long long ldc, int r0, int c0, int rows,
                       int cols, int m_end, int n_end, int a_off, int b_off, int tri, int grid_cap, DevStatus *st,
-                      cudaStream_t s);
+                      cudaStream_t s, int overwrite);
 size_t oz_chol_workspace_bytes(int nrows, int nb, int S);
-// Dense Cholesky as chol64_factor, trailing updates on the tensor cores with S slices.
+// Dense Cholesky as chol64_factor, trailing updates and panel solves on the
+// tensor cores with S slices (nb <= 1024).
 cudaError_t chol_oz_factor(double *A, long long ld, int N, int nrows, int nb, int S, void *ws, size_t ws_bytes,
                            DevStatus *st, cudaStream_t s);
 size_t oz_gemm_workspace_bytes(int m, int n, int k, int S);
@@ -182,6 +184,11 @@ cudaError_t launch_loglik_reduce(const double *A, long long ld, int N, const dou
 // x <- L^-1 x.
 cudaError_t forward_solve(const double *A, long long ld, int N, double *x, int *sync, int *timeout_word,
                           cudaStream_t s);
+// Forward solve with block 0 withheld (a dependency nothing satisfies) and a
+// wait budget of wait_limit cycles: the bounded waits give up, record code 3
+// in *timeout_word and the launch returns (self-test of the waits).
+cudaError_t forward_solve_withheld(const double *A, long long ld, int N, double *x, int *sync, int *timeout_word,
+                                   long long wait_limit, cudaStream_t s);
 // w = L^-T y (y strided; w may be y's storage when ystride == 1).
 cudaError_t backward_solve(const double *A, long long ld, int N, const double *y, long long ystride, double *w,
                            int *sync, int *timeout_word, cudaStream_t s);

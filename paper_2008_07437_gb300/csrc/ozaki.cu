@@ -23,20 +23,27 @@
 //               partial sum in the FP32 tensor-memory accumulator is an
 //               integer below 2^24, so the tensor cores add without rounding
 //               (the depth of one launch is capped at kmax = 4096 / S);
-//   recombine   the epilogue converts each level to an integer and folds the
-//               levels 2..5 and 6..S+1 into two 64-bit integers (exact), then
-//               applies C -= 2^(e_r + e_c) (H 2^(2 - 7 h) + L 2^(2 - 7(S+1)))
-//               with two FP64 FMAs.
+//   recombine   the epilogue converts each level to an integer and folds
+//               groups of four levels (2..5, 6..9) into 64-bit integers
+//               (exact: below 2^46), then applies
+//               C -= 2^(e_r + e_c) sum_w W_w 2^(2 - 7 hi_w), hi_w the last
+//               level of group w, with one FP64 FMA per group.
 //
-// The kernel is persistent (one CTA per SM) over 128 x 64 output tiles:
-//   warp 0, one lane: TMA producer, ring of K chunks of 32 (64-byte rows,
-//     64-byte swizzle), each chunk holding the S digit slices of the A rows
-//     (128 x 32 BF16 each) and of the B rows (64 x 32 each);
-//   warp 1: allocates the 512 TMEM columns (S <= 8 accumulators of 64
-//     columns), one lane issues tcgen05.mma kind::f16 (M 128, N 64, K 16)
-//     level by level and commits chunks back to the producer;
+// The kernel is persistent (one CTA per SM) over 128 x BN output tiles, the
+// K range in chunks of BK.  TMEM (512 columns) holds 512 / BN level
+// accumulators of 128 x BN FP32: with BN = 64 all eight levels of 8 slices
+// fit and a tile is one pass over K; with BN = 128 (used from 6 slices on,
+// where the 128-row A operand read per 128 x 64 MMA otherwise keeps the MMA
+// issue path twice as busy as the math) the level groups run as passes over
+// K, each loading only the slices its levels use and writing its part of C.
+//   warp 0, one lane: TMA producer, ring of K chunks (32 or 64-byte rows,
+//     swizzled to match), each chunk holding the digit slices of the A rows
+//     (128 x BK BF16 each) and of the B rows (BN x BK each);
+//   warp 1: allocates the 512 TMEM columns; one lane issues tcgen05.mma
+//     kind::f16 (M 128, N BN, K 16) level by level from precomputed shared
+//     memory descriptors and commits chunks back to the producer;
 //   warps 2-9: epilogue; tcgen05.ld of each level, fold into registers,
-//     release TMEM (the next tile's MMAs start), then the FP64
+//     release TMEM (the next pass or tile starts its MMAs), then the FP64
 //     read-modify-write of C.
 // Every mbarrier wait is bounded; on expiry the thread records a code in the
 // status word, the CTA drains what it has in flight, frees TMEM and returns.
@@ -52,21 +59,41 @@ namespace {
 
 using namespace tc;
 
-constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 32;
+constexpr int OZ_BM = 128;        // output rows per tile (MMA M, TMEM lanes)
+constexpr int OZ_KALIGN = 32;     // slice arrays: K padded to a multiple of 32 (64-byte rows)
 constexpr int OZ_EPI_WARPS = 8;
 constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;
 constexpr int OZ_TMEM_COLS = 512;
-constexpr int OZ_A_BYTES = OZ_BM * OZ_BK * 2;
-constexpr int OZ_B_BYTES = OZ_BN * OZ_BK * 2;
 constexpr int OZ_SMEM_CAP = 225 * 1024;
-constexpr int OZ_GROUP = 8;   // row blocks swept together (operand reuse in L2)
+constexpr int OZ_GROUP = 8;       // row blocks swept together (operand reuse in L2)
+constexpr int OZ_LPW = 4;         // levels folded into one 64-bit word
 
-template <int S>
+// Tile width BN (MMA N), K chunk BK (16: 32-byte rows, 32-byte swizzle; 32:
+// 64-byte rows, 64-byte swizzle).  TMEM holds 512 / BN level accumulators, so
+// the S levels are processed in passes of WPP words over the whole K range;
+// each pass loads only the slices its levels use.
+template <int S, int BN, int BK>
 struct OzCfg {
-    static constexpr int STAGE_BYTES = S * (OZ_A_BYTES + OZ_B_BYTES);
-    static constexpr int STAGES = (OZ_SMEM_CAP / STAGE_BYTES) < 4 ? (OZ_SMEM_CAP / STAGE_BYTES) : 4;
+    static constexpr int NWT = (S + OZ_LPW - 1) / OZ_LPW;            // words of <= 4 levels (levels 2 .. S+1)
+    static constexpr int WPP = OZ_TMEM_COLS / (BN * OZ_LPW);          // words per pass
+    static constexpr int PASSES = (NWT + WPP - 1) / WPP;
+    static constexpr int WREG = WPP < NWT ? WPP : NWT;                // words an epilogue thread holds
+    static constexpr int A_BYTES = OZ_BM * BK * 2;
+    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int STAGE_BYTES = S * (A_BYTES + B_BYTES);      // the widest pass uses every slice
+    static constexpr int STAGES = (OZ_SMEM_CAP / STAGE_BYTES) < 6 ? (OZ_SMEM_CAP / STAGE_BYTES) : 6;
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
-    static constexpr int HEND = (S + 1) < 5 ? (S + 1) : 5;   // last level folded into the high word
+    static constexpr int CPT = BN / 2;                                // columns per epilogue thread
+    // levels of pass g: [lev_lo, lev_hi]; slices it reads: 1 .. tmax
+    __host__ __device__ static constexpr int lev_lo(int g) { return 2 + OZ_LPW * WPP * g; }
+    __host__ __device__ static constexpr int lev_hi(int g) {
+        return (1 + OZ_LPW * WPP * (g + 1)) < (S + 1) ? (1 + OZ_LPW * WPP * (g + 1)) : (S + 1);
+    }
+    __host__ __device__ static constexpr int tmax(int g) { return (lev_hi(g) - 1) < S ? (lev_hi(g) - 1) : S; }
+    // last level of word w (its unit is 2^(2 - 7 hi))
+    __host__ __device__ static constexpr int word_hi(int w) {
+        return (5 + OZ_LPW * w) < (S + 1) ? (5 + OZ_LPW * w) : (S + 1);
+    }
 };
 
 struct OzArgs {
@@ -74,14 +101,16 @@ struct OzArgs {
     long long ldc;
     int r0, c0;          // global row / col of the region's first output
     int m_end, n_end;    // outputs with global row >= m_end or col >= n_end are not written
-    int mt, nt;          // 128-row x 64-col tiles of the region
+    int mt, nt;          // 128-row x BN-col tiles of the region
     int tri;             // write only global row >= global col; skip tiles entirely above the diagonal
+    int overwrite;       // 1: C = -A B' (C is not read)
     int a_off, b_off;    // slice row of the region's first row (A) / first column (B)
-    int nk;              // K chunks of 32
+    int nk;              // K chunks of BK
     const int *ea, *eb;  // per-row exponents of the A / B slices
     DevStatus *st;
 };
 
+template <int BN>
 __device__ __forceinline__ bool oz_tile(const OzArgs &a, long long L, int *gr, int *gc, int *ar, int *br) {
     const long long per_band = (long long)OZ_GROUP * a.nt;
     const long long band = L / per_band;
@@ -90,9 +119,9 @@ __device__ __forceinline__ bool oz_tile(const OzArgs &a, long long L, int *gr, i
     const long long w = L - band * per_band;
     const int j = (int)(w / gm), i = i0 + (int)(w % gm);
     *gr = a.r0 + i * OZ_BM;
-    *gc = a.c0 + j * OZ_BN;
+    *gc = a.c0 + j * BN;
     *ar = a.a_off + i * OZ_BM;
-    *br = a.b_off + j * OZ_BN;
+    *br = a.b_off + j * BN;
     return !(a.tri && *gr + OZ_BM - 1 < *gc);
 }
 
@@ -104,13 +133,30 @@ __device__ __forceinline__ double pow2i(int e) {
     return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
-template <int S>
+template <int BK>
+__device__ __forceinline__ uint64_t oz_desc(uint32_t saddr) {
+    if constexpr (BK == 16) {
+        uint64_t d = 0;   // SWIZZLE_32B: 8 rows x 32 bytes = 256-byte groups
+        d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+        d |= (uint64_t)1 << 16;
+        d |= (uint64_t)(256 >> 4) << 32;
+        d |= (uint64_t)1 << 46;
+        d |= (uint64_t)6 << 61;
+        return d;
+    } else {
+        return smem_desc_sw64(saddr);
+    }
+}
+
+template <int S, int BN, int BK>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 const OzArgs args) {
-    constexpr int ST = OzCfg<S>::STAGES;
-    constexpr int STAGE_BYTES = OzCfg<S>::STAGE_BYTES;
-    constexpr int HEND = OzCfg<S>::HEND;
+    using Cfg = OzCfg<S, BN, BK>;
+    constexpr int ST = Cfg::STAGES;
+    constexpr int STAGE_BYTES = Cfg::STAGE_BYTES;
+    constexpr int A_BYTES = Cfg::A_BYTES, B_BYTES = Cfg::B_BYTES;
+    constexpr int PASSES = Cfg::PASSES, CPT = Cfg::CPT, WREG = Cfg::WREG;
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[ST], empty_bar[ST], acc_full, acc_empty, drain_bar;
     __shared__ uint32_t tmem_slot;
@@ -153,19 +199,22 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             bool ok = true;
             for (long long L = blockIdx.x; L < ntiles && ok; L += gridDim.x) {
                 int gr, gc, ar, br;
-                if (!oz_tile(args, L, &gr, &gc, &ar, &br)) continue;
-                for (int kb = 0; kb < args.nk; ++kb, ++g) {
-                    const int s = (int)(g % ST);
-                    if (g >= ST && !mbar_wait(&empty_bar[s], (uint32_t)(((g / ST) & 1) ^ 1), tword, 21)) {
-                        ok = false;
-                        break;
-                    }
-                    uint8_t *base = smem + (size_t)s * STAGE_BYTES;
-                    mbar_arrive_expect_tx(&full_bar[s], STAGE_BYTES);
+                if (!oz_tile<BN>(args, L, &gr, &gc, &ar, &br)) continue;
 #pragma unroll
-                    for (int t = 0; t < S; ++t) {
-                        tma_load_3d(&mapA, &full_bar[s], base + t * OZ_A_BYTES, kb * OZ_BK, ar, t);
-                        tma_load_3d(&mapB, &full_bar[s], base + S * OZ_A_BYTES + t * OZ_B_BYTES, kb * OZ_BK, br, t);
+                for (int ps = 0; ps < PASSES; ++ps) {
+                    const int tm = Cfg::tmax(ps);
+                    for (int kb = 0; kb < args.nk && ok; ++kb, ++g) {
+                        const int s = (int)(g % ST);
+                        if (g >= ST && !mbar_wait(&empty_bar[s], (uint32_t)(((g / ST) & 1) ^ 1), tword, 21)) {
+                            ok = false;
+                            break;
+                        }
+                        uint8_t *base = smem + (size_t)s * STAGE_BYTES;
+                        mbar_arrive_expect_tx(&full_bar[s], (uint32_t)(tm * (A_BYTES + B_BYTES)));
+                        for (int t = 0; t < tm; ++t) {
+                            tma_load_3d(&mapA, &full_bar[s], base + t * A_BYTES, kb * BK, ar, t);
+                            tma_load_3d(&mapB, &full_bar[s], base + S * A_BYTES + t * B_BYTES, kb * BK, br, t);
+                        }
                     }
                 }
             }
@@ -176,47 +225,54 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = instr_desc_f16(1, OZ_BM, OZ_BN);
+            const uint32_t idesc = instr_desc_f16(1, OZ_BM, BN);
             long long g = 0;
-            int lt = 0;   // tiles of this CTA
+            int job = 0;   // (tile, pass) jobs of this CTA
             bool ok = true;
             for (long long L = blockIdx.x; L < ntiles && ok; L += gridDim.x) {
                 int gr, gc, ar, br;
-                if (!oz_tile(args, L, &gr, &gc, &ar, &br)) continue;
-                if (lt >= 1 && !mbar_wait(&acc_empty, (uint32_t)((lt - 1) & 1), tword, 25)) {
-                    ok = false;
-                    break;
-                }
-                fence_after_sync();
-                for (int kb = 0; kb < args.nk; ++kb, ++g) {
-                    const int s = (int)(g % ST);
-                    if (!mbar_wait(&full_bar[s], (uint32_t)((g / ST) & 1), tword, 23)) {
+                if (!oz_tile<BN>(args, L, &gr, &gc, &ar, &br)) continue;
+#pragma unroll
+                for (int ps = 0; ps < PASSES; ++ps) {
+                    if (!ok) break;
+                    if (job >= 1 && !mbar_wait(&acc_empty, (uint32_t)((job - 1) & 1), tword, 25)) {
                         ok = false;
                         break;
                     }
                     fence_after_sync();
-                    const uint32_t a0 = smem_u32(smem + (size_t)s * STAGE_BYTES);
-                    const uint32_t b0 = a0 + S * OZ_A_BYTES;
+                    const int llo = Cfg::lev_lo(ps), lhi = Cfg::lev_hi(ps);
+                    for (int kb = 0; kb < args.nk; ++kb, ++g) {
+                        const int s = (int)(g % ST);
+                        if (!mbar_wait(&full_bar[s], (uint32_t)((g / ST) & 1), tword, 23)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after_sync();
+                        const uint32_t a0 = smem_u32(smem + (size_t)s * STAGE_BYTES);
+                        const uint64_t da0 = oz_desc<BK>(a0), db0 = oz_desc<BK>(a0 + S * A_BYTES);
 #pragma unroll
-                    for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+                        for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
-                        for (int l = 2; l <= S + 1; ++l) {
-                            const int tlo = (l - S > 1) ? l - S : 1, thi = (l - 1 < S) ? l - 1 : S;
+                            for (int l = 2; l <= S + 1; ++l) {
+                                if (l < llo || l > lhi) continue;
+                                const int tlo = (l - S > 1) ? l - S : 1, thi = (l - 1 < S) ? l - 1 : S;
 #pragma unroll
-                            for (int t = tlo; t <= thi; ++t) {
-                                const int u = l - t;
-                                const uint32_t acc = tmem + (uint32_t)((l - 2) * OZ_BN);
-                                mma_f16(acc, smem_desc_sw64(a0 + (t - 1) * OZ_A_BYTES + kk * 32),
-                                        smem_desc_sw64(b0 + (u - 1) * OZ_B_BYTES + kk * 32), idesc,
-                                        (kb != 0 || kk != 0 || t != tlo) ? 1u : 0u);
+                                for (int t = tlo; t <= thi; ++t) {
+                                    const int u = l - t;
+                                    const uint32_t acc = tmem + (uint32_t)((l - llo) * BN);
+                                    // start-address field += offset / 16 (no carry: smem addresses < 2^18)
+                                    mma_f16(acc, da0 + (uint64_t)(((t - 1) * A_BYTES + kk * 32) >> 4),
+                                            db0 + (uint64_t)(((u - 1) * B_BYTES + kk * 32) >> 4), idesc,
+                                            (kb != 0 || kk != 0 || t != tlo) ? 1u : 0u);
+                                }
                             }
                         }
+                        mma_commit(&empty_bar[s]);
                     }
-                    mma_commit(&empty_bar[s]);
+                    if (!ok) break;
+                    mma_commit(&acc_full);
+                    ++job;
                 }
-                if (!ok) break;
-                mma_commit(&acc_full);
-                ++lt;
             }
             // every MMA issued so far has completed before TMEM can be freed
             mma_commit(&drain_bar);
@@ -227,51 +283,61 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         // epilogue: warps 2..9; TMEM lane quarter q = warp % 4 (tile rows 32q..), column half h
         const int q = warp % 4, h = (warp - 2) / 4;
         const int row = q * 32 + lane;
-        int lt = 0;
-        for (long long L = blockIdx.x; L < ntiles; L += gridDim.x) {
+        int job = 0;
+        bool ok = true;
+        for (long long L = blockIdx.x; L < ntiles && ok; L += gridDim.x) {
             int gr, gc, ar, br;
-            if (!oz_tile(args, L, &gr, &gc, &ar, &br)) continue;
-            bool ok = mbar_wait(&acc_full, (uint32_t)(lt & 1), tword, 24);
-            ok = __all_sync(0xffffffffu, ok);   // every lane takes part in tcgen05.ld
-            if (!ok) break;
-            fence_after_sync();
-            long long hw[32], lw[32];
-#pragma unroll
-            for (int l = 2; l <= S + 1; ++l) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((l - 2) * OZ_BN + h * 32), v);
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const long long d = (long long)__float2int_rn(v[j]);   // an exact integer below 2^24
-                    if (l == 2)
-                        hw[j] = d;
-                    else if (l <= HEND)
-                        hw[j] = hw[j] * 128 + d;
-                    else if (l == 6)
-                        lw[j] = d;
-                    else
-                        lw[j] = lw[j] * 128 + d;
-                }
-            }
-            fence_before_sync();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty);
+            if (!oz_tile<BN>(args, L, &gr, &gc, &ar, &br)) continue;
             const int grow = gr + row;
-            if (grow < args.m_end) {
-                const int er = args.ea[ar + row];
+            const int er = (grow < args.m_end) ? args.ea[ar + row] : 0;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int gcol = gc + h * 32 + j;
-                    if (gcol >= args.n_end || (args.tri && grow < gcol)) continue;
-                    const int e = er + args.eb[br + h * 32 + j];
-                    double *pc = args.C + (long long)gcol * args.ldc + grow;
-                    double c = *pc;
-                    if (S + 1 > 5) c = fma(-(double)lw[j], pow2i(e + 2 - 7 * (S + 1)), c);
-                    c = fma(-(double)hw[j], pow2i(e + 2 - 7 * HEND), c);
-                    *pc = c;
+            for (int ps = 0; ps < PASSES; ++ps) {
+                ok = mbar_wait(&acc_full, (uint32_t)(job & 1), tword, 24);
+                ok = __all_sync(0xffffffffu, ok);   // every lane takes part in tcgen05.ld
+                if (!ok) break;
+                fence_after_sync();
+                const int llo = Cfg::lev_lo(ps), lhi = Cfg::lev_hi(ps);
+                const int w0 = ps * Cfg::WPP;
+                long long acc[WREG][CPT];
+#pragma unroll
+                for (int l = 2; l <= S + 1; ++l) {
+                    if (l < llo || l > lhi) continue;
+                    const int wi = (l - 2) / OZ_LPW - w0;   // word of this level within the pass
+                    const bool first = ((l - 2) % OZ_LPW) == 0;
+#pragma unroll
+                    for (int c32 = 0; c32 < CPT / 32; ++c32) {
+                        float v[32];
+                        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((l - llo) * BN + h * CPT + c32 * 32),
+                                  v);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const long long d = (long long)__float2int_rn(v[j]);   // an exact integer below 2^24
+                            acc[wi][c32 * 32 + j] = first ? d : acc[wi][c32 * 32 + j] * 128 + d;
+                        }
+                    }
+                }
+                fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty);
+                ++job;
+                if (grow < args.m_end) {
+                    const bool over = args.overwrite && ps == 0;
+#pragma unroll
+                    for (int j = 0; j < CPT; ++j) {
+                        const int gcol = gc + h * CPT + j;
+                        if (gcol >= args.n_end || (args.tri && grow < gcol)) continue;
+                        const int e = er + args.eb[br + h * CPT + j];
+                        double *pc = args.C + (long long)gcol * args.ldc + grow;
+                        double c = over ? 0.0 : *pc;
+#pragma unroll
+                        for (int wi = WREG - 1; wi >= 0; --wi) {
+                            if (w0 + wi >= Cfg::NWT) continue;
+                            c = fma(-(double)acc[wi][j], pow2i(e + 2 - 7 * Cfg::word_hi(w0 + wi)), c);
+                        }
+                        *pc = c;
+                    }
                 }
             }
-            ++lt;
         }
     }
     fence_before_sync();
@@ -301,7 +367,7 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double *P, long long ld,
     if (skip) return;
     const int r0 = blockIdx.x * 32;
     const int kbeg = blockIdx.y * kchunk, kend = min(K, kbeg + kchunk);
-    const int kpad_end = min(Kp, kbeg + (kchunk + OZ_BK - 1) / OZ_BK * OZ_BK);
+    const int kpad_end = min(Kp, kbeg + (kchunk + OZ_KALIGN - 1) / OZ_KALIGN * OZ_KALIGN);
     const int rr = threadIdx.x % 32, g = threadIdx.x / 32;
     double mx = 0.0;
     if (r0 + rr < R)
@@ -342,38 +408,61 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double *P, long long ld,
     }
 }
 
-template <int S>
+template <int S, int BN, int BK>
 cudaError_t launch_oz_kernel(const CUtensorMap &ma, const CUtensorMap &mb, const OzArgs &a, int grid,
                              cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_oz_update<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)OzCfg<S>::SMEM);
+    using Cfg = OzCfg<S, BN, BK>;
+    static_assert(Cfg::STAGES >= 2, "shared memory holds fewer than two chunks");
+    cudaError_t e = cudaFuncSetAttribute(k_oz_update<S, BN, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Cfg::SMEM);
     if (e != cudaSuccess) return e;
-    k_oz_update<S><<<grid, OZ_THREADS, OzCfg<S>::SMEM, s>>>(ma, mb, a);
+    k_oz_update<S, BN, BK><<<grid, OZ_THREADS, Cfg::SMEM, s>>>(ma, mb, a);
     return cudaGetLastError();
 }
 
-// 3-D tensor map over the slices: (k, row, slice), box 32 x rows_box x 1, 64-byte swizzle.
-cudaError_t slice_map(CUtensorMap *map, const OzSlices &sl, int chunk, int rows_box) {
+// Kernel shape per slice count (measured on GB300 with C 8192 x 8192, K = 512):
+// with 6 or more slices the 128-column tile in passes of four levels keeps the
+// tensor pipe busiest (8 slices: 1,290 against 1,063 TFLOP/s of BF16 work for
+// the single-pass 64-column tile); with fewer the passes get short and the
+// 64-column single pass wins (5 slices: 902 against 655).
+struct OzShape {
+    int bn, bk;
+};
+
+OzShape oz_shape(int S) { return S >= 6 ? OzShape{128, 16} : OzShape{64, 32}; }
+
+template <int S>
+cudaError_t launch_oz_shape(OzShape sh, const CUtensorMap &ma, const CUtensorMap &mb, const OzArgs &a, int grid,
+                            cudaStream_t s) {
+    if constexpr (S >= 6)
+        return launch_oz_kernel<S, 128, 16>(ma, mb, a, grid, s);
+    else
+        return launch_oz_kernel<S, 64, 32>(ma, mb, a, grid, s);
+}
+
+// 3-D tensor map over the slices: (k, row, slice), box bk x rows_box x 1,
+// swizzle = the K chunk's row width (32 or 64 bytes).
+cudaError_t slice_map(CUtensorMap *map, const OzSlices &sl, int chunk, int rows_box, int bk) {
     tc::EncodeTiledFn enc = tc::encode_fn();
     if (!enc) return cudaErrorNotSupported;
     void *base = (__nv_bfloat16 *)sl.d + (size_t)chunk * sl.kchunk;   // 64-byte aligned: kchunk is a multiple of 32
     cuuint64_t dims[3] = {(cuuint64_t)std::min(sl.kchunk, sl.Kp - chunk * sl.kchunk), (cuuint64_t)sl.valid,
                           (cuuint64_t)sl.S};
     cuuint64_t strides[2] = {(cuuint64_t)sl.Kp * 2, (cuuint64_t)sl.slice_stride * 2};
-    cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)rows_box, 1};
+    cuuint32_t box[3] = {(cuuint32_t)bk, (cuuint32_t)rows_box, 1};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult cr = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
-                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, bk == 16 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return cr == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-int oz_kmax(int S) { return (4096 / S) / OZ_BK * OZ_BK; }
+int oz_kmax(int S) { return (4096 / S) / OZ_KALIGN * OZ_KALIGN; }
 
 size_t oz_slices_bytes(long long rows, int K, int S) {
-    const long long Kp = (K + OZ_BK - 1) / OZ_BK * OZ_BK;
+    const long long Kp = (K + OZ_KALIGN - 1) / OZ_KALIGN * OZ_KALIGN;
     const int nchunk = (K + oz_kmax(S) - 1) / oz_kmax(S);
     return (size_t)S * (size_t)rows * (size_t)Kp * 2 + sizeof(int) * (size_t)rows * nchunk + 512;
 }
@@ -384,7 +473,7 @@ OzSlices oz_slices_carve(void *ws, long long rows, int K, int S) {
     o.rows = rows;
     o.K = K;
     o.kchunk = oz_kmax(S);
-    o.Kp = (K + OZ_BK - 1) / OZ_BK * OZ_BK;
+    o.Kp = (K + OZ_KALIGN - 1) / OZ_KALIGN * OZ_KALIGN;
     o.nchunk = (K + o.kchunk - 1) / o.kchunk;
     o.valid = rows;
     o.slice_stride = (long long)rows * o.Kp;
@@ -406,7 +495,7 @@ cudaError_t oz_slice(const double *P, long long ld, int R, const OzSlices &o, co
 
 cudaError_t oz_update(const OzSlices &A, const OzSlices &B, double *C, long long ldc, int r0, int c0, int rows,
                       int cols, int m_end, int n_end, int a_off, int b_off, int tri, int grid_cap, DevStatus *st,
-                      cudaStream_t s) {
+                      cudaStream_t s, int overwrite) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     if (A.S != B.S || A.K != B.K || A.S < 3 || A.S > 8) return cudaErrorInvalidValue;
     const int S = A.S;
@@ -417,10 +506,12 @@ cudaError_t oz_update(const OzSlices &A, const OzSlices &B, double *C, long long
     a.c0 = c0;
     a.m_end = m_end;
     a.n_end = n_end;
+    const OzShape sh = oz_shape(S);
     a.mt = (rows + OZ_BM - 1) / OZ_BM;
-    a.nt = (cols + OZ_BN - 1) / OZ_BN;
+    a.nt = (cols + sh.bn - 1) / sh.bn;
     a.tri = tri;
     a.a_off = a_off;
+    a.overwrite = 0;
     a.b_off = b_off;
     a.st = st;
     const long long ntiles = (long long)a.mt * a.nt;
@@ -430,43 +521,126 @@ cudaError_t oz_update(const OzSlices &A, const OzSlices &B, double *C, long long
     const double outs = tri ? std::max(0.0, rr * cc - cc * (cc - 1.0) / 2.0) : rr * cc;
     for (int ch = 0; ch < A.nchunk; ++ch) {
         const int kc = std::min(A.kchunk, A.K - ch * A.kchunk);
-        a.nk = (kc + OZ_BK - 1) / OZ_BK;
+        a.nk = (kc + sh.bk - 1) / sh.bk;
         a.ea = A.e + (long long)ch * A.rows;
         a.eb = B.e + (long long)ch * B.rows;
         CUtensorMap ma, mb;
         cudaError_t e;
-        if ((e = slice_map(&ma, A, ch, OZ_BM)) != cudaSuccess || (e = slice_map(&mb, B, ch, OZ_BN)) != cudaSuccess)
+        if ((e = slice_map(&ma, A, ch, OZ_BM, sh.bk)) != cudaSuccess ||
+            (e = slice_map(&mb, B, ch, sh.bn, sh.bk)) != cudaSuccess)
             return e;
+        a.overwrite = (overwrite && ch == 0) ? 1 : 0;   // later K chunks accumulate onto the first
         KScope ks(GEO_K_TCGEMM, s, 2.0 * kc * outs, 16.0 * outs + 2.0 * S * kc * (rr + cc));
         switch (S) {
-            case 3: e = launch_oz_kernel<3>(ma, mb, a, grid, s); break;
-            case 4: e = launch_oz_kernel<4>(ma, mb, a, grid, s); break;
-            case 5: e = launch_oz_kernel<5>(ma, mb, a, grid, s); break;
-            case 6: e = launch_oz_kernel<6>(ma, mb, a, grid, s); break;
-            case 7: e = launch_oz_kernel<7>(ma, mb, a, grid, s); break;
-            default: e = launch_oz_kernel<8>(ma, mb, a, grid, s); break;
+            case 3: e = launch_oz_shape<3>(sh, ma, mb, a, grid, s); break;
+            case 4: e = launch_oz_shape<4>(sh, ma, mb, a, grid, s); break;
+            case 5: e = launch_oz_shape<5>(sh, ma, mb, a, grid, s); break;
+            case 6: e = launch_oz_shape<6>(sh, ma, mb, a, grid, s); break;
+            case 7: e = launch_oz_shape<7>(sh, ma, mb, a, grid, s); break;
+            default: e = launch_oz_shape<8>(sh, ma, mb, a, grid, s); break;
         }
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-size_t oz_chol_workspace_bytes(int nrows, int nb, int S) { return oz_slices_bytes((long long)nrows + 128, nb, S); }
+namespace {
 
-// Right-looking over panels of width nb with a lookahead of one (as the
-// mixed form): step j slices its panel (rows below the diagonal tile,
-// right-hand-side rows included), updates the next panel's tile column
-// first, factors that panel's diagonal tile (and solves its right-hand-side
-// rows) on a high-priority second stream while the rest of the trailing
-// update runs (its persistent launch leaves SIDE_SMS SMs free), and solves
-// the rows below the new diagonal tile in FP64 after the join.  POTRF and
-// TRSM stay native FP64; every trailing update is emulated.
+// W = -L^-1 for the lower-triangular jb x jb tile L (column-major, ld),
+// written column-major with leading dimension ldw (zeros above the diagonal).
+// Column-oriented forward substitution L w = e_c for the TRTRI_COLS columns of
+// a CTA: at step k the owner of row k divides by L_kk and publishes w_k, every
+// thread then updates its rows below with column k of L (read along the
+// column, coalesced).  The broadcast buffer is double-buffered, so one barrier
+// per step suffices.
+constexpr int TRTRI_COLS = 8, TRTRI_THREADS = 256, TRTRI_RPT = 4;   // rows per thread: jb <= 1024
+
+__global__ void __launch_bounds__(TRTRI_THREADS) k_trtri_neg(const double *__restrict__ L, long long ld, int jb,
+                                                          double *W, long long ldw, const DevStatus *st) {
+    __shared__ double wk[2][TRTRI_COLS];
+    __shared__ int skip;
+    if (threadIdx.x == 0) skip = *(volatile const int *)&st->info;
+    __syncthreads();
+    if (skip) return;
+    const int c0 = blockIdx.x * TRTRI_COLS;
+    const int ncol = min(TRTRI_COLS, jb - c0);
+    double w[TRTRI_RPT][TRTRI_COLS];
+#pragma unroll
+    for (int q = 0; q < TRTRI_RPT; ++q) {
+        const int r = threadIdx.x + q * TRTRI_THREADS;
+#pragma unroll
+        for (int c = 0; c < TRTRI_COLS; ++c) w[q][c] = (r == c0 + c) ? 1.0 : 0.0;
+    }
+    for (int k = c0; k < jb; ++k) {
+        const int owner_q = k / TRTRI_THREADS, owner_t = k % TRTRI_THREADS;
+        if (threadIdx.x == owner_t) {
+            const double inv = 1.0 / L[(long long)k * ld + k];
+#pragma unroll
+            for (int q = 0; q < TRTRI_RPT; ++q)
+                if (q == owner_q) {
+#pragma unroll
+                    for (int c = 0; c < TRTRI_COLS; ++c) {
+                        w[q][c] *= inv;
+                        wk[k & 1][c] = w[q][c];
+                    }
+                }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < TRTRI_RPT; ++q) {
+            const int r = threadIdx.x + q * TRTRI_THREADS;
+            if (r > k && r < jb) {
+                const double l = L[(long long)k * ld + r];
+#pragma unroll
+                for (int c = 0; c < TRTRI_COLS; ++c) w[q][c] = fma(-l, wk[k & 1][c], w[q][c]);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < TRTRI_RPT; ++q) {
+        const int r = threadIdx.x + q * TRTRI_THREADS;
+        if (r >= jb) continue;
+#pragma unroll
+        for (int c = 0; c < TRTRI_COLS; ++c)
+            if (c < ncol) W[(long long)(c0 + c) * ldw + r] = (r >= c0 + c) ? -w[q][c] : 0.0;
+    }
+}
+
+cudaError_t launch_trtri_neg(const double *L, long long ld, int jb, double *W, long long ldw, const DevStatus *st,
+                             cudaStream_t s) {
+    if (jb > TRTRI_THREADS * TRTRI_RPT) return cudaErrorInvalidValue;
+    KScope ks(GEO_K_TRSM, s, (double)jb * jb * jb / 3.0, 16.0 * jb * jb);
+    k_trtri_neg<<<(jb + TRTRI_COLS - 1) / TRTRI_COLS, TRTRI_THREADS, 0, s>>>(L, ld, jb, W, ldw, st);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t oz_chol_workspace_bytes(int nrows, int nb, int S) {
+    return oz_slices_bytes((long long)nrows + 128, nb, S) + oz_slices_bytes(nb, nb, S) + sizeof(double) * (size_t)nb * nb +
+           1024;
+}
+
+// Right-looking over panels of width nb with a lookahead of one (as the mixed
+// form).  Step j slices its solved panel (the rows below the diagonal tile,
+// right-hand-side rows included) and updates the next panel's tile column
+// first; on a high-priority second stream the next diagonal tile is factored
+// (native FP64 POTRF) and inverted, W = -L_kk^-1, while the rest of the
+// trailing update runs (its persistent launch leaves SIDE_SMS SMs free).
+// After the join the rows below the new diagonal tile are solved as one
+// emulated product, L_ik = A_ik L_kk^-T = -(A_ik W'), written over A_ik.
+// Every trailing update and panel solve is emulated; POTRF of the diagonal
+// tiles and their inversion are native FP64, and so is the last panel.
 cudaError_t chol_oz_factor(double *A, long long ld, int N, int nrows, int nb, int S, void *ws, size_t ws_bytes,
                            DevStatus *st, cudaStream_t s) {
     constexpr int SIDE_SMS = 8;
-    if (nb < 64 || nb % 64 != 0 || S < 3 || S > 8) return cudaErrorInvalidValue;
+    if (nb < 64 || nb % 64 != 0 || nb > TRTRI_THREADS * TRTRI_RPT || S < 3 || S > 8) return cudaErrorInvalidValue;
     if (ws_bytes < oz_chol_workspace_bytes(nrows, nb, S)) return cudaErrorInvalidValue;
     const OzSlices sl = oz_slices_carve(ws, (long long)nrows + 128, nb, S);
+    uintptr_t wp = ((uintptr_t)ws + oz_slices_bytes((long long)nrows + 128, nb, S) + 255) & ~(uintptr_t)255;
+    const OzSlices slw0 = oz_slices_carve((void *)wp, nb, nb, S);
+    wp = (wp + oz_slices_bytes(nb, nb, S) + 255) & ~(uintptr_t)255;
+    double *W = (double *)wp;   // nb x nb, ld nb
     int prio_lo = 0, prio_hi = 0;
     cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     cudaStream_t s2 = nullptr;
@@ -480,15 +654,37 @@ cudaError_t chol_oz_factor(double *A, long long ld, int N, int nrows, int nb, in
         return e;
     }
     const int all = tc::num_sms();
+    // rows [x0, x1) of panel [t0, t0 + jb) <- A L^-T with W = -L^-1 already in place
+    auto panel_solve = [&](int t0, int jb, int x0, int x1, cudaStream_t st_) -> cudaError_t {
+        if (x0 >= x1) return cudaSuccess;
+        OzSlices p = sl, q = slw0;
+        p.K = q.K = jb;
+        p.nchunk = q.nchunk = (jb + p.kchunk - 1) / p.kchunk;
+        p.valid = x1 - x0;
+        q.valid = jb;
+        cudaError_t r;
+        if ((r = oz_slice(A + (long long)t0 * ld + x0, ld, x1 - x0, p, st, st_)) != cudaSuccess ||
+            (r = oz_slice(W, nb, jb, q, st, st_)) != cudaSuccess)
+            return r;
+        return oz_update(p, q, A, ld, x0, t0, x1 - x0, jb, x1, t0 + jb, 0, 0, 0, all, st, st_, 1);
+    };
+    // native FP64 factorisation of the diagonal tile [t0, t0 + jb) and its inverse
+    auto diag = [&](int t0, int jb, cudaStream_t st_) -> cudaError_t {
+        cudaError_t r = chol64_panel(A, ld, t0, jb, t0 + jb, t0 + jb, st, st_);
+        if (r != cudaSuccess) return r;
+        return launch_trtri_neg(A + (long long)t0 * ld + t0, ld, jb, W, nb, st, st_);
+    };
     auto run = [&]() -> cudaError_t {
         cudaError_t r;
         const int jb0 = std::min(nb, N);
-        if ((r = chol64_panel(A, ld, 0, jb0, jb0, nrows, st, s)) != cudaSuccess) return r;
+        if (jb0 == N) return chol64_panel(A, ld, 0, N, N, nrows, st, s);   // one tile: native
+        if ((r = diag(0, jb0, s)) != cudaSuccess || (r = panel_solve(0, jb0, jb0, nrows, s)) != cudaSuccess)
+            return r;
         for (int j0 = 0;;) {
             const int jb = std::min(nb, N - j0);
             const int t0 = j0 + jb;
             if (t0 >= N) break;
-            // the panel's rows below the diagonal tile (right-hand-side rows included) as digit slices
+            // the solved panel's rows below the diagonal tile as digit slices
             OzSlices p = sl;
             p.K = jb;
             p.nchunk = (jb + p.kchunk - 1) / p.kchunk;
@@ -496,7 +692,7 @@ cudaError_t chol_oz_factor(double *A, long long ld, int N, int nrows, int nb, in
             if ((r = oz_slice(A + (long long)j0 * ld + t0, ld, nrows - t0, p, st, s)) != cudaSuccess) return r;
             const int n1 = std::min(N, t0 + nb);
             // the next panel's tile column: rows [t0, nrows), cols [t0, n1)
-            if ((r = oz_update(p, p, A, ld, t0, t0, nrows - t0, n1 - t0, nrows, n1, 0, 0, 1, all, st, s)) !=
+            if ((r = oz_update(p, p, A, ld, t0, t0, nrows - t0, n1 - t0, nrows, n1, 0, 0, 1, all, st, s, 0)) !=
                 cudaSuccess)
                 return r;
             if (n1 >= N) {
@@ -507,14 +703,14 @@ cudaError_t chol_oz_factor(double *A, long long ld, int N, int nrows, int nb, in
             }
             if ((r = cudaEventRecord(e_upd, s)) != cudaSuccess) return r;
             if ((r = cudaStreamWaitEvent(s2, e_upd, 0)) != cudaSuccess) return r;
-            if ((r = chol64_panel(A, ld, t0, n1 - t0, N, nrows, st, s2)) != cudaSuccess) return r;
+            if ((r = diag(t0, n1 - t0, s2)) != cudaSuccess) return r;
             if ((r = cudaEventRecord(e_pan, s2)) != cudaSuccess) return r;
             // the rest of the trailing update meanwhile: rows [n1, nrows), cols [n1, N)
             if ((r = oz_update(p, p, A, ld, n1, n1, nrows - n1, N - n1, nrows, N, n1 - t0, n1 - t0, 1,
-                               all - SIDE_SMS, st, s)) != cudaSuccess)
+                               all - SIDE_SMS, st, s, 0)) != cudaSuccess)
                 return r;
             if ((r = cudaStreamWaitEvent(s, e_pan, 0)) != cudaSuccess) return r;
-            if ((r = chol64_panel(A, ld, t0, n1 - t0, n1, N, st, s, false)) != cudaSuccess) return r;
+            if ((r = panel_solve(t0, n1 - t0, n1, nrows, s)) != cudaSuccess) return r;
             j0 = t0;
         }
         return cudaSuccess;
@@ -544,5 +740,5 @@ cudaError_t oz_gemm(int m, int n, int k, const double *A, long long lda, const d
     cudaError_t e;
     if ((e = oz_slice(A, lda, m, sa, st, s)) != cudaSuccess || (e = oz_slice(B, ldb, n, sb, st, s)) != cudaSuccess)
         return e;
-    return oz_update(sa, sb, C, ldc, 0, 0, m, n, m, n, 0, 0, 0, tc::num_sms(), st, s);
+    return oz_update(sa, sb, C, ldc, 0, 0, m, n, m, n, 0, 0, 0, tc::num_sms(), st, s, 0);
 }

@@ -35,14 +35,15 @@ __device__ __forceinline__ void st_release(int *p, int v) {
 }
 
 // Wait until done >= target.  Returns done, or -1 when the solve was aborted
-// (here or elsewhere).
-__device__ int wait_done(int *sync, int target, int *timeout_word, int code) {
+// (here or elsewhere).  limit: the wait's clock budget (0 = WAIT_CYCLES).
+__device__ int wait_done(int *sync, int target, int *timeout_word, int code, long long limit) {
     const long long t0 = clock64();
+    const long long budget = limit > 0 ? limit : WAIT_CYCLES;
     for (;;) {
         const int d = ld_acquire(&sync[1]);
         if (d >= target) return d;
         if (ld_acquire(&sync[2])) return -1;
-        if (clock64() - t0 > WAIT_CYCLES) {
+        if (clock64() - t0 > budget) {
             atomicExch(&sync[2], 1);
             if (timeout_word) atomicCAS(timeout_word, 0, code);
             return -1;
@@ -63,7 +64,7 @@ __device__ __forceinline__ void load_diag(const double *__restrict__ A, long lon
 }
 
 __global__ void __launch_bounds__(TT) k_trsv_fwd(const double *__restrict__ A, long long ld, int N, double *x,
-                                                 int *sync, int *timeout_word) {
+                                                 int *sync, int *timeout_word, long long wait_limit) {
     __shared__ double Ls[TB][TB + 1];
     __shared__ double dinv[TB];
     __shared__ double part[TT / TB][TB];
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(TT) k_trsv_fwd(const double *__restrict__ A, l
         for (int J = 0; J < I; ++J) {
             if (J >= seen) {   // warp-uniform
                 // every lane waits with its own acquire loads before it reads x
-                const int d = __reduce_min_sync(0xffffffffu, wait_done(sync, J + 1, timeout_word, 3));
+                const int d = __reduce_min_sync(0xffffffffu, wait_done(sync, J + 1, timeout_word, 3, wait_limit));
                 if (d < 0) {
                     aborted = true;
                     break;
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(TT) k_trsv_bwd(const double *__restrict__ A, l
             const int need = nblk - J;   // tickets 0 .. need-1 done
             if (need > seen) {   // warp-uniform
                 // every lane waits with its own acquire loads before it reads w
-                const int d = __reduce_min_sync(0xffffffffu, wait_done(sync, need, timeout_word, 4));
+                const int d = __reduce_min_sync(0xffffffffu, wait_done(sync, need, timeout_word, 4, 0));
                 if (d < 0) {
                     aborted = true;
                     break;
@@ -234,6 +235,9 @@ __global__ void k_copy_strided(const double *__restrict__ in, long long stride, 
     if (k < N) out[k] = in[(long long)k * stride];
 }
 
+// sync[0] = v (the ticket counter) before a launch
+__global__ void k_set_ticket(int *sync, int v) { sync[0] = v; }
+
 int solve_grid(int N) {
     const int nblk = (N + TB - 1) / TB;
     return nblk < 152 * 4 ? nblk : 152 * 4;
@@ -247,7 +251,22 @@ cudaError_t forward_solve(const double *A, long long ld, int N, double *x, int *
     cudaError_t e = cudaMemsetAsync(sync, 0, 4 * sizeof(int), s);
     if (e != cudaSuccess) return e;
     KScope ks(GEO_K_SOLVE, s, (double)N * N, 8.0 * (double)N * N / 2.0);
-    k_trsv_fwd<<<solve_grid(N), TT, 0, s>>>(A, ld, N, x, sync, timeout_word);
+    k_trsv_fwd<<<solve_grid(N), TT, 0, s>>>(A, ld, N, x, sync, timeout_word, 0);
+    return cudaGetLastError();
+}
+
+// The forward solve with its first block withheld: the ticket counter starts
+// at 1, so no CTA ever solves block 0 and publishes it, and the CTA of block 1
+// waits for a completion that never comes.  With a wait budget of
+// wait_limit cycles that wait gives up, raises the abort word (every other
+// waiter returns too), records code 3 in *timeout_word and the launch ends.
+cudaError_t forward_solve_withheld(const double *A, long long ld, int N, double *x, int *sync, int *timeout_word,
+                                   long long wait_limit, cudaStream_t s) {
+    if (N <= TB || wait_limit <= 0) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(sync, 0, 4 * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_set_ticket<<<1, 1, 0, s>>>(sync, 1);
+    k_trsv_fwd<<<solve_grid(N), TT, 0, s>>>(A, ld, N, x, sync, timeout_word, wait_limit);
     return cudaGetLastError();
 }
 
