@@ -66,7 +66,7 @@ def test_server_mixed_requests_match_oracle(built):
             locs, Z, new, th = data[k]
             assert res[rid]["status"] == geo.GEO_OK
             ref = oracle.predict(o_theta(th), locs, Z, new)
-            assert np.linalg.norm(buf - ref) <= 1e-8 * np.linalg.norm(ref)
+            assert np.all(np.abs(buf - ref) <= 1e-8 * (np.abs(ref).max() + np.abs(ref)))
             assert res[rid]["t_end"] >= res[rid]["t_start"] >= res[rid]["t_submit"]
     finally:
         srv.close()
@@ -90,6 +90,42 @@ def test_server_result_same_alone_and_in_the_mix(built):
             srv.submit_loglik(l2, z2, t2, geo.opts(nb=128))
         res = _collect(srv, 6)
         assert res[rid]["loglik"] == alone   # bitwise
+        _assert_some_overlap(res)
+    finally:
+        srv.close()
+
+
+def _assert_some_overlap(res):
+    """At least two requests ran at the same time: their [t_start, t_end] intersect."""
+    spans = sorted((r["t_start"], r["t_end"]) for r in res.values())
+    assert any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1)), spans
+
+
+def test_server_emulated_reduced_form_same_alone_and_in_the_mix(built):
+    # the served reduced form: tensor-core updates with 5 digit slices; the
+    # result of a request does not depend on what runs beside it
+    opt = geo.opts(nb=128, fp64_gemm=1, oz_slices=5)
+    locs, Z, new, th = _dataset(700, 20, 9)
+    srv = geo.Server(0, 0, slots=1)
+    try:
+        rid = srv.submit_loglik(locs, Z, th, opt)
+        alone = _collect(srv, 1)[rid]["loglik"]
+    finally:
+        srv.close()
+    ref = oracle.loglik(o_theta(th), locs, Z).loglik
+    assert abs(alone - ref) <= 1e-8 * abs(ref)
+    srv = geo.Server(0, 0, slots=4)
+    try:
+        others = [_dataset(n, 10, 40 + k) for k, n in enumerate([900, 400, 800, 650, 1000])]
+        for l2, z2, _, t2 in others[:3]:
+            srv.submit_loglik(l2, z2, t2, opt)
+        rid = srv.submit_loglik(locs, Z, th, opt)
+        for l2, z2, _, t2 in others[3:]:
+            srv.submit_loglik(l2, z2, t2, opt)
+        res = _collect(srv, 6)
+        assert all(r["status"] == geo.GEO_OK for r in res.values())
+        assert res[rid]["loglik"] == alone   # bitwise
+        _assert_some_overlap(res)
     finally:
         srv.close()
 
