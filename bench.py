@@ -3,12 +3,15 @@
 
 Default workload "bivariate-n20000": the parsimonious bivariate Matern model
 at n = 20,000 jittered-grid locations (N = 40,000), theta = (1, 1, 0.03, 0.5,
-1.5, 0.5), tile 960, dense FP64, plus cokriging of 2,000 held-out locations.
-One step = one full evaluation: Eq. 2 covariance generation, tiled Cholesky,
-L^-1 Z, log-determinant and Eq. 1, backward solve and the Eq. 3 predictor at
-the 2,000 new locations.  Inputs are synthetic: locations from a seeded
-jittered grid, Z = L e drawn once at setup from the joint 22,000-location
-covariance (the held-out 2,000 give the MSPE).
+1.5, 0.5), dense FP64 tiled Cholesky (tile 512) whose trailing updates and
+panel solves run emulated on the BF16 tensor cores (8 digit slices, FP64-class
+accuracy), plus cokriging of 2,000 held-out locations.  One step = one full
+evaluation: Eq. 2 covariance generation, tiled Cholesky, L^-1 Z,
+log-determinant and Eq. 1, backward solve and the Eq. 3 predictor at the
+2,000 new locations.  Inputs are synthetic: locations from a seeded jittered
+grid, Z = L e drawn once at setup from the joint 22,000-location covariance
+(the held-out 2,000 give the MSPE).  The same step with native FP64 FMA
+updates is timed once beside it (``fp64_dense``: time, l and |dl| / |l|).
 
 Output: one JSON line (rank 0).  ``--impl reference`` times the CPU FP64
 oracle on a bounded sample of the same workload instead (this repository has
@@ -85,18 +88,22 @@ def replica_value(units_per_rank: float, seconds: float, world: int) -> float:
 
 
 # Roofline of each kernel class: (bound, peak, unit, what the peak is).
+# The tensor-core classes are timed inside long steps: the sustained bf16 rate.
 def class_roofline(cls):
     mp = measured_peaks()
     if cls == "tcgemm":
-        if "bf16_tflops" in mp:
-            return "tensor", float(mp["bf16_tflops"]), "measured cuBLAS bf16 burst (FP16 runs at the bf16 rate)"
-        return "tensor", 1900.0, "fallback 1.9 PFLOP/s bf16 burst"
+        if "bf16_tflops_sustained" in mp:
+            return ("tensor", float(mp["bf16_tflops_sustained"]),
+                    "measured cuBLAS bf16 sustained (FP16 and BF16 MMAs run at the same rate)")
+        return "tensor", 1700.0, "fallback 1.7 PFLOP/s bf16 sustained"
     if cls == "sgemm":
         return "alu", FP32_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
     return "alu", FP64_PEAK_TFLOPS, "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"
 
 
 KERNEL_NAMES = {"gemm": "k_dgemm_update (FP64 FMA trailing/panel updates)",
+                "oz": "k_oz_update (tcgen05 BF16 digit products, exact FP32 accumulation: emulated FP64 "
+                      "trailing updates and panel solves)",
                 "sgemm": "k_sgemm_nt (FP32 SIMT diagonal/band and panel updates)",
                 "tcgemm": "k_tc_update (tcgen05 FP16x2 updates beyond the band)",
                 "covgen": "k_covgen_sym (FP64 Matern + Bessel K_nu)"}
@@ -104,13 +111,18 @@ TLR_KERNEL_NAMES = {"gemm": "k_bgemm + k_dgemm_update (FP64 low-rank updates of 
                     "tlr": "k_house_qr + k_jacobi_svd_cl (FP64 compression of the tiles)",
                     "covgen": "k_covgen_block (FP64 Matern + Bessel K_nu)"}
 METRIC = "loglik evals/s"
+
+
+def DENSE_EMULATED(geo):
+    """The dense FP64 form with tensor-core emulated updates, 8 slices (FP64-class accuracy)."""
+    return geo.opts(nb=512, fp64_gemm=1, oz_slices=8)
 UNIT = "evals/s"
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bivariate-n20000",
@@ -141,6 +153,15 @@ def parse():
                     help="estimation: comma-separated subset of the fits")
     ap.add_argument("--est-budget-s", type=float, default=600.0,
                     help="estimation: start no new MLE run after this many seconds")
+    ap.add_argument("--fp64-ref", default="auto", choices=["auto", "on", "off"],
+                    help="time one native FP64 step beside a reduced or emulated form (auto: when N <= 50,000)")
+    ap.add_argument("--tlr-z", default="model", choices=["model", "white"],
+                    help="tile low-rank workloads: Z drawn from the model (dense emulated factor) or white noise")
+    ap.add_argument("--tlr-ref", action="store_true",
+                    help="tile low-rank workloads: also l at the other accuracy (1e-7 / 1e-9) and the dense "
+                         "emulated-FP64 l of the same Z")
+    ap.add_argument("--oracle-subset", type=int, default=0,
+                    help="also compare l with the oracle on the first this-many locations (0 = off)")
     ap.add_argument("--dst", type=int, default=0,
                     help="tile low-rank workloads: Diagonal Super Tile, keep this many tile diagonals (Sec. 3.4)")
     return ap.parse_args()
@@ -259,14 +280,32 @@ def oracle_sample_run(w, n_s: int, m_s: int):
     return t_full, det
 
 
+def oracle_full_config0():
+    """The oracle's full evaluation of the N = 800 workload (covariance, Cholesky, solve, Eq. 1), timed."""
+    import oracle
+    oracle.build()
+    w0 = inputs.WORKLOADS["bivariate-n400"]
+    spec = w0.theta
+    th = oracle.Theta(list(spec.sigma2), spec.a, list(spec.nu), spec.beta_matrix())
+    locs, _ = w0.locations()
+    Z = inputs.normals(w0.z_seed, spec.p * w0.n)
+    t0 = time.perf_counter()
+    r = oracle.loglik(th, locs, Z)
+    t = time.perf_counter() - t0
+    return {"workload": w0.name, "N": spec.p * w0.n, "seconds": t, "evals_per_s": 1.0 / t, "loglik": r.loglik}
+
+
 def cpu_baseline_json(w, n_s, m_s, t_full, det, cores):
     return {"value": 1.0 / t_full, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "extrapolated": True, "sample_N": w.theta.p * det["n_sample"], "sample_m": det["m_sample"],
+            "sample_seconds": det["sample_s"],
             "sample": ("oracle (C, OpenMP, FP64) on the first %d observed + %d held-out locations "
-                       "(N = %d) in %.1f s; extrapolated to N = %d by N^3 for the Cholesky, N^2 for "
+                       "(N = %d), timed: %.1f s; value extrapolated to N = %d by N^3 for the Cholesky, N^2 for "
                        "covariance generation and the solve, n*m for prediction"
                        % (det["n_sample"], det["m_sample"], w.theta.p * det["n_sample"], det["sample_s"],
                           w.theta.p * w.n)),
-            "phases_s": {k: round(v, 3) for k, v in det.items() if k.endswith("_s")}}
+            "phases_s": {k: round(v, 3) for k, v in det.items() if k.endswith("_s")},
+            "config0_full": oracle_full_config0()}
 
 
 def run_reference(args):
@@ -279,15 +318,19 @@ def run_reference(args):
     m_s = 200 if w.n_pred else 0
     for _ in range(args.warmup):
         oracle_sample_run(w, args.cpu_sample_n, m_s)
-    ts, det = [], None
+    ts, ss, det = [], [], None
     for _ in range(args.steps):
         t_full, det = oracle_sample_run(w, args.cpu_sample_n, m_s)
         ts.append(t_full)
+        ss.append(det["sample_s"])
     t = sum(ts) / len(ts)
     value = 1.0 / t
+    # steps / ms_per_step describe what ran: one bounded oracle sample per step;
+    # value is the full workload's rate extrapolated from those samples
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(ss) / len(ss),
+            "extrapolated": True, "extrapolated_ms_per_eval": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_json(w, args),
             "cpu_baseline": cpu_baseline_json(w, args.cpu_sample_n, m_s, t, det, cores),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -307,14 +350,21 @@ def config_json(w, args):
     if w.extra.get("prec") == 1:
         form = ("mixed: FP64 diagonal tiles, FP32 band of %d tiles, %s tensor cores beyond, %d FP64 refinement sweeps"
                 % (w.extra.get("band", 4), "BF16" if w.extra.get("lowp") else "FP16x2", w.extra.get("refine_iters", 2)))
+    if w.extra.get("fp64_gemm") == 1:
+        S = w.extra.get("oz_slices", 8)
+        form = ("dense tiled Cholesky, FP64 diagonal tiles (native POTRF and inversion); trailing updates and panel "
+                "solves on the BF16 tensor cores: %d 7-bit digit slices per operand row with a power-of-two row "
+                "scale, exact FP32 accumulation, FP64 recombination (%s)"
+                % (S, "FP64-class accuracy" if S >= 8 else "about %d bits per operand" % (7 * S)))
     return {"workload": w.name, "n": w.n, "p": p, "N": p * w.n, "nb": w.nb, "n_pred": w.n_pred,
             "form": form, "theta": {"sigma2": list(w.theta.sigma2), "a": w.theta.a,
                                                            "nu": list(w.theta.nu), "beta": list(w.theta.beta)},
             "l2": ("inputs larger than L2: every tile column (%.1f GB) is regenerated every step" % (
                 8.0 * p * w.n * w.nb / 1e9) if w.extra.get("prec") == 2 else
                 "inputs larger than L2: the %.1f GB matrix is regenerated every step" % (8.0 * (p * w.n) ** 2 / 1e9)),
-            "z": ("white noise (cost does not depend on Z)" if w.extra.get("prec") == 2 and not args.mle
-                  else "Z = L e, joint draw")}
+            "z": ("white noise (cost does not depend on Z)" if w.extra.get("prec") == 2 and args.tlr_z == "white"
+                  else "Z = L e, joint draw" + (" (L: dense emulated-FP64 factor)" if w.extra.get("prec") == 2
+                                               else ""))}
 
 
 # --------------------------------------------------------------------------
@@ -349,8 +399,9 @@ def run_ours(args):
     ctx = geo.geo_create(dev.index)
 
     # ---- setup (untimed): locations and one joint draw Z = L e -------------
-    # (tile low-rank: the draw would need the dense factor of the full
-    # matrix, so Z is white noise there; the evaluation's cost does not depend on Z)
+    # (tile low-rank: the draw needs the dense factor of the full matrix; it
+    # is taken with the emulated FP64 form in a context of its own, which is
+    # destroyed afterwards so that the dense matrix does not stay cached)
     tlr = w.extra.get("prec") == 2
     obs, pred = w.locations()
     allp = np.vstack([obs, pred])
@@ -358,10 +409,14 @@ def run_ours(args):
     d_all = torch.as_tensor(allp, device=dev)
     d_e = torch.as_tensor(e, device=dev)
     d_zall = torch.empty(p * len(allp), dtype=torch.float64, device=dev)
-    if tlr and not args.mle:
+    if tlr and args.tlr_z == "white":
         d_zall.copy_(d_e)
+    elif tlr:
+        sctx = geo.geo_create(dev.index)
+        geo.geo_simulate(sctx, d_all, d_e, theta, d_zall, DENSE_EMULATED(geo))
+        sctx.close()
     else:
-        geo.geo_simulate(ctx, d_all, d_e, theta, d_zall, geo.opts(nb=960) if tlr else o)
+        geo.geo_simulate(ctx, d_all, d_e, theta, d_zall, o)
     d_locs = torch.as_tensor(obs, device=dev).contiguous()
     d_pred = torch.as_tensor(pred, device=dev).contiguous()
     d_z = d_zall[:N].clone()
@@ -444,6 +499,72 @@ def run_ours(args):
                "h2d_bytes_per_step": 8 * (2 * w.n + N + 2 * w.n_pred),
                "d2h_bytes_per_step": 8 * (p * w.n_pred + 1)}
 
+    # ---- native FP64 beside a reduced or emulated form (same step, same inputs) ----
+    emulated = w.extra.get("fp64_gemm") == 1
+    fp64_dense = None
+    want_ref = args.fp64_ref == "on" or (args.fp64_ref == "auto" and (emulated or w.extra.get("prec") == 1)
+                                         and N <= 100000 and not tlr)
+    if want_ref and (rank == 0 or world == 1):
+        o_nat = geo.opts(nb=960)
+        if N <= 50000:   # warm-up of the native kernels (negligible against a step beyond that)
+            ll_ref, fac = geo.geo_loglik(ctx, d_locs, d_z, theta, o_nat, keep=True)
+            fac.free()
+        geo.geo_profile_enable(ctx, True)
+        torch.cuda.synchronize()
+        r0 = torch.cuda.Event(enable_timing=True)
+        r1 = torch.cuda.Event(enable_timing=True)
+        r0.record()
+        ll_ref, fac = geo.geo_loglik(ctx, d_locs, d_z, theta, o_nat, keep=True)
+        if w.n_pred:
+            geo.geo_predict(ctx, fac, d_pred, d_zhat)
+        fac.free()
+        r1.record()
+        torch.cuda.synchronize()
+        pref = geo.geo_profile_read(ctx)
+        geo.geo_profile_enable(ctx, False)
+        ms_ref = r0.elapsed_time(r1)
+        g = pref["gemm"]
+        fp64_dense = {"form": "native FP64 FMA updates, tile 960", "ms_per_step": ms_ref,
+                      "evals_per_s": 1e3 / ms_ref, "loglik": ll_ref,
+                      "rel_dl": abs(ll - ll_ref) / abs(ll_ref),
+                      "speedup": ms_ref / (ms / args.steps),
+                      "k_dgemm_update_frac_of_fp64_peak": (g["flops"] / (g["ms"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS
+                                                           if g["ms"] > 0 else None)}
+    tlr_accuracy = None
+    if tlr and args.tlr_ref and (rank == 0 or world == 1):
+        tol = w.extra.get("tlr_tol", 1e-9)
+        other = 1e-7 if tol < 1e-8 else 1e-9
+        o_other = geo.opts(nb=w.nb, **dict(w.extra, tlr_tol=other))
+        t0 = time.perf_counter()
+        ll_other, _ = geo.geo_loglik(ctx, d_locs, d_z, theta, o_other)
+        t_other = time.perf_counter() - t0
+        ctx.close()   # release the TLR workspaces before the dense matrix
+        dctx = geo.geo_create(dev.index)
+        t0 = time.perf_counter()
+        ll_dense, _ = geo.geo_loglik(dctx, d_locs, d_z, theta, DENSE_EMULATED(geo))
+        t_dense = time.perf_counter() - t0
+        dctx.close()
+        ctx = geo.geo_create(dev.index)
+        tlr_accuracy = {"reference": "dense FP64 form, tensor-core emulated updates (8 slices)",
+                        "loglik_dense": ll_dense, "dense_seconds": t_dense,
+                        "tol": tol, "loglik": ll, "rel_dl_vs_dense": abs(ll - ll_dense) / abs(ll_dense),
+                        "other_tol": other, "loglik_other": ll_other, "other_seconds": t_other,
+                        "rel_dl_other_vs_dense": abs(ll_other - ll_dense) / abs(ll_dense)}
+    oracle_subset = None
+    if args.oracle_subset > 0 and (rank == 0 or world == 1):
+        import oracle
+        k = min(args.oracle_subset, w.n)
+        spec = w.theta
+        th_o = oracle.Theta(list(spec.sigma2), spec.a, list(spec.nu), spec.beta_matrix())
+        zs = d_z[: p * k].cpu().numpy()
+        t0 = time.perf_counter()
+        ref_sub = oracle.loglik(th_o, obs[:k], zs).loglik
+        t_or = time.perf_counter() - t0
+        ll_sub, _ = geo.geo_loglik(ctx, d_locs[:k].contiguous(), d_z[: p * k].contiguous(), theta,
+                                   geo.opts(nb=min(w.nb, 256) if emulated else 256, **w.extra))
+        oracle_subset = {"n": k, "N": p * k, "loglik_gpu": ll_sub, "loglik_oracle": ref_sub,
+                         "rel_dl": abs(ll_sub - ref_sub) / abs(ref_sub), "oracle_seconds": t_or}
+
     # ---- report ------------------------------------------------------------
     launches = sum(v["launches"] for v in prof.values())
     # dominant kernel class of the step and its roofline
@@ -451,25 +572,41 @@ def run_ours(args):
     dk = prof[dom]
     bound, peak, peak_src = class_roofline(dom)
     dom_tflops = dk["flops"] / (dk["ms"] * 1e-3) / 1e12 if dk["ms"] > 0 and dk["flops"] > 0 else 0.0
-    chol_ms = sum(prof[k]["ms"] for k in ("potrf", "trsm", "gemm", "sgemm", "tcgemm")) / args.steps
-    chol_tflops = (N ** 3 / 3.0) / (chol_ms * 1e-3) / 1e12 if chol_ms > 0 else 0.0
+    fp64eq_tflops = None
+    kname = (TLR_KERNEL_NAMES if tlr else KERNEL_NAMES).get(dom, dom)
+    if dom == "tcgemm" and emulated:
+        # the class counts FP64-equivalent flops (2 K per output); the tensor cores
+        # run S (S + 1) / 2 digit products of that size
+        S = w.extra.get("oz_slices", 8)
+        fp64eq_tflops = dom_tflops
+        dom_tflops *= S * (S + 1) / 2.0
+        kname = KERNEL_NAMES["oz"]
+    # Cholesky rate: N^3 / 3 over the step's time outside covariance generation,
+    # reductions, solves and prediction (the lookahead overlaps the classes)
+    other = sum(prof[k]["ms"] for k in ("covgen", "reduce", "solve", "predict")) / args.steps
+    chol_ms = max(ms / args.steps - other, 1e-9)
+    chol_tflops = (N ** 3 / 3.0) / (chol_ms * 1e-3) / 1e12
     # DRAM bytes per launch: an ncu capture of a full rank-960 trailing update
     # (N = 8,000) measured 0.822 x the algorithmic bytes; scaled to this run's
     # average launch (FP64 update kernel only)
     traffic = 0.822 * dk["bytes"] / max(dk["launches"], 1) if dom == "gemm" and not tlr else None
+    dtype = "f64"
+    if emulated:
+        dtype = "f64 (emulated: bf16 digit products, exact fp32 accumulation, %d slices)" % w.extra.get("oz_slices", 8)
     out = {"metric": METRIC, "value": replica_value(args.steps, ms * 1e-3, world), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
            "data": "synthetic", "config": config_json(w, args),
            "cholesky_tflops": None if tlr else chol_tflops,
            "dense_equivalent_tflops": chol_tflops if tlr else None,
-           "roofline": {"bound": bound, "kernel": (TLR_KERNEL_NAMES if tlr else KERNEL_NAMES).get(dom, dom),
+           "roofline": {"bound": bound, "kernel": kname,
                         "achieved": dom_tflops, "peak": peak,
                         "unit": "TFLOP/s", "frac": dom_tflops / peak, "peak_source": peak_src,
-                        "traffic": traffic},
+                        "traffic": traffic, "fp64_equivalent_tflops": fp64eq_tflops},
            "gpu_launches": launches,
            "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
            "quality": {"loglik": ll, "mspe": mspe},
+           "fp64_dense": fp64_dense, "oracle_subset": oracle_subset, "tlr_accuracy": tlr_accuracy,
            "tlr_factor": tlr_stats or None,
            "clocks": clk, "e2e": e2e}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

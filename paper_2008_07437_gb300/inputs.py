@@ -124,16 +124,30 @@ THETA_FIG5 = ThetaSpec(sigma2=(1.0, 1.0), a=0.09, nu=(0.5, 1.0), beta=(0.5,))
 WORKLOADS = {
     # 400 locations on a jittered 20 x 20 grid, N = 800, plain dense FP64.
     "bivariate-n400": Workload("bivariate-n400", 400, THETA_FIG5, nb=128, loc_seed=1000, z_seed=2000),
-    # 20,000 locations (N = 40,000), tile 960, dense FP64, 2,000 held-out locations to predict.
+    # 20,000 locations (N = 40,000), dense FP64 tiled Cholesky, 2,000 held-out locations to
+    # predict; the trailing updates and panel solves emulated on the tensor cores with 8 digit
+    # slices (FP64-class accuracy), tile 512.
     "bivariate-n20000": Workload("bivariate-n20000", 20000,
                                  ThetaSpec((1.0, 1.0), 0.03, (0.5, 1.5), (0.5,)),
-                                 n_pred=2000, nb=960, loc_seed=1001, z_seed=2001),
-    # 50,000 locations (N = 100,000), mixed precision.
-    # FP64 diagonal tiles, FP32 band of 4 tiles, FP16 x 2 tensor cores beyond, 2 refinement sweeps.
+                                 n_pred=2000, nb=512, loc_seed=1001, z_seed=2001,
+                                 extra={"fp64_gemm": 1, "oz_slices": 8}),
+    # The same with native FP64 FMA updates, tile 960.
+    "bivariate-n20000-native": Workload("bivariate-n20000-native", 20000,
+                                        ThetaSpec((1.0, 1.0), 0.03, (0.5, 1.5), (0.5,)),
+                                        n_pred=2000, nb=960, loc_seed=1001, z_seed=2001),
+    # 50,000 locations (N = 100,000), reduced precision: FP64 diagonal tiles, BF16 tensor cores
+    # with a power-of-two scale per row and FP32 accumulation for every other tile, as 5 digit
+    # slices (about 35 bits per operand).
     "bivariate-n50000-mixed": Workload("bivariate-n50000-mixed", 50000,
                                        ThetaSpec((1.0, 1.0), 0.1, (0.5, 1.0), (0.7,)),
-                                       nb=1024, loc_seed=1002, z_seed=2002,
-                                       extra={"prec": 1, "band": 4, "lowp": 0, "refine_iters": 2}),
+                                       nb=768, loc_seed=1002, z_seed=2002,
+                                       extra={"fp64_gemm": 1, "oz_slices": 5}),
+    # The FP32-class mixed form: FP64 diagonal tiles, FP32 band of 4 tiles, FP16 x 2 tensor cores
+    # beyond, 2 refinement sweeps.
+    "bivariate-n50000-fp16x2": Workload("bivariate-n50000-fp16x2", 50000,
+                                        ThetaSpec((1.0, 1.0), 0.1, (0.5, 1.0), (0.7,)),
+                                        nb=1024, loc_seed=1002, z_seed=2002,
+                                        extra={"prec": 1, "band": 4, "lowp": 0, "refine_iters": 2}),
     # 60,000 locations, trivariate (N = 180,000), tile low-rank at accuracy 1e-9, rank <= 200.
     "trivariate-n60000-tlr": Workload("trivariate-n60000-tlr", 60000,
                                       ThetaSpec((1.0, 1.0, 1.0), 0.05, (0.5, 1.0, 1.5), (0.5, 0.3, 0.4)),
