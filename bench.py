@@ -415,8 +415,8 @@ def run_ours(args):
         sctx = geo.geo_create(dev.index)
         geo.geo_simulate(sctx, d_all, d_e, theta, d_zall, DENSE_EMULATED(geo))
         sctx.close()
-    else:
-        geo.geo_simulate(ctx, d_all, d_e, theta, d_zall, o)
+    else:   # the draw takes an FP64-class factor whatever form is measured
+        geo.geo_simulate(ctx, d_all, d_e, theta, d_zall, DENSE_EMULATED(geo))
     d_locs = torch.as_tensor(obs, device=dev).contiguous()
     d_pred = torch.as_tensor(pred, device=dev).contiguous()
     d_z = d_zall[:N].clone()
