@@ -590,6 +590,10 @@ def run_ours(args):
     # (N = 8,000) measured 0.822 x the algorithmic bytes; scaled to this run's
     # average launch (FP64 update kernel only)
     traffic = 0.822 * dk["bytes"] / max(dk["launches"], 1) if dom == "gemm" and not tlr else None
+    if dom == "tcgemm" and emulated:
+        # k_oz_update: an ncu capture of every launch of one emulated evaluation at N = 16,000 measured
+        # 1.70 x the algorithmic bytes (16 B per output, the digit slices); scaled to this run's launches
+        traffic = 1.70 * dk["bytes"] / max(dk["launches"], 1)
     dtype = "f64"
     if emulated:
         dtype = "f64 (emulated: bf16 digit products, exact fp32 accumulation, %d slices)" % w.extra.get("oz_slices", 8)

@@ -408,12 +408,23 @@ int geo_server_pending(geo_server *server, int *queued, int *inflight, long long
 int geo_server_destroy(geo_server *server);
 
 /*
- * Autotuner for the tile size: times geo_loglik (one warm-up, one timed run)
- * on the caller's problem for each candidate nb and returns the fastest; the
- * choice is cached for the whole process, per device, form and order bucket
- * (powers of two of N), and geo_loglik with opts->nb = 0 on any context of
- * that device uses it (or 960 FP64 / 1024 mixed when nothing is cached).
+ * Autotuner (no paper counterpart: the paper fixes its tile sizes by hand,
+ * Sec. 6): times geo_loglik on the caller's problem for every candidate tile
+ * size nb and, in the mixed form (opts->prec = GEO_PREC_MIXED), every
+ * candidate FP32 band, and keeps the fastest.  Each candidate gets one
+ * warm-up and `samples` timed evaluations (CUDA events on `stream`; 0 = 3);
+ * its time is their median.  Candidates that are not valid for the form are
+ * skipped.  The choice is cached for the whole process, per device, form
+ * (FP64, FP64 with tensor-core updates, mixed, TLR) and order bucket (powers
+ * of two of N): geo_loglik with opts->nb = 0 on any context of that device
+ * takes the tuned nb and, in the mixed form, the tuned band (defaults when
+ * nothing is cached: nb 960 FP64, 512 FP64 with tensor-core updates, 1024
+ * mixed).  best_band receives -1 when the band was not tuned.
  */
+int geo_autotune(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev, const geo_theta *theta,
+                 const geo_opts *base, const int *nb_candidates, int n_nb, const int *band_candidates, int n_band,
+                 int samples, int *best_nb, int *best_band, double *best_ms, void *stream);
+/* geo_autotune over tile sizes only, 3 samples per candidate. */
 int geo_autotune_nb(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev, const geo_theta *theta,
                     const geo_opts *base, const int *candidates, int ncand, int *best_nb, double *best_ms,
                     void *stream);

@@ -134,6 +134,8 @@ SIGNATURES = {
     "geo_server_destroy": (_I, [_P]),
     "geo_autotune_nb": (_I, [_P, _P, _I, _P, ctypes.POINTER(geo_theta), ctypes.POINTER(geo_opts), _P, _I,
                              ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
+    "geo_autotune": (_I, [_P, _P, _I, _P, ctypes.POINTER(geo_theta), ctypes.POINTER(geo_opts), _P, _I, _P, _I, _I,
+                          ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
 }
 
 _lib = None
@@ -685,3 +687,20 @@ def geo_autotune_nb(ctx: Context, locs, z, theta: Theta, candidates, options: ge
                                       ctypes.byref(options) if options is not None else None, cand, len(candidates),
                                       ctypes.byref(best), ctypes.byref(ms), _stream(stream)))
     return best.value, ms.value
+
+
+def geo_autotune(ctx: Context, locs, z, theta: Theta, nb_candidates, band_candidates=(), samples: int = 3,
+                 options: geo_opts | None = None, stream=None):
+    """Fastest (nb, band) on this problem (band only in the mixed form, else -1); median of ``samples``
+    timed evaluations per candidate.  Cached process-wide for nb = 0.  Returns (nb, band, ms)."""
+    import torch
+    th, _keep = theta.to_c()
+    nbc = (ctypes.c_int * len(nb_candidates))(*nb_candidates)
+    bc = (ctypes.c_int * max(1, len(band_candidates)))(*band_candidates) if band_candidates else None
+    bnb, bband, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    ctx.check(ctx.lib.geo_autotune(ctx.handle, _dev_ptr(locs, "locs", torch.float64), locs.shape[0],
+                                   _dev_ptr(z, "z", torch.float64), ctypes.byref(th),
+                                   ctypes.byref(options) if options is not None else None, nbc, len(nb_candidates),
+                                   bc, len(band_candidates), int(samples), ctypes.byref(bnb), ctypes.byref(bband),
+                                   ctypes.byref(ms), _stream(stream)))
+    return bnb.value, bband.value, ms.value

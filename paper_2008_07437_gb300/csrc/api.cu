@@ -184,10 +184,14 @@ struct SetDevice {
 
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
-// Tile sizes picked by geo_autotune_nb, shared by every context of the
-// process: (device, form, floor(log2 N)) -> nb.
+// Tile sizes (and, for the mixed form, FP32 bands) picked by the autotuner,
+// shared by every context of the process: (device, form, floor(log2 N)) ->
+// (nb, band); band < 0 when it was not tuned.
+struct Tuned {
+    int nb, band;
+};
 std::mutex g_tuned_mu;
-std::map<std::tuple<int, int, int>, int> g_tuned_nb;
+std::map<std::tuple<int, int, int>, Tuned> g_tuned;
 
 int order_bucket(int N) {
     int b = 0;
@@ -202,9 +206,19 @@ int form_of(const geo_opts &o) { return (o.prec == GEO_PREC_FP64 && o.fp64_gemm 
 
 int resolve_nb(int device, int form, int N) {
     std::lock_guard<std::mutex> lk(g_tuned_mu);
-    auto it = g_tuned_nb.find(std::make_tuple(device, form, order_bucket(N)));
-    if (it != g_tuned_nb.end()) return it->second;
+    auto it = g_tuned.find(std::make_tuple(device, form, order_bucket(N)));
+    if (it != g_tuned.end()) return it->second.nb;
     return form == GEO_PREC_MIXED ? 1024 : form == FORM_F64E ? 512 : 960;
+}
+
+// nb = 0 in the options: the tuned tile size, and for the mixed form the tuned band.
+void resolve_tuned(int device, int N, geo_opts *o) {
+    const int form = form_of(*o);
+    o->nb = resolve_nb(device, form, N);
+    if (o->prec != GEO_PREC_MIXED) return;
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    auto it = g_tuned.find(std::make_tuple(device, form, order_bucket(N)));
+    if (it != g_tuned.end() && it->second.band >= 0) o->band = it->second.band;
 }
 
 int oz_slices_of(const geo_opts &o) { return o.oz_slices > 0 ? o.oz_slices : 8; }
@@ -710,7 +724,7 @@ int geo_loglik(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev,
     else
         geo_opts_default(&o);
     if (n <= 0 || !locs_dev || !z_dev) return fail(ctx, GEO_EINVAL, "n must be > 0 and pointers non-NULL");
-    if (o.nb == 0 && theta) o.nb = resolve_nb(ctx->device, form_of(o), theta->p * n);
+    if (o.nb == 0 && theta) resolve_tuned(ctx->device, theta->p * n, &o);
     if (o.nb < 64) return fail(ctx, GEO_EINVAL, "nb must be >= 64");
     if (int rc0 = check_dense_opts(ctx, o)) return rc0;
     if (o.prec != GEO_PREC_FP64 && o.prec != GEO_PREC_MIXED && o.prec != GEO_PREC_TLR)
@@ -1344,53 +1358,84 @@ int geo_mloe_mmom(geo_ctx *ctx, const double *locs_dev, int n, const double *pre
     return done(GEO_OK);
 }
 
-int geo_autotune_nb(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev, const geo_theta *theta,
-                    const geo_opts *base, const int *candidates, int ncand, int *best_nb, double *best_ms,
-                    void *stream) {
-    if (!ctx || !theta || !candidates || ncand <= 0) return GEO_EINVAL;
-    SetDevice sd(ctx->device);
+// Median device time of `samples` evaluations after one warm-up; GEO_EINVAL /
+// GEO_EUNSUPPORTED when the options are not valid for the form.
+static int time_candidate(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev, const geo_theta *theta,
+                          const geo_opts &o, int samples, void *stream, cudaEvent_t e0, cudaEvent_t e1, double *ms_out) {
     cudaStream_t s = (cudaStream_t)stream;
+    double ll;
+    int rc = geo_loglik(ctx, locs_dev, n, z_dev, theta, &o, &ll, nullptr, nullptr, stream);   // warm-up
+    if (rc != GEO_OK) return rc;
+    std::vector<float> t;
+    for (int k = 0; k < samples; ++k) {
+        cudaEventRecord(e0, s);
+        rc = geo_loglik(ctx, locs_dev, n, z_dev, theta, &o, &ll, nullptr, nullptr, stream);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        if (rc != GEO_OK) return rc;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        t.push_back(ms);
+    }
+    std::sort(t.begin(), t.end());
+    *ms_out = t[t.size() / 2];
+    return GEO_OK;
+}
+
+int geo_autotune(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev, const geo_theta *theta,
+                 const geo_opts *base, const int *nb_cand, int n_nb, const int *band_cand, int n_band, int samples,
+                 int *best_nb, int *best_band, double *best_ms, void *stream) {
+    if (!ctx || !theta || !nb_cand || n_nb <= 0 || (n_band > 0 && !band_cand) || n_band < 0) return GEO_EINVAL;
+    if (samples < 1) samples = 3;
+    SetDevice sd(ctx->device);
     geo_opts o;
     if (base)
         o = *base;
     else
         geo_opts_default(&o);
+    const bool tune_band = o.prec == GEO_PREC_MIXED && n_band > 0;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    int best = -1;
+    int bnb = -1, bband = -1;
     double bms = 1e300;
-    for (int c = 0; c < ncand; ++c) {
-        o.nb = candidates[c];
-        double ll;
-        int rc = geo_loglik(ctx, locs_dev, n, z_dev, theta, &o, &ll, nullptr, nullptr, stream);   // warm-up
-        if (rc == GEO_EINVAL || rc == GEO_EUNSUPPORTED) continue;   // candidate not valid for this form
-        if (rc != GEO_OK) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return rc;
-        }
-        cudaEventRecord(e0, s);
-        rc = geo_loglik(ctx, locs_dev, n, z_dev, theta, &o, &ll, nullptr, nullptr, stream);
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rc == GEO_OK && ms < bms) {
-            bms = ms;
-            best = candidates[c];
+    for (int c = 0; c < n_nb; ++c) {
+        for (int b = 0; b < (tune_band ? n_band : 1); ++b) {
+            o.nb = nb_cand[c];
+            if (tune_band) o.band = band_cand[b];
+            double ms = 0.0;
+            const int rc = time_candidate(ctx, locs_dev, n, z_dev, theta, o, samples, stream, e0, e1, &ms);
+            if (rc == GEO_EINVAL || rc == GEO_EUNSUPPORTED) continue;   // candidate not valid for this form
+            if (rc != GEO_OK) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return rc;
+            }
+            if (ms < bms) {
+                bms = ms;
+                bnb = o.nb;
+                bband = tune_band ? o.band : -1;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (best < 0) return fail(ctx, GEO_EINVAL, "no valid tile-size candidate");
+    if (bnb < 0) return fail(ctx, GEO_EINVAL, "no valid candidate");
     {
         std::lock_guard<std::mutex> lk(g_tuned_mu);
-        g_tuned_nb[std::make_tuple(ctx->device, form_of(o), order_bucket(theta->p * n))] = best;
+        g_tuned[std::make_tuple(ctx->device, form_of(o), order_bucket(theta->p * n))] = Tuned{bnb, bband};
     }
-    if (best_nb) *best_nb = best;
+    if (best_nb) *best_nb = bnb;
+    if (best_band) *best_band = bband;
     if (best_ms) *best_ms = bms;
     return GEO_OK;
+}
+
+int geo_autotune_nb(geo_ctx *ctx, const double *locs_dev, int n, const double *z_dev, const geo_theta *theta,
+                    const geo_opts *base, const int *candidates, int ncand, int *best_nb, double *best_ms,
+                    void *stream) {
+    return geo_autotune(ctx, locs_dev, n, z_dev, theta, base, candidates, ncand, nullptr, 0, 3, best_nb, nullptr,
+                        best_ms, stream);
 }
 
 int geo_gemm_f64e(geo_ctx *ctx, int m, int n, int k, const double *A_dev, long long lda, const double *B_dev,

@@ -183,6 +183,26 @@ def test_autotuner_picks_a_candidate_and_nb0_uses_it(built):
         ctx.close()
 
 
+def test_autotuner_tunes_nb_and_band_and_nb0_uses_both(built):
+    # mixed form: the tuned (nb, band) pair is what nb = 0 runs -- the likelihood with nb = 0 is
+    # bitwise the one of the explicit pair, and the band changes the arithmetic
+    ctx = geo.geo_create(0)
+    try:
+        locs, Z, _, th = _dataset(1200, 0, 61)
+        dl, dz = torch.as_tensor(locs, device="cuda"), torch.as_tensor(Z, device="cuda")
+        base = geo.opts(prec=geo.GEO_PREC_MIXED, refine_iters=2)
+        nb, band, ms = geo.geo_autotune(ctx, dl, dz, th, [128, 256], [0, 1, 3], samples=3, options=base)
+        assert nb in (128, 256) and band in (0, 1, 3) and ms > 0
+        v0, _ = geo.geo_loglik(ctx, dl, dz, th, geo.opts(nb=0, prec=geo.GEO_PREC_MIXED, refine_iters=2))
+        vb, _ = geo.geo_loglik(ctx, dl, dz, th, geo.opts(nb=nb, band=band, prec=geo.GEO_PREC_MIXED, refine_iters=2))
+        assert v0 == vb
+        others = [geo.geo_loglik(ctx, dl, dz, th, geo.opts(nb=nb, band=b, prec=geo.GEO_PREC_MIXED,
+                                                             refine_iters=2))[0] for b in (0, 1, 3) if b != band]
+        assert any(v != v0 for v in others)   # the band is not a no-op at this size
+    finally:
+        ctx.close()
+
+
 def test_server_escalates_a_reduced_form_that_is_not_spd(built):
     # a = 0.2, nu_2 = 1.5 at 5,000 locations: FP32 off-diagonal tiles lose
     # positive definiteness, FP64 does not
