@@ -997,7 +997,7 @@ def run_batch(args):
            "data": "synthetic",
            "config": {"workload": "batch", "problems": len(items), "p": 2, "n_range": [50, 1000],
                       "theta_box": "a in [0.03, 0.2], nu_i in [0.5, 1.5], beta in [-0.7, 0.7], sigma^2_i in [0.5, 2]",
-                      "form": "dense FP64, one launch sequence per panel step for the whole batch, CUDA graph replay",
+                      "form": "dense FP64, one persistent launch over the units of every problem (progress counters, bounded waits), CUDA graph replay",
                       "l2": "inputs larger than L2: %.1f GB of matrices regenerated every step" % (
                           sum(8.0 * (2 * n) ** 2 for n, _, _, _ in probs) / 1e9)},
            "dense_equivalent_tflops": tflops,

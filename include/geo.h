@@ -287,13 +287,18 @@ int geo_mle_best(const geo_mle_state *state, double *sigma2, double *a, double *
 
 /*
  * Batched log-likelihoods of many small, uneven problems (Eq. 1 for each),
- * dense FP64, in the callers' location order.  One launch per step serves the
- * whole batch (covariance generation, each 64-wide panel of the Cholesky
- * factorisation, the reduction); the launch sequence of a batch shape (count
+ * dense FP64, in the callers' location order.  One launch builds the K_nu
+ * tables of every theta; one persistent launch does the rest for the whole
+ * batch: its CTAs walk a table of units (a 64 x 64 block of location pairs of
+ * Eq. 2, the POTRF of a 64-wide diagonal block, the TRSM of 128 rows below
+ * it, a 128 x 64 tile of the trailing update, the reduction), each unit
+ * waiting (bounded) on its problem's progress counter.  The table's order
+ * comes from a list-scheduling simulation on the host (cached while the
+ * problem sizes stay the same).  The launch sequence of a batch shape (count
  * and largest order) is captured once as a CUDA graph and replayed, with the
- * per-problem inputs and theta refreshed in device descriptors.  A problem's
- * result depends only on its own inputs: it is bit-identical alone and in any
- * batch.
+ * per-problem inputs, theta and units refreshed in device memory.  A
+ * problem's result depends only on its own inputs: it is bit-identical alone
+ * and in any batch.  GEO_ETIMEOUT if a bounded wait expired.
  *   items        count entries (host array); each names device inputs and a
  *                host theta, as for geo_loglik
  *   loglik_host  count results (host); NaN where Sigma is not positive definite

@@ -51,6 +51,8 @@ struct geo_ctx {
     void *bws = nullptr, *bdesc_d = nullptr, *bdesc_h = nullptr;
     size_t bws_bytes = 0, bdesc_cap = 0;
     std::map<std::tuple<int, int, int>, std::pair<cudaGraphExec_t, long long>> graphs;   // -> (exec, kernel nodes)
+    std::vector<int> border;            // problem orders of the cached ticket table
+    std::vector<unsigned char> bunits;  // cached ticket table (16 bytes per unit)
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture (the legacy stream cannot capture)
     std::vector<geo_factor *> factors;
     // K_nu tables of the theta of the last geo_covgen call
@@ -1159,7 +1161,15 @@ int geo_loglik_batch(geo_ctx *ctx, int count, const geo_batch_item *items, doubl
     }
     int rc;
     if ((rc = ensure_buffer(ctx, &ctx->bws, &ctx->bws_bytes, sizeof(double) * total, s))) return rc;
-    const size_t dbytes = batch_desc_bytes() * (size_t)count;
+    // device buffer: descriptors, counters (4 + count ints), the unit count, the ticket table
+    std::vector<int> orders(2 * count);   // orders, then location counts
+    for (int k = 0; k < count; ++k) orders[k] = items[k].theta.p * items[k].n, orders[count + k] = items[k].n;
+    const int nunits = -batch_units(orders.data(), orders.data() + count, count, 0, nullptr, 0);   // size query
+    const size_t desc_bytes = batch_desc_bytes() * (size_t)count;
+    const size_t cnt_off = (desc_bytes + 255) / 256 * 256;
+    const size_t nun_off = cnt_off + (sizeof(int) * (4 + (size_t)count) + 255) / 256 * 256;
+    const size_t unit_off = nun_off + 256;
+    const size_t dbytes = unit_off + 16 * (size_t)nunits;
     if (ctx->bdesc_cap < dbytes) {
         CK(cudaStreamSynchronize(s));
         if (ctx->bdesc_d) cudaFree(ctx->bdesc_d);
@@ -1183,7 +1193,20 @@ int geo_loglik_batch(geo_ctx *ctx, int count, const geo_batch_item *items, doubl
         cps[k].tab = base + offs[k] + (size_t)ld * N;
         batch_fill_desc(ctx->bdesc_h, k, base + offs[k], ld, N, it.n, it.locs_dev, it.z_dev, cps[k]);
     }
-    CK(cudaMemcpyAsync(ctx->bdesc_d, ctx->bdesc_h, dbytes, cudaMemcpyHostToDevice, s));
+    char *hb = (char *)ctx->bdesc_h, *db = (char *)ctx->bdesc_d;
+    *(int *)(hb + nun_off) = nunits;
+    // the ticket table depends only on the problem orders: rebuilt when they change
+    if (ctx->border != orders) {
+        ctx->bunits.resize(16 * (size_t)nunits);
+        batch_units(orders.data(), orders.data() + count, count, batch_workers(), ctx->bunits.data(), (size_t)nunits);
+        ctx->border = orders;
+    }
+    memcpy(hb + unit_off, ctx->bunits.data(), 16 * (size_t)nunits);
+    CK(cudaMemcpyAsync(db, hb, desc_bytes, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(db + nun_off, hb + nun_off, dbytes - nun_off, cudaMemcpyHostToDevice, s));
+    int *counters_d = (int *)(db + cnt_off);
+    const int *nunits_d = (const int *)(db + nun_off);
+    const void *units_d = db + unit_off;
     const auto key = std::make_tuple(count, nmax, Nmax);
     auto itg = ctx->graphs.find(key);
     if (itg == ctx->graphs.end()) {
@@ -1193,7 +1216,7 @@ int geo_loglik_batch(geo_ctx *ctx, int count, const geo_batch_item *items, doubl
         ProfBind pb(&counter);
         cudaGraph_t graph;
         CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = batch_record(ctx->bdesc_d, count, nmax, Nmax, ctx->cap_stream);
+        cudaError_t e = batch_record(ctx->bdesc_d, units_d, nunits_d, counters_d, count, nmax, Nmax, ctx->cap_stream);
         cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &graph);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "batch capture");
         if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "batch capture end");
@@ -1211,6 +1234,9 @@ int geo_loglik_batch(geo_ctx *ctx, int count, const geo_batch_item *items, doubl
     CK(batch_results(ctx->bdesc_d, ctx->bdesc_h, count, loglik_host, info.data(), s));
     if (info_host)
         for (int k = 0; k < count; ++k) info_host[k] = info[k];
+    int tmo = 0;   // a bounded wait of the persistent launch that expired
+    CK(cudaMemcpy(&tmo, counters_d + 2, sizeof(int), cudaMemcpyDeviceToHost));
+    if (tmo) return fail(ctx, GEO_ETIMEOUT, "a bounded wait of the batched factorisation expired");
     return GEO_OK;
 }
 

@@ -301,7 +301,17 @@ cudaError_t tlr_reduce(const TlrFactor &F, const double *y, const DevStatus *st,
 size_t batch_desc_bytes();
 void batch_fill_desc(void *hdesc, int k, double *A, long long ld, int N, int n, const double *locs, const double *z,
                      const CovParams &cp);
-cudaError_t batch_record(void *ddesc, int count, int nmax, int Nmax, cudaStream_t s);
+// Ticket table of the persistent launch (16 bytes per unit) for problems of orders N[0..count) and
+// n[0..count) locations,
+// ordered by a list-scheduling simulation on `workers` CTAs; returns the unit count, or minus it when
+// out is NULL or cap (units) is too small.
+int batch_units(const int *N, const int *n, int count, int workers, void *out, size_t cap);
+// CTAs of the persistent launch.
+int batch_workers();
+// units: device ticket table, nunits: device int holding its length (read by the launch, so a captured
+// sequence serves any table); counters: 4 + count device ints (zeroed by the sequence itself).
+cudaError_t batch_record(void *ddesc, const void *units, const int *nunits, int *counters, int count, int nmax,
+                         int Nmax, cudaStream_t s);
 cudaError_t batch_results(const void *ddesc, void *hdesc, int count, double *loglik, int *info, cudaStream_t s);
 
 // ---- host helpers (api.cu) ------------------------------------------------
