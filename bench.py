@@ -138,7 +138,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrival rate (req/s)")
     ap.add_argument("--slots", type=int, default=4, help="serving: worker threads")
     ap.add_argument("--budget-gb", type=float, default=200.0, help="serving: device-memory budget (GiB)")
-    ap.add_argument("--serving-prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--serving-prec", default="mixed", choices=["mixed", "fp64", "emulated"],
+                    help="serving form: FP32 off-diagonal tiles (mixed), native FP64, or the 5-slice tensor-core form")
     ap.add_argument("--no-tune", action="store_true", help="serving: skip the tile-size autotuner")
     ap.add_argument("--batch-count", type=int, default=512, help="batch: problems per call")
     ap.add_argument("--mle", type=int, default=0, help="run this many Nelder-Mead steps instead of evaluations")
@@ -635,6 +636,10 @@ SERVING_METRIC = "serving latency p50 (ms; p99 beside)"
 def serving_opts(geo, prec):
     if prec == "fp64":
         return geo.opts(nb=0), "dense FP64"
+    if prec == "emulated":
+        return (geo.opts(nb=0, fp64_gemm=1, oz_slices=5),
+                "FP64 diagonal tiles; every other tile's update and panel solve on the BF16 tensor cores, 5 digit "
+                "slices (about 35 bits per operand, exact FP32 accumulation); no refinement, no FP64 re-run")
     return (geo.opts(nb=0, prec=1, band=1 << 20, refine_iters=2),
             "FP64 diagonal tiles, FP32 off-diagonal tiles (FP32 TRSM and updates), 2 FP64 refinement sweeps; "
             "run again in FP64 when the reduced form is not positive definite")
@@ -739,7 +744,8 @@ def run_serving(args):
             locs = inputs.jittered_grid(n, 3997)
             dl = torch.as_tensor(locs, device=dev)
             dz = torch.as_tensor(inputs.normals(3996, 2 * n), device=dev)
-            cands = [c for c in (256, 512, 1024) if c <= 2 * n] or [256]
+            cands = ([c for c in (256, 512, 768) if c <= 2 * n] if args.serving_prec == "emulated"
+                     else [c for c in (256, 512, 1024) if c <= 2 * n]) or [256]
             best, _ = geo.geo_autotune_nb(ctx, dl, dz, th_t, cands, o)
             tuned["N>=%d" % (1 << b)] = best
 
@@ -758,7 +764,7 @@ def run_serving(args):
     for i in range(max(args.warmup, 1) * args.slots):
         wr = inputs.ServingRequest(10 ** 6 + i, 0.0, "loglik", n=1000, theta=inputs.THETA_FIG5)
         wids[srv.submit_loglik(wr.locations(), wr.observations(), geo.Theta.from_spec(wr.theta), o,
-                               escalate=True)] = wr
+                               escalate=args.serving_prec == "mixed")] = wr
     collect(wids)
     torch.cuda.synchronize()
     launches0 = sum(v["launches"] for v in srv.profile().values())
@@ -776,7 +782,8 @@ def run_serving(args):
             time.sleep(delay)
         if r.kind == "loglik":
             locs, z, th = prep[r.k]
-            rid = srv.submit_loglik(locs, z, th, o, dataset=r.dataset, keep=r.keep, escalate=True)
+            rid = srv.submit_loglik(locs, z, th, o, dataset=r.dataset, keep=r.keep,
+                                    escalate=args.serving_prec == "mixed")
         else:
             rid, _ = srv.submit_predict(r.dataset, prep[r.k], 2, release=r.release)
         ids[rid] = r
@@ -796,7 +803,7 @@ def run_serving(args):
     svc = [x["t_end"] - x["t_start"] for _, x in rows]
     span = max(x["t_end"] for _, x in rows) - min(x["t_submit"] for _, x in rows)
     n_ll = sum(1 for r, x in rows if r.kind == "loglik" and x["status"] == 0)
-    escalated = sum(1 for r, x in rows if r.kind == "loglik" and x["prec"] == 0 and args.serving_prec != "fp64")
+    escalated = sum(1 for r, x in rows if r.kind == "loglik" and x["prec"] == 0 and args.serving_prec == "mixed")
     failed = sum(1 for _, x in rows if x["status"] != 0)
     lat_k = {k: [x["t_end"] - x["t_submit"] for r, x in rows if r.kind == k] for k in ("loglik", "predict")}
     allv = gather_over_ranks({"lat": lat, "span": span, "n": len(rows), "n_ll": n_ll, "launches": launches})
@@ -810,7 +817,8 @@ def run_serving(args):
     acc = None
     if args.serving_prec != "fp64":
         acc = []
-        small = sorted((r for r, x in rows if r.kind == "loglik" and x["prec"] == 1), key=lambda r: r.n)[:3]
+        served_reduced = (lambda x: x["prec"] == 1) if args.serving_prec == "mixed" else (lambda x: x["status"] == 0)
+        small = sorted((r for r, x in rows if r.kind == "loglik" and served_reduced(x)), key=lambda r: r.n)[:3]
         for r in small:
             locs, _, th = prep[r.k]
             dl = torch.as_tensor(locs, device=dev)
@@ -831,7 +839,8 @@ def run_serving(args):
     out = {"metric": SERVING_METRIC, "value": p50, "unit": "ms", "n_gpus": world, "steps": total,
            "warmup": max(args.warmup, 1) * args.slots, "ms_per_step": span * 1e3 / max(total, 1),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64+f32" if args.serving_prec != "fp64" else "f64", "data": "synthetic",
+           "dtype": {"mixed": "f64+f32", "fp64": "f64", "emulated": "f64 (emulated: bf16 digit products, 5 slices)"}[
+               args.serving_prec], "data": "synthetic",
            "config": serving_config(args, stream, form, tuned),
            "p50_ms": p50, "p99_ms": p99,
            "p50_ms_by_kind": {k: float(np.percentile(v, 50)) * 1e3 for k, v in lat_k.items() if v},

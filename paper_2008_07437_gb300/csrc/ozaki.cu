@@ -42,9 +42,10 @@
 //   warp 1: allocates the 512 TMEM columns; one lane issues tcgen05.mma
 //     kind::f16 (M 128, N BN, K 16) level by level from precomputed shared
 //     memory descriptors and commits chunks back to the producer;
-//   warps 2-9: epilogue; tcgen05.ld of each level, fold into registers,
-//     release TMEM (the next pass or tile starts its MMAs), then the FP64
-//     read-modify-write of C.
+//   warps 2-9: epilogue; tcgen05.ld of each level, releasing that
+//     accumulator slot as soon as it is read (the MMAs of the next pass or
+//     tile may start into it while the epilogue folds the values in
+//     registers), then the FP64 read-modify-write of C.
 // Every mbarrier wait is bounded; on expiry the thread records a code in the
 // status word, the CTA drains what it has in flight, frees TMEM and returns.
 #include <cuda.h>
@@ -158,7 +159,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     constexpr int A_BYTES = Cfg::A_BYTES, B_BYTES = Cfg::B_BYTES;
     constexpr int PASSES = Cfg::PASSES, CPT = Cfg::CPT, WREG = Cfg::WREG;
     extern __shared__ uint8_t smem_raw[];
-    __shared__ uint64_t full_bar[ST], empty_bar[ST], acc_full, acc_empty, drain_bar;
+    constexpr int NSLOT = OZ_TMEM_COLS / BN;   // accumulator slots of BN columns
+    __shared__ uint64_t full_bar[ST], empty_bar[ST], acc_full, slot_empty[NSLOT], drain_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int skip;
 
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             mbar_init(&empty_bar[s], 1);
         }
         mbar_init(&acc_full, 1);
-        mbar_init(&acc_empty, OZ_EPI_WARPS);
+        for (int j = 0; j < NSLOT; ++j) mbar_init(&slot_empty[j], OZ_EPI_WARPS);
         mbar_init(&drain_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -227,7 +229,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         if (lane == 0) {
             const uint32_t idesc = instr_desc_f16(1, OZ_BM, BN);
             long long g = 0;
-            int job = 0;   // (tile, pass) jobs of this CTA
+            int use[NSLOT];   // jobs that have used each accumulator slot so far
+#pragma unroll
+            for (int j = 0; j < NSLOT; ++j) use[j] = 0;
             bool ok = true;
             for (long long L = blockIdx.x; L < ntiles && ok; L += gridDim.x) {
                 int gr, gc, ar, br;
@@ -235,11 +239,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
                 for (int ps = 0; ps < PASSES; ++ps) {
                     if (!ok) break;
-                    if (job >= 1 && !mbar_wait(&acc_empty, (uint32_t)((job - 1) & 1), tword, 25)) {
-                        ok = false;
-                        break;
-                    }
-                    fence_after_sync();
                     const int llo = Cfg::lev_lo(ps), lhi = Cfg::lev_hi(ps);
                     for (int kb = 0; kb < args.nk; ++kb, ++g) {
                         const int s = (int)(g % ST);
@@ -256,6 +255,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                             for (int l = 2; l <= S + 1; ++l) {
                                 if (l < llo || l > lhi) continue;
                                 const int tlo = (l - S > 1) ? l - S : 1, thi = (l - 1 < S) ? l - 1 : S;
+                                const int slot = l - llo;
+                                if (kb == 0 && kk == 0 && use[slot] >= 1) {
+                                    // the epilogue has read this slot's previous contents (per-slot release)
+                                    if (!mbar_wait(&slot_empty[slot], (uint32_t)((use[slot] - 1) & 1), tword, 25)) {
+                                        ok = false;
+                                        break;
+                                    }
+                                    fence_after_sync();
+                                }
 #pragma unroll
                                 for (int t = tlo; t <= thi; ++t) {
                                     const int u = l - t;
@@ -266,12 +274,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                                             (kb != 0 || kk != 0 || t != tlo) ? 1u : 0u);
                                 }
                             }
+                            if (!ok) break;
                         }
+                        if (!ok) break;
                         mma_commit(&empty_bar[s]);
                     }
                     if (!ok) break;
                     mma_commit(&acc_full);
-                    ++job;
+#pragma unroll
+                    for (int l = 2; l <= S + 1; ++l)
+                        if (l >= llo && l <= lhi) ++use[l - llo];
                 }
             }
             // every MMA issued so far has completed before TMEM can be freed
@@ -309,6 +321,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                         float v[32];
                         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((l - llo) * BN + h * CPT + c32 * 32),
                                   v);
+                        if (c32 == CPT / 32 - 1) {
+                            // this warp has read the slot: the MMAs of the next job may overwrite it
+                            fence_before_sync();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&slot_empty[l - llo]);
+                        }
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
                             const long long d = (long long)__float2int_rn(v[j]);   // an exact integer below 2^24
@@ -316,9 +334,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                         }
                     }
                 }
-                fence_before_sync();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&acc_empty);
                 ++job;
                 if (grow < args.m_end) {
                     const bool over = args.overwrite && ps == 0;
