@@ -146,6 +146,8 @@ def parse():
     ap.add_argument("--profile-lik", action="store_true",
                     help="mle: optimise the profile likelihood (marginal variances estimated, Sec. 4.2)")
     ap.add_argument("--mloe-m", type=int, default=100, help="mloe: prediction locations")
+    ap.add_argument("--mloe-form", default="native", choices=["native", "emulated"],
+                    help="mloe: FP64 factorisations with native FMA updates or on the tensor cores (8 slices)")
     ap.add_argument("--tlr-tol", type=float, default=0.0, help="tile low-rank accuracy (default: the workload's)")
     ap.add_argument("--est-a", default="0.03,0.09,0.2", help="estimation: range parameters (weak, moderate, strong)")
     ap.add_argument("--replicates", type=int, default=2, help="estimation: simulated fields per range")
@@ -1058,7 +1060,7 @@ def run_mloe(args):
     ctx = geo.geo_create(0)
     dl, dp = torch.as_tensor(locs, device=dev), torch.as_tensor(pred, device=dev)
     th_t, th_a = geo.Theta.from_spec(spec), geo.Theta.from_spec(th_a_spec)
-    o = geo.opts(nb=960)
+    o = geo.opts(nb=960) if args.mloe_form == "native" else DENSE_EMULATED(geo)
     for _ in range(args.warmup):
         geo.geo_mloe_mmom(ctx, dl, dp, th_t, th_a, o)
     torch.cuda.synchronize()
@@ -1074,16 +1076,22 @@ def run_mloe(args):
     prof = geo.geo_profile_read(ctx)
     ph = {k: v["ms"] / args.steps for k, v in prof.items()}
     gen = ph["covgen"]
-    fact = ph["potrf"] + ph["trsm"] + ph["gemm"]
+    fact = ph["potrf"] + ph["trsm"] + ph["gemm"] + ph["tcgemm"]
     comp = ph["solve"] + ph["reduce"] + ph["aux"]
-    dk = prof["gemm"]
-    bound, peak, peak_src = class_roofline("gemm")
+    cls = "gemm" if args.mloe_form == "native" else "tcgemm"
+    dk = prof[cls]
+    bound, peak, peak_src = class_roofline(cls)
     ach = dk["flops"] / (dk["ms"] * 1e-3) / 1e12 if dk["ms"] > 0 else 0.0
+    if cls == "tcgemm":
+        ach *= 36.0   # 8 slices: 36 BF16 digit products per FP64-equivalent product
     out = {"metric": "MLOE/MMOM time", "value": t, "unit": "s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": mloe_config(args, n, spec, th_a_spec),
            "mloe": ml, "mmom": mm, "phases_ms": {"GEN": gen, "FACT": fact, "COMP": comp},
-           "roofline": {"bound": bound, "kernel": "k_dgemm_update (both factorisations)", "achieved": ach,
+           "form": ("native FP64 FMA updates" if args.mloe_form == "native"
+                    else "FP64 updates and panel solves on the tensor cores (8 digit slices)"),
+           "roofline": {"bound": bound, "kernel": ("k_dgemm_update" if cls == "gemm" else "k_oz_update") +
+                        " (both factorisations)", "achieved": ach,
                         "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "peak_source": peak_src,
                         "traffic": None},
            "gpu_launches": sum(v["launches"] for v in prof.values()), "clocks": clk}

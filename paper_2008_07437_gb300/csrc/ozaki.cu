@@ -586,10 +586,24 @@ __global__ void __launch_bounds__(TRTRI_THREADS) k_trtri_neg(const double *__res
 #pragma unroll
         for (int c = 0; c < TRTRI_COLS; ++c) w[q][c] = (r == c0 + c) ? 1.0 : 0.0;
     }
+    // column k of L for this thread's rows (and the diagonal entry for the owner of row k),
+    // loaded one step ahead so that the load latency is off the chain of barriers
+    double lcol[TRTRI_RPT], ldiag = 0.0;
+    auto load_col = [&](int k, double *dst, double *dg) {
+#pragma unroll
+        for (int q = 0; q < TRTRI_RPT; ++q) {
+            const int r = threadIdx.x + q * TRTRI_THREADS;
+            dst[q] = (k < jb && r >= k && r < jb) ? L[(long long)k * ld + r] : 0.0;
+            if (r == k) *dg = dst[q];
+        }
+    };
+    load_col(c0, lcol, &ldiag);
     for (int k = c0; k < jb; ++k) {
+        double lnext[TRTRI_RPT], dnext = 0.0;
+        load_col(k + 1, lnext, &dnext);
         const int owner_q = k / TRTRI_THREADS, owner_t = k % TRTRI_THREADS;
         if (threadIdx.x == owner_t) {
-            const double inv = 1.0 / L[(long long)k * ld + k];
+            const double inv = 1.0 / ldiag;
 #pragma unroll
             for (int q = 0; q < TRTRI_RPT; ++q)
                 if (q == owner_q) {
@@ -605,11 +619,13 @@ __global__ void __launch_bounds__(TRTRI_THREADS) k_trtri_neg(const double *__res
         for (int q = 0; q < TRTRI_RPT; ++q) {
             const int r = threadIdx.x + q * TRTRI_THREADS;
             if (r > k && r < jb) {
-                const double l = L[(long long)k * ld + r];
 #pragma unroll
-                for (int c = 0; c < TRTRI_COLS; ++c) w[q][c] = fma(-l, wk[k & 1][c], w[q][c]);
+                for (int c = 0; c < TRTRI_COLS; ++c) w[q][c] = fma(-lcol[q], wk[k & 1][c], w[q][c]);
             }
         }
+#pragma unroll
+        for (int q = 0; q < TRTRI_RPT; ++q) lcol[q] = lnext[q];
+        if (threadIdx.x == (k + 1) % TRTRI_THREADS) ldiag = dnext;
     }
 #pragma unroll
     for (int q = 0; q < TRTRI_RPT; ++q) {
