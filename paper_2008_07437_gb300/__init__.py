@@ -103,6 +103,7 @@ SIGNATURES = {
     "geo_loglik": (_I, [_P, _P, _I, _P, ctypes.POINTER(geo_theta), ctypes.POINTER(geo_opts),
                         ctypes.POINTER(_D), ctypes.POINTER(_P), ctypes.POINTER(_I), _P]),
     "geo_predict": (_I, [_P, _P, _P, _I, _P, _P]),
+    "geo_predict_batch": (_I, [_P, _I, _P, _P, _P, _P, _P]),
     "geo_simulate": (_I, [_P, _P, _I, _P, ctypes.POINTER(geo_theta), ctypes.POINTER(geo_opts), _P,
                           ctypes.POINTER(_I), _P]),
     "geo_factor_stats_get": (_I, [_P, ctypes.POINTER(geo_factor_stats)]),
@@ -354,6 +355,19 @@ def geo_predict(ctx: Context, factor: Factor, new_locs, zhat, stream=None):
     ctx.check(ctx.lib.geo_predict(ctx.handle, factor.handle, _dev_ptr(new_locs, "new_locs", torch.float64),
                                   new_locs.shape[0], _dev_ptr(zhat, "zhat", torch.float64), _stream(stream)))
     return zhat
+
+
+def geo_predict_batch(ctx: Context, entries, stream=None):
+    """Cokriging on many kept factors in one launch: entries = [(factor, new_locs, zhat), ...]."""
+    import torch
+    count = len(entries)
+    facs = (ctypes.c_void_p * count)(*[f.handle.value if isinstance(f.handle, ctypes.c_void_p) else f.handle
+                                       for f, _, _ in entries])
+    locs = (ctypes.c_void_p * count)(*[_dev_ptr(l, "new_locs", torch.float64).value for _, l, _ in entries])
+    ms = (ctypes.c_int * count)(*[l.shape[0] for _, l, _ in entries])
+    outs = (ctypes.c_void_p * count)(*[_dev_ptr(z, "zhat", torch.float64).value for _, _, z in entries])
+    ctx.check(ctx.lib.geo_predict_batch(ctx.handle, count, facs, locs, ms, outs, _stream(stream)))
+    return [z for _, _, z in entries]
 
 
 def geo_simulate(ctx: Context, locs, e, theta: Theta, out, options: geo_opts | None = None, stream=None):

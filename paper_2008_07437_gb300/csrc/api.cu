@@ -52,6 +52,9 @@ struct geo_ctx {
     size_t bws_bytes = 0, bdesc_cap = 0;
     std::map<std::tuple<int, int, int>, std::pair<cudaGraphExec_t, long long>> graphs;   // -> (exec, kernel nodes)
     std::vector<int> border;            // problem orders of the cached ticket table
+    // batched predictions: descriptors (device + pinned staging)
+    void *pdesc_d = nullptr, *pdesc_h = nullptr;
+    size_t pdesc_cap = 0;
     std::vector<unsigned char> bunits;  // cached ticket table (16 bytes per unit)
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture (the legacy stream cannot capture)
     std::vector<geo_factor *> factors;
@@ -457,6 +460,8 @@ int geo_destroy(geo_ctx *ctx) {
     if (ctx->bws) dev_free(ctx, ctx->bws, ctx->bws_bytes);
     if (ctx->bdesc_d) cudaFree(ctx->bdesc_d);
     if (ctx->bdesc_h) cudaFreeHost(ctx->bdesc_h);
+    if (ctx->pdesc_d) cudaFree(ctx->pdesc_d);
+    if (ctx->pdesc_h) cudaFreeHost(ctx->pdesc_h);
     if (ctx->st) cudaFree(ctx->st);
     if (ctx->res) cudaFree(ctx->res);
     if (ctx->sync) cudaFree(ctx->sync);
@@ -938,6 +943,24 @@ static int predict_var_tlr(geo_ctx *ctx, const geo_factor *f, const double *new_
     return done(GEO_OK);
 }
 
+// w = Sigma^-1 Z of a kept factor (computed once, on first use).
+static int ensure_weights(geo_ctx *ctx, geo_factor *f, cudaStream_t s) {
+    if (f->w) return GEO_OK;
+    int rc;
+    if (f->tlr && (rc = tlr_solve_buffers(ctx, *f->tlr, s))) return rc;
+    void *pw;
+    if ((rc = dev_alloc(ctx, &pw, sizeof(double) * f->N))) return rc;
+    f->w = (double *)pw;
+    if (f->tlr) {
+        CK(cudaMemcpyAsync(f->w, f->ybuf, sizeof(double) * f->N, cudaMemcpyDeviceToDevice, s));
+        CK(tlr_solve(*f->tlr, f->w, true, ctx->tws, ctx->tarena, s));
+        CK(cudaStreamSynchronize(s));   // the solve's descriptors sit in the shared pinned arena
+    } else {
+        CK(backward_solve(f->A, f->ld, f->N, f->A + f->N, f->ld, f->w, ctx->sync, &ctx->st->timeout, s));
+    }
+    return GEO_OK;
+}
+
 int geo_predict(geo_ctx *ctx, const geo_factor *factor, const double *new_locs_dev, int m, double *zhat_dev,
                 void *stream) {
     if (!ctx || !factor) return GEO_EINVAL;
@@ -948,21 +971,50 @@ int geo_predict(geo_ctx *ctx, const geo_factor *factor, const double *new_locs_d
     SetDevice sd(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     geo_factor *f = const_cast<geo_factor *>(factor);
-    if (!f->w) {
-        int rc;
-        if (f->tlr && (rc = tlr_solve_buffers(ctx, *f->tlr, s))) return rc;
-        void *pw;
-        if ((rc = dev_alloc(ctx, &pw, sizeof(double) * f->N))) return rc;
-        f->w = (double *)pw;
-        if (f->tlr) {
-            CK(cudaMemcpyAsync(f->w, f->ybuf, sizeof(double) * f->N, cudaMemcpyDeviceToDevice, s));
-            CK(tlr_solve(*f->tlr, f->w, true, ctx->tws, ctx->tarena, s));
-            CK(cudaStreamSynchronize(s));   // the solve's descriptors sit in the shared pinned arena
-        } else {
-            CK(backward_solve(f->A, f->ld, f->N, f->A + f->N, f->ld, f->w, ctx->sync, &ctx->st->timeout, s));
-        }
-    }
+    if (int rc = ensure_weights(ctx, f, s)) return rc;
     CK(launch_predict(f->cp, new_locs_dev, m, f->lx, f->ly, f->n, f->w, zhat_dev, s));
+    return GEO_OK;
+}
+
+int geo_predict_batch(geo_ctx *ctx, int count, const geo_factor *const *factors, const double *const *new_locs_dev,
+                      const int *m, double *const *zhat_dev, void *stream) {
+    if (!ctx) return GEO_EINVAL;
+    ProfBind pb(&ctx->prof);
+    if (count <= 0 || !factors || !new_locs_dev || !m || !zhat_dev)
+        return fail(ctx, GEO_EINVAL, "count must be > 0 and arrays non-NULL");
+    SetDevice sd(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<PredDesc> h(count);
+    long long total = 0;
+    double flops = 0.0;
+    for (int k = 0; k < count; ++k) {
+        geo_factor *f = const_cast<geo_factor *>(factors[k]);
+        if (!f || m[k] < 0 || (m[k] > 0 && (!new_locs_dev[k] || !zhat_dev[k])))
+            return fail(ctx, GEO_EINVAL, "batch entry " + std::to_string(k) + ": bad factor, size or pointer");
+        if (int rc = ensure_weights(ctx, f, s)) return rc;
+        h[k] = PredDesc{f->cp, f->lx, f->ly, f->w, new_locs_dev[k], zhat_dev[k], f->n, m[k], (int)total};
+        total += m[k];
+        flops += 2.0 * f->p * (double)m[k] * f->p * (double)f->n;
+    }
+    if (total == 0) return GEO_OK;
+    if (total > (1LL << 31) - 1) return fail(ctx, GEO_EINVAL, "too many new locations");
+    const size_t bytes = sizeof(PredDesc) * (size_t)count;
+    if (ctx->pdesc_cap < bytes) {
+        CK(cudaStreamSynchronize(s));
+        if (ctx->pdesc_d) cudaFree(ctx->pdesc_d);
+        if (ctx->pdesc_h) cudaFreeHost(ctx->pdesc_h);
+        ctx->pdesc_d = ctx->pdesc_h = nullptr;
+        ctx->pdesc_cap = 0;
+        if (cudaMalloc(&ctx->pdesc_d, bytes) != cudaSuccess || cudaMallocHost(&ctx->pdesc_h, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, GEO_ENOMEM, "prediction descriptors");
+        }
+        ctx->pdesc_cap = bytes;
+    }
+    CK(cudaStreamSynchronize(s));   // the pinned staging buffer is reused by every call
+    memcpy(ctx->pdesc_h, h.data(), bytes);
+    CK(cudaMemcpyAsync(ctx->pdesc_d, ctx->pdesc_h, bytes, cudaMemcpyHostToDevice, s));
+    CK(launch_predict_batch((const PredDesc *)ctx->pdesc_d, count, (int)total, flops, s));
     return GEO_OK;
 }
 

@@ -162,6 +162,65 @@ cudaError_t launch_covgen_rect(const CovParams &cp, const double *l1, int n1, co
     return cudaGetLastError();
 }
 
+// Batched predictions: CTA g serves the new location g of the concatenation of
+// every entry's locations; it finds its entry by binary search over the
+// entries' first indices, copies the entry's theta constants into shared
+// memory and computes exactly what k_predict computes for that location (same
+// thread-to-r assignment, same reduction tree): bit-identical to one call per
+// factor.
+__global__ void __launch_bounds__(PRED_THREADS) k_predict_batch(const PredDesc *__restrict__ d, int count) {
+    __shared__ CovParams cps;
+    __shared__ int ent;
+    const int g = blockIdx.x;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = count - 1;   // the last entry with first <= g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (d[mid].first <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        ent = lo;
+    }
+    __syncthreads();
+    const PredDesc &q = d[ent];
+    {
+        const int words = (int)(sizeof(CovParams) / sizeof(int));
+        const int *src = reinterpret_cast<const int *>(&q.cp);
+        int *dst = reinterpret_cast<int *>(&cps);
+        for (int t = threadIdx.x; t < words; t += PRED_THREADS) dst[t] = src[t];
+    }
+    __syncthreads();
+    const CovParams &cp = cps;
+    const int l = g - q.first, n = q.n;
+    const double *lx = q.lx, *ly = q.ly, *w = q.w;
+    const double x0 = q.s0[2 * l], y0 = q.s0[2 * l + 1];
+    const int p = cp.p;
+    double acc[GEO_PMAX_DEV] = {0.0, 0.0, 0.0, 0.0};
+    double v[GEO_PMAX_DEV * GEO_PMAX_DEV];
+    for (int r = threadIdx.x; r < n; r += PRED_THREADS) {
+        const double dx = x0 - lx[r], dy = y0 - ly[r];
+        cov_block(cp, sqrt(dx * dx + dy * dy), v);
+        for (int i = 0; i < p; ++i) {
+            double t = 0.0;
+            for (int j = 0; j < p; ++j) t += v[i * GEO_PMAX_DEV + j] * w[(long long)p * r + j];
+            acc[i] += t;
+        }
+    }
+    __shared__ double red[GEO_PMAX_DEV][PRED_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = 0; i < p; ++i) {
+        double t = acc[i];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) red[i][wid] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < p) {
+        double t = 0.0;
+        for (int k = 0; k < PRED_THREADS / 32; ++k) t += red[threadIdx.x][k];
+        q.zhat[(long long)p * l + threadIdx.x] = t;
+    }
+}
+
 cudaError_t launch_predict(const CovParams &cp, const double *new_locs, int m, const double *lx,
                            const double *ly, int n, const double *w, double *zhat, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
@@ -193,5 +252,12 @@ cudaError_t launch_scatter_vec(const double *in, long long stride, const int *pe
     if (t <= 0) return cudaSuccess;
     KScope ks(GEO_K_AUX, s);
     k_scatter_vec<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(in, stride, perm, n, p, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_predict_batch(const PredDesc *d, int count, int total, double flops, cudaStream_t s) {
+    if (total <= 0) return cudaSuccess;
+    KScope ks(GEO_K_PREDICT, s, flops, 0.0);
+    k_predict_batch<<<total, PRED_THREADS, 0, s>>>(d, count);
     return cudaGetLastError();
 }

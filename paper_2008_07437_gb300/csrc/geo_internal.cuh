@@ -79,6 +79,17 @@ cudaError_t launch_covgen_rect(const CovParams &cp, const double *l1, int n1, co
 // zhat[p*l + i] = sum_{r,j} C_ij(|s0_l - s_r|) w[p*r + j]; s0 interleaved (x,y), s SoA.
 cudaError_t launch_predict(const CovParams &cp, const double *new_locs, int m, const double *lx,
                            const double *ly, int n, const double *w, double *zhat, cudaStream_t s);
+// One entry of a batched prediction: a factor's theta constants, locations (SoA, n), weights w
+// (p n), its m new locations s0 (AoS) and outputs zhat (p m); first = the entry's first global index.
+struct PredDesc {
+    CovParams cp;
+    const double *lx, *ly, *w;
+    const double *s0;
+    double *zhat;
+    int n, m, first;
+};
+// d: count device entries whose m sum to total; one CTA per new location.
+cudaError_t launch_predict_batch(const PredDesc *d, int count, int total, double flops, cudaStream_t s);
 // AoS (x, y) -> SoA gathered by perm (device ints).
 cudaError_t launch_gather_locs(const double *locs, const int *perm, int n, double *lx, double *ly,
                                cudaStream_t s);

@@ -11,6 +11,7 @@ Tolerances (all FP64; the arithmetic is the same up to rounding order):
 * cokriging predictions, entry by entry: |dz| <= 1e-8 (max |z| + |z|)
   (Sigma^-1 amplifies rounding by the condition number).
 """
+import ctypes
 import math
 
 import numpy as np
@@ -261,6 +262,48 @@ def test_predict_at_observed_locations_returns_data(ctx):
     finally:
         fac.free()
     np.testing.assert_allclose(got, np.concatenate([Z[0:2], Z[34:36], Z[598:600]]), atol=1e-8)
+
+
+def test_predict_batch_equals_single_calls_across_forms(ctx):
+    """geo_predict_batch over factors of different forms, orders and sizes gives,
+    bit for bit, what one geo_predict per factor gives, and matches the oracle."""
+    cases = [(TH2, 500, 61, geo.opts(nb=192), 1e-8),
+             (TH3, 300, 40, geo.opts(nb=128), 1e-8),
+             (TH2G, 700, 0, geo.opts(nb=128, fp64_gemm=1), 1e-8),          # no new locations
+             (TH2, 640, 129, geo.opts(nb=128, fp64_gemm=1), 1e-8),
+             (TH3, 600, 33, geo.opts(prec=geo.GEO_PREC_TLR, nb=120, tlr_tol=1e-9, tlr_kmax=120), 1e-6)]
+    facs, entries, refs = [], [], []
+    try:
+        for k, (theta, n, m, o, _) in enumerate(cases):
+            p = len(theta.sigma2)
+            allp = inputs.jittered_grid(n + m, 70 + k)
+            locs, new = allp[:n], allp[n:]
+            Z = oracle.simulate(o_theta(theta), allp, inputs.normals(80 + k, p * (n + m)))[: p * n]
+            refs.append(oracle.predict(o_theta(theta), locs, Z, new) if m else np.zeros(0))
+            _, fac = geo.geo_loglik(ctx, dev(locs), dev(Z), theta, o, keep=True)
+            facs.append(fac)
+            entries.append((fac, dev(new.reshape(m, 2)), torch.full((p * m,), float("nan"), dtype=torch.float64,
+                                                                     device="cuda")))
+        geo.geo_predict_batch(ctx, entries)
+        got = [z.cpu().numpy() for _, _, z in entries]
+        for k, (fac, new, z) in enumerate(entries):
+            if new.shape[0] == 0:
+                continue
+            single = torch.full_like(z, float("nan"))
+            geo.geo_predict(ctx, fac, new, single)
+            assert np.array_equal(got[k], single.cpu().numpy()), "entry %d differs from geo_predict" % k
+            assert_pred_close(got[k], refs[k], cases[k][4])
+        # a NULL factor in entry 1 is refused by name, before anything runs
+        lib, vp = ctx.lib, ctypes.c_void_p
+        fa = (vp * 2)(entries[0][0].handle, None)
+        la = (vp * 2)(entries[0][1].data_ptr(), entries[1][1].data_ptr())
+        ma = (ctypes.c_int * 2)(entries[0][1].shape[0], entries[1][1].shape[0])
+        za = (vp * 2)(entries[0][2].data_ptr(), entries[1][2].data_ptr())
+        assert lib.geo_predict_batch(ctx.handle, 2, fa, la, ma, za, None) == geo.GEO_EINVAL
+        assert b"batch entry 1" in lib.geo_last_error(ctx.handle)
+    finally:
+        for f in facs:
+            f.free()
 
 
 # ---------------------------------------------------------------- simulate --
