@@ -24,6 +24,7 @@ value = evaluations of all ranks / max over ranks of the timed region.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -143,6 +144,11 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="serving: skip the tile-size autotuner")
     ap.add_argument("--batch-count", type=int, default=512, help="batch: problems per call")
     ap.add_argument("--mle", type=int, default=0, help="run this many Nelder-Mead steps instead of evaluations")
+    ap.add_argument("--mle-checkpoint", default="",
+                    help="MLE: save the Nelder-Mead state and the step times here after every step, and resume "
+                         "from it when the file exists")
+    ap.add_argument("--mle-budget-s", type=float, default=0.0,
+                    help="MLE: stop (state saved) before a step that would end after this many seconds")
     ap.add_argument("--profile-lik", action="store_true",
                     help="mle: optimise the profile likelihood (marginal variances estimated, Sec. 4.2)")
     ap.add_argument("--mloe-m", type=int, default=100, help="mloe: prediction locations")
@@ -165,6 +171,9 @@ def parse():
                          "emulated-FP64 l of the same Z")
     ap.add_argument("--oracle-subset", type=int, default=0,
                     help="also compare l with the oracle on the first this-many locations (0 = off)")
+    ap.add_argument("--oz-cut", type=int, default=-1, choices=[-1, 0, 1],
+                    help="emulated FP64 workloads: magnitude-aware level cut in the trailing updates "
+                         "(-1: the workload's setting)")
     ap.add_argument("--dst", type=int, default=0,
                     help="tile low-rank workloads: Diagonal Super Tile, keep this many tile diagonals (Sec. 3.4)")
     return ap.parse_args()
@@ -185,6 +194,9 @@ def workload(args):
     if args.dst > 0 and w.extra.get("prec") == 2:
         w = inputs.Workload(w.name + "-dst%d" % args.dst, w.n, w.theta, n_pred=w.n_pred, nb=w.nb,
                             loc_seed=w.loc_seed, z_seed=w.z_seed, extra=dict(w.extra, dst=args.dst))
+    if args.oz_cut >= 0 and w.extra.get("fp64_gemm") == 1 and args.oz_cut != w.extra.get("oz_cut", 0):
+        w = inputs.Workload(w.name + ("-cut" if args.oz_cut else "-nocut"), w.n, w.theta, n_pred=w.n_pred, nb=w.nb,
+                            loc_seed=w.loc_seed, z_seed=w.z_seed, extra=dict(w.extra, oz_cut=args.oz_cut))
     return w
 
 
@@ -357,8 +369,10 @@ def config_json(w, args):
         S = w.extra.get("oz_slices", 8)
         form = ("dense tiled Cholesky, FP64 diagonal tiles (native POTRF and inversion); trailing updates and panel "
                 "solves on the BF16 tensor cores: %d 7-bit digit slices per operand row with a power-of-two row "
-                "scale, exact FP32 accumulation, FP64 recombination (%s)"
-                % (S, "FP64-class accuracy" if S >= 8 else "about %d bits per operand" % (7 * S)))
+                "scale, exact FP32 accumulation, FP64 recombination (%s)%s"
+                % (S, "FP64-class accuracy" if S >= 8 else "about %d bits per operand" % (7 * S),
+                   "; level cut: each trailing-update tile keeps the digit levels its operands' magnitudes need "
+                   "against the update's largest rows" if w.extra.get("oz_cut") else ""))
     return {"workload": w.name, "n": w.n, "p": p, "N": p * w.n, "nb": w.nb, "n_pred": w.n_pred,
             "form": form, "theta": {"sigma2": list(w.theta.sigma2), "a": w.theta.a,
                                                            "nu": list(w.theta.nu), "beta": list(w.theta.beta)},
@@ -578,11 +592,11 @@ def run_ours(args):
     fp64eq_tflops = None
     kname = (TLR_KERNEL_NAMES if tlr else KERNEL_NAMES).get(dom, dom)
     if dom == "tcgemm" and emulated:
-        # the class counts FP64-equivalent flops (2 K per output); the tensor cores
-        # run S (S + 1) / 2 digit products of that size
-        S = w.extra.get("oz_slices", 8)
+        # the class counts FP64-equivalent flops (2 K per output); the tensor-core work is
+        # what the kernels issued (counted on the device): S (S + 1) / 2 digit products of
+        # that size per output without the level cut, fewer with it
         fp64eq_tflops = dom_tflops
-        dom_tflops *= S * (S + 1) / 2.0
+        dom_tflops = dk["tensor_flops"] / (dk["ms"] * 1e-3) / 1e12 if dk["ms"] > 0 else 0.0
         kname = KERNEL_NAMES["oz"]
     # Cholesky rate: N^3 / 3 over the step's time outside covariance generation,
     # reductions, solves and prediction (the lookahead overlaps the classes)
@@ -593,10 +607,7 @@ def run_ours(args):
     # (N = 8,000) measured 0.822 x the algorithmic bytes; scaled to this run's
     # average launch (FP64 update kernel only)
     traffic = 0.822 * dk["bytes"] / max(dk["launches"], 1) if dom == "gemm" and not tlr else None
-    if dom == "tcgemm" and emulated:
-        # k_oz_update: an ncu capture of every launch of one emulated evaluation at N = 16,000 measured
-        # 1.70 x the algorithmic bytes (16 B per output, the digit slices); scaled to this run's launches
-        traffic = 1.70 * dk["bytes"] / max(dk["launches"], 1)
+    # k_oz_update: no DRAM counters of the current kernel yet (null until a capture is taken)
     dtype = "f64"
     if emulated:
         dtype = "f64 (emulated: bf16 digit products, exact fp32 accumulation, %d slices)" % w.extra.get("oz_slices", 8)
@@ -879,6 +890,25 @@ def theta_rel_error(best, spec):
             "beta_abs": [abs(e - t) for e, t in zip(est_b, true_b)]}
 
 
+def _mle_load(path, geo):
+    """Nelder-Mead state and step records saved by an earlier run, or None."""
+    if not path or not os.path.exists(path):
+        return None, []
+    with open(path, "rb") as f:
+        blob = f.read()
+    size = ctypes.sizeof(geo.geo_mle_state)
+    st = geo.geo_mle_state.from_buffer_copy(blob[:size])
+    return st, json.loads(blob[size:].decode())
+
+
+def _mle_save(path, st, records):
+    tmp = path + ".tmp"
+    with open(tmp, "wb") as f:
+        f.write(bytes(st))
+        f.write(json.dumps(records).encode())
+    os.replace(tmp, path)
+
+
 def run_mle(args, w, ctx, d_locs, d_z, theta, o, dev):
     import torch
 
@@ -887,25 +917,42 @@ def run_mle(args, w, ctx, d_locs, d_z, theta, o, dev):
     # start: a x 1.3, nu x 0.9, sigma^2 x 1.1, beta x 0.8
     th0 = geo.Theta(tuple(1.1 * v for v in spec.sigma2), 1.3 * spec.a, tuple(0.9 * v for v in spec.nu),
                     tuple(0.8 * v for v in spec.beta) if spec.p > 1 else None)
-    st = geo.geo_mle_init(th0, profile=args.profile_lik)
+    st, records = _mle_load(args.mle_checkpoint, geo)
+    resumed = len(records)
+    if st is None:
+        st = geo.geo_mle_init(th0, profile=args.profile_lik)
     ll_true, _ = geo.geo_loglik(ctx, d_locs, d_z, theta, o)
     torch.cuda.synchronize()
     clocks = ClockSampler(dev.index)
     clocks.start()
-    t0 = time.perf_counter()
-    traj = []
-    for _ in range(args.mle):
+    t_call = time.perf_counter()
+    while len(records) < args.mle:
+        if args.mle_budget_s > 0 and records:
+            longest = max(r["seconds"] for r in records)
+            if time.perf_counter() - t_call + longest > args.mle_budget_s:
+                break
+        t0 = time.perf_counter()
+        ev0 = st.evals
         geo.geo_mle_step(ctx, st, d_locs, d_z, o)
-        traj.append(geo.geo_mle_best(st)[1])
-    torch.cuda.synchronize()
-    t = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        records.append({"step": len(records) + 1, "seconds": time.perf_counter() - t0,
+                        "evals": st.evals - ev0, "best_loglik": geo.geo_mle_best(st)[1]})
+        if args.mle_checkpoint:
+            _mle_save(args.mle_checkpoint, st, records)
+        print("mle step %d: %.1f s, %d evaluations, best %.6f" % (
+            records[-1]["step"], records[-1]["seconds"], records[-1]["evals"], records[-1]["best_loglik"]),
+            file=sys.stderr, flush=True)
     clk = clocks.stop()
+    t = sum(r["seconds"] for r in records)
     best, ll = geo.geo_mle_best(st)
-    out = {"metric": "MLE wall time", "value": t, "unit": "s", "n_gpus": 1, "steps": args.mle, "warmup": 0,
-           "ms_per_step": 1e3 * t / args.mle, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64", "data": "synthetic", "config": config_json(w, args),
-           "evals": st.evals, "evals_per_s": st.evals / t, "loglik_at_truth": ll_true,
-           "best_loglik": ll, "best_loglik_by_step": traj,
+    out = {"metric": "MLE wall time", "value": t, "unit": "s", "n_gpus": 1, "steps": len(records), "warmup": 0,
+           "ms_per_step": 1e3 * t / max(len(records), 1), "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_json(w, args),
+           "complete": len(records) >= args.mle, "steps_requested": args.mle,
+           "resumed_after_step": resumed,
+           "evals": st.evals, "evals_per_s": st.evals / t if t > 0 else None, "loglik_at_truth": ll_true,
+           "best_loglik": ll, "best_loglik_by_step": [r["best_loglik"] for r in records],
+           "seconds_by_step": [r["seconds"] for r in records], "evals_by_step": [r["evals"] for r in records],
            "best_theta": {"sigma2": list(best.sigma2), "a": best.a, "nu": list(best.nu),
                           "beta": [float(b) for b in np.asarray(best.beta).ravel()]},
            "start_theta": {"sigma2": list(th0.sigma2), "a": th0.a, "nu": list(th0.nu)},

@@ -96,7 +96,13 @@ typedef struct {
     int oz_slices;      /* fp64_gemm = 1: digits per operand, 3..8 (0 = 8).  An update then carries a
                            relative error of about 2^(-7 oz_slices) of max|a_r| max|b_c| per product
                            term (8 slices: below FP64's 2^-53 rounding; 5 slices: ~2^-35) */
-    int reserved[5];
+    int oz_cut;         /* fp64_gemm = 1: 1 = magnitude-aware level cut in the trailing updates: an
+                           output tile keeps only the digit levels whose products reach
+                           2^-(7 oz_slices) of the update's largest products (from the per-row
+                           exponents), so tiles of small entries (far from the diagonal) cost less
+                           or nothing; every entry's error stays within that of the largest
+                           products.  0 = every tile keeps all levels (default) */
+    int reserved[4];
 } geo_opts;
 
 typedef struct geo_ctx geo_ctx;
@@ -515,6 +521,8 @@ typedef struct {
     double flops;     /* algorithmic floating-point operations */
     double bytes;     /* algorithmic HBM bytes */
     long long timed;  /* launches with events */
+    double tensor_flops; /* GEO_K_TCGEMM: BF16 tensor-core flops the emulated products issued (counted
+                            on the device; the level cut lowers it), 0 for the other classes */
 } geo_kstat;
 
 int geo_profile_enable(geo_ctx *ctx, int enable);

@@ -41,7 +41,7 @@ class geo_opts(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int), ("prec", ctypes.c_int), ("band", ctypes.c_int), ("lowp", ctypes.c_int),
                 ("refine_iters", ctypes.c_int), ("tlr_tol", ctypes.c_double), ("tlr_kmax", ctypes.c_int),
                 ("morton", ctypes.c_int), ("fp64_gemm", ctypes.c_int), ("dst", ctypes.c_int),
-                ("oz_slices", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("oz_slices", ctypes.c_int), ("oz_cut", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class geo_factor_stats(ctypes.Structure):
@@ -86,7 +86,7 @@ class geo_result(ctypes.Structure):
 
 class geo_kstat(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("ms", ctypes.c_double), ("flops", ctypes.c_double),
-                ("bytes", ctypes.c_double), ("timed", ctypes.c_longlong)]
+                ("bytes", ctypes.c_double), ("timed", ctypes.c_longlong), ("tensor_flops", ctypes.c_double)]
 
 
 # every symbol include/geo.h declares, with (restype, argtypes)
@@ -457,7 +457,7 @@ def geo_profile_read(ctx: Context) -> dict:
     arr = (geo_kstat * GEO_K_COUNT)()
     ctx.check(ctx.lib.geo_profile_read(ctx.handle, arr))
     return {GEO_K_NAMES[k]: dict(launches=arr[k].launches, ms=arr[k].ms, flops=arr[k].flops,
-                                 bytes=arr[k].bytes, timed=arr[k].timed) for k in range(GEO_K_COUNT)}
+                                 bytes=arr[k].bytes, timed=arr[k].timed, tensor_flops=arr[k].tensor_flops) for k in range(GEO_K_COUNT)}
 
 
 def _check_noalloc_args(locs, z, theta: Theta, out, info) -> int:

@@ -431,7 +431,9 @@ int geo_create(geo_ctx **out, int device, size_t hbm_budget_bytes) {
         cudaMalloc(&ctx->res, sizeof(DevResults)) != cudaSuccess ||
         cudaMalloc(&ctx->sync, 4 * sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_st, sizeof(DevStatus)) != cudaSuccess ||
-        cudaMallocHost(&ctx->h_res, sizeof(DevResults)) != cudaSuccess) {
+        cudaMallocHost(&ctx->h_res, sizeof(DevResults)) != cudaSuccess ||
+        cudaMalloc(&ctx->prof.d_tc_flops, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(ctx->prof.d_tc_flops, 0, sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         geo_destroy(ctx);
         return GEO_ECUDA;
@@ -446,6 +448,7 @@ int geo_destroy(geo_ctx *ctx) {
     cudaDeviceSynchronize();
     while (!ctx->factors.empty()) geo_factor_free(ctx->factors.back());
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
+    if (ctx->prof.d_tc_flops) cudaFree(ctx->prof.d_tc_flops);
     if (ctx->ws) dev_free(ctx, ctx->ws, ctx->ws_bytes);
     if (ctx->mws) dev_free(ctx, ctx->mws, ctx->mws_bytes);
     if (ctx->ows) dev_free(ctx, ctx->ows, ctx->ows_bytes);
@@ -504,6 +507,7 @@ static int check_dense_opts(geo_ctx *ctx, const geo_opts &o) {
     if (o.fp64_gemm != 0 && o.fp64_gemm != 1) return fail(ctx, GEO_EINVAL, "fp64_gemm must be 0 or 1");
     if (o.fp64_gemm == 1 && (o.oz_slices != 0 && (o.oz_slices < 3 || o.oz_slices > 8)))
         return fail(ctx, GEO_EINVAL, "oz_slices must be 0 (default 8) or 3..8");
+    if (o.oz_cut != 0 && o.oz_cut != 1) return fail(ctx, GEO_EINVAL, "oz_cut must be 0 or 1");
     if (o.fp64_gemm == 1 && (o.nb % 64 != 0 || o.nb > 1024))
         return fail(ctx, GEO_EINVAL, "fp64_gemm = 1 needs nb a multiple of 64, at most 1024");
     return GEO_OK;
@@ -522,7 +526,7 @@ static int dense_factor(geo_ctx *ctx, double *A, long long ld, int N, int nrows,
     const int S = oz_slices_of(o);
     int rc = ensure_buffer(ctx, &ctx->ows, &ctx->ows_bytes, oz_chol_workspace_bytes(nrows, o.nb, S), s);
     if (rc) return rc;
-    *err = chol_oz_factor(A, ld, N, nrows, o.nb, S, ctx->ows, ctx->ows_bytes, ctx->st, s);
+    *err = chol_oz_factor(A, ld, N, nrows, o.nb, S, o.oz_cut, ctx->ows, ctx->ows_bytes, ctx->st, s);
     return GEO_OK;
 }
 
@@ -1588,6 +1592,7 @@ int geo_profile_enable(geo_ctx *ctx, int enable) {
     if (enable) {
         cudaDeviceSynchronize();
         ctx->prof.clear();
+        if (ctx->prof.d_tc_flops) cudaMemset(ctx->prof.d_tc_flops, 0, sizeof(unsigned long long));
     }
     ctx->prof.enabled = enable != 0;
     return GEO_OK;
@@ -1604,7 +1609,12 @@ int geo_profile_read(geo_ctx *ctx, geo_kstat *out) {
         out[k].flops = ctx->prof.flops[k];
         out[k].bytes = ctx->prof.bytes[k];
         out[k].timed = ctx->prof.timed[k];
+        out[k].tensor_flops = 0.0;
     }
+    unsigned long long tc = 0;
+    if (ctx->prof.d_tc_flops)
+        CK(cudaMemcpy(&tc, ctx->prof.d_tc_flops, sizeof(tc), cudaMemcpyDeviceToHost));
+    out[GEO_K_TCGEMM].tensor_flops = (double)tc;
     return GEO_OK;
 }
 

@@ -41,6 +41,7 @@ struct Profiler {
     double flops[GEO_K_COUNT] = {};
     double bytes[GEO_K_COUNT] = {};
     double ms[GEO_K_COUNT] = {};
+    unsigned long long *d_tc_flops = nullptr;   // device counter: tensor-core flops of the emulated products
     struct Rec {
         int cls;
         cudaEvent_t a, b;
@@ -127,6 +128,9 @@ struct OzSlices {
     long long rows;           // capacity: row stride of the exponent array
     long long valid;          // rows holding data (extent of the tensor maps)
     long long slice_stride;   // elements between slices
+    int *be;                  // per 32-row block exponent maxima: 2 nchunk x bstride (all rows, reference rows)
+    long long bstride;
+    long long ref_rows;       // rows that set the level cut's reference scale (-1: every sliced row)
 };
 // Depth of one exact-accumulation launch: S * kmax * 2^12 <= 2^24.
 int oz_kmax(int S);
@@ -136,15 +140,16 @@ OzSlices oz_slices_carve(void *ws, long long rows, int K, int S);
 cudaError_t oz_slice(const double *P, long long ld, int R, const OzSlices &o, const DevStatus *st, cudaStream_t s);
 // C[r0 + i, c0 + j] -= sum_k A[a_off + i, k] B[b_off + j, k] for i < rows, j < cols, written only
 // where the global row < m_end and col < n_end (and row >= col when tri); grid_cap persistent CTAs.
-// overwrite = 1: C = -sum (C is not read).
+// overwrite = 1: C = -sum (C is not read).  cut = 1: each output tile keeps only the digit levels
+// its operands' magnitudes need against the launch's largest rows (not with overwrite).
 cudaError_t oz_update(const OzSlices &A, const OzSlices &B, double *C, long long ldc, int r0, int c0, int rows,
                       int cols, int m_end, int n_end, int a_off, int b_off, int tri, int grid_cap, DevStatus *st,
-                      cudaStream_t s, int overwrite);
+                      cudaStream_t s, int overwrite, int cut);
 size_t oz_chol_workspace_bytes(int nrows, int nb, int S);
 // Dense Cholesky as chol64_factor, trailing updates and panel solves on the
-// tensor cores with S slices (nb <= 1024).
-cudaError_t chol_oz_factor(double *A, long long ld, int N, int nrows, int nb, int S, void *ws, size_t ws_bytes,
-                           DevStatus *st, cudaStream_t s);
+// tensor cores with S slices (nb <= 1024); cut = 1: the trailing updates use the level cut.
+cudaError_t chol_oz_factor(double *A, long long ld, int N, int nrows, int nb, int S, int cut, void *ws,
+                           size_t ws_bytes, DevStatus *st, cudaStream_t s);
 size_t oz_gemm_workspace_bytes(int m, int n, int k, int S);
 // C (m x n) -= A (m x k) B (n x k)', column-major FP64, S slices.
 cudaError_t oz_gemm(int m, int n, int k, const double *A, long long lda, const double *B, long long ldb, double *C,

@@ -29,6 +29,18 @@
 //               C -= 2^(e_r + e_c) sum_w W_w 2^(2 - 7 hi_w), hi_w the last
 //               level of group w, with one FP64 FMA per group.
 //
+//   level cut  (optional, trailing updates of the factorisation) the levels
+//               kept for an output tile follow its operands' magnitudes: with
+//               E the largest row exponent of the launch's A rows plus that of
+//               its B rows, and e_i + e_j the same over the tile's own rows,
+//               the tile keeps the levels l <= S + 1 - floor((E - e_i - e_j) / 7).
+//               A dropped level of such a tile is below 2^(E - 7(S + 1)) times
+//               the digit-product sum, the size of the first level every tile
+//               drops anyway, so each entry's error stays within the bound of
+//               the launch's largest products; tiles whose operands are tiny
+//               against the launch's largest (far from the diagonal in a
+//               spatially ordered covariance) skip levels or vanish entirely.
+//
 // The kernel is persistent (one CTA per SM) over 128 x BN output tiles, the
 // K range in chunks of BK.  TMEM (512 columns) holds 512 / BN level
 // accumulators of 128 x BN FP32: with BN = 64 all eight levels of 8 slices
@@ -68,6 +80,7 @@ constexpr int OZ_TMEM_COLS = 512;
 constexpr int OZ_SMEM_CAP = 225 * 1024;
 constexpr int OZ_GROUP = 8;       // row blocks swept together (operand reuse in L2)
 constexpr int OZ_LPW = 4;         // levels folded into one 64-bit word
+constexpr int OZ_E_NONE = -4096;  // block exponent of rows that are all zero (or absent)
 
 // Tile width BN (MMA N), K chunk BK (16: 32-byte rows, 32-byte swizzle; 32:
 // 64-byte rows, 64-byte swizzle).  TMEM holds 512 / BN level accumulators, so
@@ -108,8 +121,25 @@ struct OzArgs {
     int a_off, b_off;    // slice row of the region's first row (A) / first column (B)
     int nk;              // K chunks of BK
     const int *ea, *eb;  // per-row exponents of the A / B slices
+    // level cut: per 32-row block maxima of the row exponents over every row (ba, bb) and over the
+    // reference rows (ra, rb) of the A / B slices, nba / nbb blocks; cut = 0 keeps every level
+    const int *ba, *bb, *ra, *rb;
+    int nba, nbb, cut;
+    unsigned long long *tc_flops;   // tensor-core flops issued, summed over CTAs (may be NULL)
     DevStatus *st;
 };
+
+// Highest level an output tile keeps (< 2: the tile is skipped); eref = E_A + E_B.
+template <int S, int BN>
+__device__ __forceinline__ int oz_lcut(const OzArgs &a, int ar, int br, int eref) {
+    if (!a.cut) return S + 1;
+    int ei = OZ_E_NONE, ej = OZ_E_NONE;
+    const int a1 = min((ar + OZ_BM - 1) >> 5, a.nba - 1), b1 = min((br + BN - 1) >> 5, a.nbb - 1);
+    for (int b = ar >> 5; b <= a1; ++b) ei = max(ei, a.ba[b]);
+    for (int b = br >> 5; b <= b1; ++b) ej = max(ej, a.bb[b]);
+    if (ei == OZ_E_NONE || ej == OZ_E_NONE) return 1;   // every row of one side is zero: nothing to add
+    return S + 1 - max(0, eref - ei - ej) / 7;
+}
 
 template <int BN>
 __device__ __forceinline__ bool oz_tile(const OzArgs &a, long long L, int *gr, int *gc, int *ar, int *br) {
@@ -162,13 +192,31 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     constexpr int NSLOT = OZ_TMEM_COLS / BN;   // accumulator slots of BN columns
     __shared__ uint64_t full_bar[ST], empty_bar[ST], acc_full, slot_empty[NSLOT], drain_bar;
     __shared__ uint32_t tmem_slot;
-    __shared__ int skip;
+    __shared__ int skip, emax_a, emax_b;
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     // one read for the whole CTA: a factorisation step on another stream may set it meanwhile
-    if (threadIdx.x == 0) skip = *(volatile const int *)&args.st->info;
+    if (threadIdx.x == 0) {
+        skip = *(volatile const int *)&args.st->info;
+        emax_a = emax_b = OZ_E_NONE;
+    }
     __syncthreads();
     if (skip) return;   // an earlier step failed
+    if (args.cut) {   // the launch's reference exponents E_A, E_B
+        int ma = OZ_E_NONE, mb = OZ_E_NONE;
+        for (int b = threadIdx.x; b < args.nba; b += OZ_THREADS) ma = max(ma, args.ra[b]);
+        for (int b = threadIdx.x; b < args.nbb; b += OZ_THREADS) mb = max(mb, args.rb[b]);
+        for (int o = 16; o > 0; o >>= 1) {
+            ma = max(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+            mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+        }
+        if (lane == 0) {
+            atomicMax(&emax_a, ma);
+            atomicMax(&emax_b, mb);
+        }
+        __syncthreads();
+    }
+    const int eref = emax_a + emax_b;
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const long long ntiles = (long long)args.mt * args.nt;
 
@@ -202,9 +250,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             for (long long L = blockIdx.x; L < ntiles && ok; L += gridDim.x) {
                 int gr, gc, ar, br;
                 if (!oz_tile<BN>(args, L, &gr, &gc, &ar, &br)) continue;
+                const int lc = oz_lcut<S, BN>(args, ar, br, eref);
 #pragma unroll
                 for (int ps = 0; ps < PASSES; ++ps) {
-                    const int tm = Cfg::tmax(ps);
+                    if (Cfg::lev_lo(ps) > lc) break;   // every level of this pass (and later ones) is cut
+                    const int tm = min(Cfg::tmax(ps), lc - 1);
                     for (int kb = 0; kb < args.nk && ok; ++kb, ++g) {
                         const int s = (int)(g % ST);
                         if (g >= ST && !mbar_wait(&empty_bar[s], (uint32_t)(((g / ST) & 1) ^ 1), tword, 21)) {
@@ -232,13 +282,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             int use[NSLOT];   // jobs that have used each accumulator slot so far
 #pragma unroll
             for (int j = 0; j < NSLOT; ++j) use[j] = 0;
+            unsigned long long nmma = 0;
             bool ok = true;
             for (long long L = blockIdx.x; L < ntiles && ok; L += gridDim.x) {
                 int gr, gc, ar, br;
                 if (!oz_tile<BN>(args, L, &gr, &gc, &ar, &br)) continue;
+                const int lc = oz_lcut<S, BN>(args, ar, br, eref);
 #pragma unroll
                 for (int ps = 0; ps < PASSES; ++ps) {
-                    if (!ok) break;
+                    if (!ok || Cfg::lev_lo(ps) > lc) break;
+                    // every slot of the pass takes part in the release protocol; only levels <= lc get MMAs
                     const int llo = Cfg::lev_lo(ps), lhi = Cfg::lev_hi(ps);
                     for (int kb = 0; kb < args.nk; ++kb, ++g) {
                         const int s = (int)(g % ST);
@@ -264,6 +317,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                                     }
                                     fence_after_sync();
                                 }
+                                if (l > lc) continue;
+                                nmma += (unsigned long long)(thi - tlo + 1);
 #pragma unroll
                                 for (int t = tlo; t <= thi; ++t) {
                                     const int u = l - t;
@@ -289,6 +344,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             // every MMA issued so far has completed before TMEM can be freed
             mma_commit(&drain_bar);
             mbar_wait(&drain_bar, 0, tword, 26);
+            if (args.tc_flops) atomicAdd(args.tc_flops, nmma * (unsigned long long)(2 * OZ_BM * BN * 16));
         }
         __syncwarp();
     } else {
@@ -300,10 +356,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         for (long long L = blockIdx.x; L < ntiles && ok; L += gridDim.x) {
             int gr, gc, ar, br;
             if (!oz_tile<BN>(args, L, &gr, &gc, &ar, &br)) continue;
+            const int lc = oz_lcut<S, BN>(args, ar, br, eref);
             const int grow = gr + row;
             const int er = (grow < args.m_end) ? args.ea[ar + row] : 0;
 #pragma unroll
             for (int ps = 0; ps < PASSES; ++ps) {
+                if (Cfg::lev_lo(ps) > lc) break;
                 ok = mbar_wait(&acc_full, (uint32_t)(job & 1), tword, 24);
                 ok = __all_sync(0xffffffffu, ok);   // every lane takes part in tcgen05.ld
                 if (!ok) break;
@@ -316,6 +374,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                     if (l < llo || l > lhi) continue;
                     const int wi = (l - 2) / OZ_LPW - w0;   // word of this level within the pass
                     const bool first = ((l - 2) % OZ_LPW) == 0;
+                    const bool live = l <= lc;   // a cut level's slot holds stale values: taken as 0
 #pragma unroll
                     for (int c32 = 0; c32 < CPT / 32; ++c32) {
                         float v[32];
@@ -329,7 +388,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                         }
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
-                            const long long d = (long long)__float2int_rn(v[j]);   // an exact integer below 2^24
+                            const long long d = live ? (long long)__float2int_rn(v[j]) : 0;   // exact, below 2^24
                             acc[wi][c32 * 32 + j] = first ? d : acc[wi][c32 * 32 + j] * 128 + d;
                         }
                     }
@@ -346,7 +405,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                         double c = over ? 0.0 : *pc;
 #pragma unroll
                         for (int wi = WREG - 1; wi >= 0; --wi) {
-                            if (w0 + wi >= Cfg::NWT) continue;
+                            if (w0 + wi >= Cfg::NWT || 2 + OZ_LPW * (w0 + wi) > lc) continue;
                             c = fma(-(double)acc[wi][j], pow2i(e + 2 - 7 * Cfg::word_hi(w0 + wi)), c);
                         }
                         *pc = c;
@@ -368,11 +427,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 // [k0, k0 + kc) for the K chunk blockIdx.y (kc = kchunk, the last one
 // shorter): slice t of row r at out[t * slice_stride + r * Kp + k] (BF16,
 // zero for k beyond the panel), the row exponent at exps[chunk * exp_stride + r].
+// Per 32-row block b the largest exponent of its non-zero rows goes to
+// bexps[2 chunk bstride + b], and that of its non-zero rows below ref_rows to
+// bexps[(2 chunk + 1) bstride + b] (OZ_E_NONE where there is none).
 // One CTA per 32 rows: a column sweep for the row maxima, then 32 x 32
 // tiles through shared memory so that each slice row is written along K.
 __global__ void __launch_bounds__(256) k_oz_slice(const double *P, long long ld, int R, int K, int kchunk, int S,
                                                   __nv_bfloat16 *out, long long slice_stride, int Kp, int *exps,
-                                                  long long exp_stride, const DevStatus *st) {
+                                                  long long exp_stride, int *bexps, long long bstride, int ref_rows,
+                                                  const DevStatus *st) {
     __shared__ double tile[32][33];
     __shared__ double red[8][32];
     __shared__ int ex[32];
@@ -397,6 +460,16 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double *P, long long ld,
         e = max(e, -960);
         ex[rr] = e;
         if (r0 + rr < R) exps[(long long)blockIdx.y * exp_stride + r0 + rr] = e;
+        const bool live = r0 + rr < R && m > 0.0;
+        int eall = live ? e : OZ_E_NONE, eref = (live && r0 + rr < ref_rows) ? e : OZ_E_NONE;
+        for (int o = 16; o > 0; o >>= 1) {
+            eall = max(eall, __shfl_xor_sync(0xffffffffu, eall, o));
+            eref = max(eref, __shfl_xor_sync(0xffffffffu, eref, o));
+        }
+        if (rr == 0) {
+            bexps[2LL * blockIdx.y * bstride + blockIdx.x] = eall;
+            bexps[(2LL * blockIdx.y + 1) * bstride + blockIdx.x] = eref;
+        }
     }
     __syncthreads();
     for (int c0 = kbeg; c0 < kpad_end; c0 += 32) {
@@ -479,7 +552,8 @@ int oz_kmax(int S) { return (4096 / S) / OZ_KALIGN * OZ_KALIGN; }
 size_t oz_slices_bytes(long long rows, int K, int S) {
     const long long Kp = (K + OZ_KALIGN - 1) / OZ_KALIGN * OZ_KALIGN;
     const int nchunk = (K + oz_kmax(S) - 1) / oz_kmax(S);
-    return (size_t)S * (size_t)rows * (size_t)Kp * 2 + sizeof(int) * (size_t)rows * nchunk + 512;
+    return (size_t)S * (size_t)rows * (size_t)Kp * 2 + sizeof(int) * (size_t)rows * nchunk +
+           sizeof(int) * 2 * (size_t)((rows + 31) / 32) * nchunk + 768;
 }
 
 OzSlices oz_slices_carve(void *ws, long long rows, int K, int S) {
@@ -495,6 +569,9 @@ OzSlices oz_slices_carve(void *ws, long long rows, int K, int S) {
     o.d = ws;
     uintptr_t e = (uintptr_t)ws + (size_t)S * o.slice_stride * 2;
     o.e = (int *)((e + 255) & ~(uintptr_t)255);
+    o.bstride = (rows + 31) / 32;
+    o.be = (int *)(((uintptr_t)(o.e + rows * o.nchunk) + 255) & ~(uintptr_t)255);
+    o.ref_rows = -1;
     return o;
 }
 
@@ -504,15 +581,17 @@ cudaError_t oz_slice(const double *P, long long ld, int R, const OzSlices &o, co
     dim3 grid((R + 31) / 32, o.nchunk);
     KScope ks(GEO_K_AUX, s, 0.0, (double)R * o.K * (16.0 + 2.0 * o.S));
     k_oz_slice<<<grid, 256, 0, s>>>(P, ld, R, o.K, o.kchunk, o.S, (__nv_bfloat16 *)o.d, o.slice_stride, o.Kp, o.e,
-                                    o.rows, st);
+                                    o.rows, o.be, o.bstride, o.ref_rows < 0 ? R : (int)std::min<long long>(o.ref_rows, R),
+                                    st);
     return cudaGetLastError();
 }
 
 cudaError_t oz_update(const OzSlices &A, const OzSlices &B, double *C, long long ldc, int r0, int c0, int rows,
                       int cols, int m_end, int n_end, int a_off, int b_off, int tri, int grid_cap, DevStatus *st,
-                      cudaStream_t s, int overwrite) {
+                      cudaStream_t s, int overwrite, int cut) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     if (A.S != B.S || A.K != B.K || A.S < 3 || A.S > 8) return cudaErrorInvalidValue;
+    if (cut && overwrite) return cudaErrorInvalidValue;   // a skipped tile would leave C unwritten
     const int S = A.S;
     OzArgs a;
     a.C = C;
@@ -529,6 +608,10 @@ cudaError_t oz_update(const OzSlices &A, const OzSlices &B, double *C, long long
     a.overwrite = 0;
     a.b_off = b_off;
     a.st = st;
+    a.cut = cut ? 1 : 0;
+    a.nba = (int)((A.valid + 31) / 32);
+    a.nbb = (int)((B.valid + 31) / 32);
+    a.tc_flops = t_prof ? t_prof->d_tc_flops : nullptr;
     const long long ntiles = (long long)a.mt * a.nt;
     const int grid = (int)std::min<long long>(ntiles, std::max(1, std::min(grid_cap, tc::num_sms())));
     // algorithmic work: 2 K flops per output written (lower triangle when tri)
@@ -539,6 +622,10 @@ cudaError_t oz_update(const OzSlices &A, const OzSlices &B, double *C, long long
         a.nk = (kc + sh.bk - 1) / sh.bk;
         a.ea = A.e + (long long)ch * A.rows;
         a.eb = B.e + (long long)ch * B.rows;
+        a.ba = A.be + 2LL * ch * A.bstride;
+        a.ra = a.ba + A.bstride;
+        a.bb = B.be + 2LL * ch * B.bstride;
+        a.rb = a.bb + B.bstride;
         CUtensorMap ma, mb;
         cudaError_t e;
         if ((e = slice_map(&ma, A, ch, OZ_BM, sh.bk)) != cudaSuccess ||
@@ -662,8 +749,8 @@ size_t oz_chol_workspace_bytes(int nrows, int nb, int S) {
 // emulated product, L_ik = A_ik L_kk^-T = -(A_ik W'), written over A_ik.
 // Every trailing update and panel solve is emulated; POTRF of the diagonal
 // tiles and their inversion are native FP64, and so is the last panel.
-cudaError_t chol_oz_factor(double *A, long long ld, int N, int nrows, int nb, int S, void *ws, size_t ws_bytes,
-                           DevStatus *st, cudaStream_t s) {
+cudaError_t chol_oz_factor(double *A, long long ld, int N, int nrows, int nb, int S, int cut, void *ws,
+                           size_t ws_bytes, DevStatus *st, cudaStream_t s) {
     constexpr int SIDE_SMS = 8;
     if (nb < 64 || nb % 64 != 0 || nb > TRTRI_THREADS * TRTRI_RPT || S < 3 || S > 8) return cudaErrorInvalidValue;
     if (ws_bytes < oz_chol_workspace_bytes(nrows, nb, S)) return cudaErrorInvalidValue;
@@ -697,7 +784,7 @@ cudaError_t chol_oz_factor(double *A, long long ld, int N, int nrows, int nb, in
         if ((r = oz_slice(A + (long long)t0 * ld + x0, ld, x1 - x0, p, st, st_)) != cudaSuccess ||
             (r = oz_slice(W, nb, jb, q, st, st_)) != cudaSuccess)
             return r;
-        return oz_update(p, q, A, ld, x0, t0, x1 - x0, jb, x1, t0 + jb, 0, 0, 0, all, st, st_, 1);
+        return oz_update(p, q, A, ld, x0, t0, x1 - x0, jb, x1, t0 + jb, 0, 0, 0, all, st, st_, 1, 0);
     };
     // native FP64 factorisation of the diagonal tile [t0, t0 + jb) and its inverse
     auto diag = [&](int t0, int jb, cudaStream_t st_) -> cudaError_t {
@@ -720,10 +807,11 @@ cudaError_t chol_oz_factor(double *A, long long ld, int N, int nrows, int nb, in
             p.K = jb;
             p.nchunk = (jb + p.kchunk - 1) / p.kchunk;
             p.valid = nrows - t0;
+            p.ref_rows = N - t0;   // the reference scale is the matrix's, not the right-hand side rows'
             if ((r = oz_slice(A + (long long)j0 * ld + t0, ld, nrows - t0, p, st, s)) != cudaSuccess) return r;
             const int n1 = std::min(N, t0 + nb);
             // the next panel's tile column: rows [t0, nrows), cols [t0, n1)
-            if ((r = oz_update(p, p, A, ld, t0, t0, nrows - t0, n1 - t0, nrows, n1, 0, 0, 1, all, st, s, 0)) !=
+            if ((r = oz_update(p, p, A, ld, t0, t0, nrows - t0, n1 - t0, nrows, n1, 0, 0, 1, all, st, s, 0, cut)) !=
                 cudaSuccess)
                 return r;
             if (n1 >= N) {
@@ -738,7 +826,7 @@ cudaError_t chol_oz_factor(double *A, long long ld, int N, int nrows, int nb, in
             if ((r = cudaEventRecord(e_pan, s2)) != cudaSuccess) return r;
             // the rest of the trailing update meanwhile: rows [n1, nrows), cols [n1, N)
             if ((r = oz_update(p, p, A, ld, n1, n1, nrows - n1, N - n1, nrows, N, n1 - t0, n1 - t0, 1,
-                               all - SIDE_SMS, st, s, 0)) != cudaSuccess)
+                               all - SIDE_SMS, st, s, 0, cut)) != cudaSuccess)
                 return r;
             if ((r = cudaStreamWaitEvent(s, e_pan, 0)) != cudaSuccess) return r;
             if ((r = panel_solve(t0, n1 - t0, n1, nrows, s)) != cudaSuccess) return r;
@@ -771,5 +859,5 @@ cudaError_t oz_gemm(int m, int n, int k, const double *A, long long lda, const d
     cudaError_t e;
     if ((e = oz_slice(A, lda, m, sa, st, s)) != cudaSuccess || (e = oz_slice(B, ldb, n, sb, st, s)) != cudaSuccess)
         return e;
-    return oz_update(sa, sb, C, ldc, 0, 0, m, n, m, n, 0, 0, 0, tc::num_sms(), st, s, 0);
+    return oz_update(sa, sb, C, ldc, 0, 0, m, n, m, n, 0, 0, 0, tc::num_sms(), st, s, 0, 0);
 }

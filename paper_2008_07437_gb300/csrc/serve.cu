@@ -417,7 +417,7 @@ int geo_server_profile_read(geo_server *S, geo_kstat *out) {
         std::lock_guard<std::mutex> lk(S->mu);
         if (!S->queue.empty() || S->inflight) return GEO_EINVAL;
     }
-    for (int k = 0; k < GEO_K_COUNT; ++k) out[k] = geo_kstat{0, 0.0, 0.0, 0.0, 0};
+    for (int k = 0; k < GEO_K_COUNT; ++k) out[k] = geo_kstat{0, 0.0, 0.0, 0.0, 0, 0.0};
     for (Worker *w : S->workers) {
         geo_kstat ks[GEO_K_COUNT];
         int rc = geo_profile_read(w->ctx, ks);
@@ -428,6 +428,7 @@ int geo_server_profile_read(geo_server *S, geo_kstat *out) {
             out[k].flops += ks[k].flops;
             out[k].bytes += ks[k].bytes;
             out[k].timed += ks[k].timed;
+            out[k].tensor_flops += ks[k].tensor_flops;
         }
     }
     return GEO_OK;

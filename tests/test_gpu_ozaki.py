@@ -25,6 +25,10 @@ Tolerances:
   also meet the 1e-6 target of the reduced forms.  With 8 slices the digit
   error is below the FP64 rounding of the rest of the computation and the
   FP64 bound (1e-10) applies instead.
+* the level cut (oz_cut = 1) drops, per output tile, only digit levels below
+  the first level every tile drops, measured against the update's largest
+  rows: each entry's error stays within the same absolute bound, so the
+  same tolerances apply with and without it.
 """
 from fractions import Fraction
 
@@ -240,13 +244,80 @@ def test_reduced_form_at_the_largest_oracle_size(ctx):
     ref = oracle.loglik(o_theta(th), locs, Z).loglik
     nat, _ = geo.geo_loglik(ctx, dev(locs), dev(Z), th, geo.opts(nb=512))
     e64 = abs(nat - ref) / abs(ref)
-    for S, nb in ((4, 1024), (5, 768), (8, 512)):
-        got, _ = geo.geo_loglik(ctx, dev(locs), dev(Z), th, emu(nb, slices=S))
+    for S, nb, cut in ((4, 1024, 0), (5, 768, 0), (5, 768, 1), (8, 512, 0), (8, 512, 1)):
+        got, _ = geo.geo_loglik(ctx, dev(locs), dev(Z), th, emu(nb, slices=S, oz_cut=cut))
         rel = abs(got - ref) / abs(ref)
-        print("N = %d, S = %d: |dl| / |l| = %.3e (bound %.3e, FP64 %.3e)" % (2 * n, S, rel, _derived_bound(S, e64), e64))
-        assert rel <= _derived_bound(S, e64), S
+        print("N = %d, S = %d, cut %d: |dl| / |l| = %.3e (bound %.3e, FP64 %.3e)"
+              % (2 * n, S, cut, rel, _derived_bound(S, e64), e64))
+        assert rel <= _derived_bound(S, e64), (S, cut)
         if S >= 5:
             assert rel <= 1e-6
+
+
+# ---------------------------------------------------------- the level cut --
+
+@pytest.mark.parametrize("n,theta", [(1, TH2), (333, TH3), (513, TH2G), (150, TH4)],
+                         ids=["n1", "n333p3", "n513", "n150p4"])
+def test_level_cut_loglik_matches_oracle(ctx, n, theta):
+    locs, Z = _problem(n, theta, seed=n)
+    ref = oracle.loglik(o_theta(theta), locs, Z)
+    for nb in (64, 192):
+        got, _ = geo.geo_loglik(ctx, dev(locs), dev(Z), theta, emu(nb, oz_cut=1))
+        assert got == pytest.approx(ref.loglik, rel=1e-10), nb
+
+
+def test_level_cut_factor_entrywise(ctx):
+    # a short range: the far tiles' entries are small, so the cut drops levels and whole tiles
+    th = geo.Theta((1.0, 1.0), 0.02, (0.5, 1.0), 0.5)
+    n = 1500
+    locs, Z = _problem(n, th, seed=15)
+    perm = oracle.morton_order(locs)
+    got, fac = geo.geo_loglik(ctx, dev(locs), dev(Z), th, emu(128, oz_cut=1), keep=True)
+    try:
+        r = oracle.loglik(o_theta(th), locs[perm], Z.reshape(n, 2)[perm].reshape(-1), keep_factor=True)
+        N = 2 * n
+        L = geo.geo_factor_read(fac, 0, 0, N, 0, N)
+        np.testing.assert_allclose(L, r.L, rtol=0, atol=1e-9)
+        np.testing.assert_allclose(geo.geo_factor_read(fac, 1, 0, N), r.y, rtol=0, atol=1e-9)
+        assert got == pytest.approx(r.loglik, rel=1e-10)
+    finally:
+        fac.free()
+
+
+def _tensor_flops(ctx, locs, Z, theta, o):
+    geo.geo_profile_enable(ctx, True)
+    ll, _ = geo.geo_loglik(ctx, locs, Z, theta, o)
+    prof = geo.geo_profile_read(ctx)
+    geo.geo_profile_enable(ctx, False)
+    return ll, prof["tcgemm"]["tensor_flops"]
+
+
+def test_level_cut_saves_tensor_work_within_the_bounds(ctx):
+    # N = 8,000 at a short range (a = 0.03): the cut must remove tensor-core work and keep the
+    # FP64 bound with 8 slices and the derived bound with 5
+    th = geo.Theta((1.0, 1.0), 0.03, (0.5, 1.5), 0.5)
+    n = 4000
+    locs = inputs.jittered_grid(n, 1001)
+    Z = oracle.simulate(o_theta(th), locs, inputs.normals(2001, 2 * n))
+    ref = oracle.loglik(o_theta(th), locs, Z).loglik
+    dl, dz = dev(locs), dev(Z)
+    nat, _ = geo.geo_loglik(ctx, dl, dz, th, geo.opts(nb=512))
+    e64 = abs(nat - ref) / abs(ref)
+    for S, nb in ((8, 512), (5, 768)):
+        full, tf_full = _tensor_flops(ctx, dl, dz, th, emu(nb, slices=S))
+        cut, tf_cut = _tensor_flops(ctx, dl, dz, th, emu(nb, slices=S, oz_cut=1))
+        again, tf_again = _tensor_flops(ctx, dl, dz, th, emu(nb, slices=S, oz_cut=1))
+        print("S = %d: tensor work with the cut %.3f of the full; |dl| / |l| %.2e (cut) %.2e (full)"
+              % (S, tf_cut / tf_full, abs(cut - ref) / abs(ref), abs(full - ref) / abs(ref)))
+        assert tf_full > 0 and tf_cut < 0.9 * tf_full
+        assert again == cut and tf_again == tf_cut   # deterministic
+        assert abs(cut - ref) / abs(ref) <= _derived_bound(S, e64), S
+
+
+def test_level_cut_rejects_bad_values(ctx):
+    locs, Z = _problem(100, TH2)
+    with pytest.raises(geo.GeoError):
+        geo.geo_loglik(ctx, dev(locs), dev(Z), TH2, emu(128, oz_cut=2))
 
 
 def test_predict_emulated_entrywise(ctx):

@@ -63,3 +63,21 @@ def test_single_process_is_the_identity():
     assert bench.max_over_ranks(1.5, torch.device("cpu")) == 1.5
     assert bench.gather_over_ranks({"a": 1}) == [{"a": 1}]
     assert bench.replica_value(4, 2.0, 1) == 2.0
+
+
+def test_mle_checkpoint_round_trip(tmp_path):
+    """The MLE bench saves the Nelder-Mead state (a plain host struct) and its
+    step records after every step; a later run resumes from them."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import paper_2008_07437_gb300 as geo
+    st = geo.geo_mle_init(geo.Theta((1.0, 1.2), 0.1, (0.5, 1.0), 0.4))
+    st.iter, st.evals = 3, 17
+    path = str(tmp_path / "mle.ckpt")
+    assert bench._mle_load(path, geo) == (None, [])
+    recs = [{"step": 1, "seconds": 2.5, "evals": 11, "best_loglik": -1.0},
+            {"step": 2, "seconds": 1.5, "evals": 2, "best_loglik": -0.5}]
+    bench._mle_save(path, st, recs)
+    st2, recs2 = bench._mle_load(path, geo)
+    assert bytes(st2) == bytes(st) and recs2 == recs
+    assert st2.evals == 17 and st2.iter == 3
