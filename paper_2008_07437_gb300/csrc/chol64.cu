@@ -33,8 +33,16 @@ __device__ __forceinline__ void set_info(DevStatus *st, int row1) {
 }
 
 // ---- POTRF of one diagonal block (cb <= IB) in shared memory -------------
+// Right-looking, two barriers per column: the rows below the pivot are scaled
+// by 1 / L_jj, then the rank-1 update runs with thread (row r, group g)
+// updating columns j + 1 + g, j + 5 + g, ...; the thread that updates the next
+// diagonal entry (it is the last to touch it) takes its square root and
+// reciprocal right away, so the pivot is ready at the next barrier.  The FP64
+// pipe (two FMAs per clock per SM) bounds the block at cb^3 / 6 FMAs; square
+// roots and divisions are taken once per column, not per thread.
 __global__ void __launch_bounds__(256) k_potrf_diag(double *A, long long ld, int c0, int cb, DevStatus *st) {
-    __shared__ double S[IB][IB + 1];   // S[col][row]
+    __shared__ double S[IB][IB + 1];   // S[col][row]: the block's Schur complement, then L
+    __shared__ double sinv;            // 1 / L_jj of the current column
     __shared__ int fail;
     if (st->info) return;
     for (int t = threadIdx.x; t < cb * cb; t += blockDim.x) {
@@ -43,32 +51,32 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double *A, long long ld, int
     }
     if (threadIdx.x == 0) fail = 0;
     __syncthreads();
+    const int r = threadIdx.x % IB, g = threadIdx.x / IB;   // 4 column groups of 64 row threads
+    auto pivot = [&](int j) {
+        const double d = S[j][j];
+        if (!(d > 0.0)) {
+            fail = 1;
+            set_info(st, c0 + j + 1);
+        } else {
+            const double l = sqrt(d);
+            S[j][j] = l;
+            sinv = 1.0 / l;
+        }
+    };
+    if (threadIdx.x == 0) pivot(0);
+    __syncthreads();
     for (int j = 0; j < cb; ++j) {
-        if (threadIdx.x == 0) {
-            const double d = S[j][j];
-            if (!(d > 0.0)) {
-                fail = 1;
-                set_info(st, c0 + j + 1);
-            } else {
-                S[j][j] = sqrt(d);
-            }
-        }
+        if (fail) return;   // read after a barrier: uniform
+        if (g == 0 && r > j && r < cb) S[j][r] *= sinv;
         __syncthreads();
-        if (fail) return;
-        const double inv = 1.0 / S[j][j];
-        for (int r = j + 1 + threadIdx.x; r < cb; r += blockDim.x) S[j][r] *= inv;
-        __syncthreads();
-        // rank-1 update of the trailing lower triangle of the block
-        const int m = cb - j - 1;
-        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-            const int c = j + 1 + t / m, r = j + 1 + t % m;
-            if (r >= c) S[c][r] -= S[j][r] * S[j][c];
-        }
+        for (int c = j + 1 + g; c < cb; c += 4)
+            if (r >= c && r < cb) S[c][r] -= S[j][r] * S[j][c];
+        if (g == 0 && r == j + 1 && r < cb) pivot(j + 1);
         __syncthreads();
     }
     for (int t = threadIdx.x; t < cb * cb; t += blockDim.x) {
-        const int c = t / cb, r = t % cb;
-        if (r >= c) A[(long long)(c0 + c) * ld + c0 + r] = S[c][r];
+        const int c = t / cb, r2 = t % cb;
+        if (r2 >= c) A[(long long)(c0 + c) * ld + c0 + r2] = S[c][r2];
     }
 }
 
@@ -94,10 +102,13 @@ __global__ void __launch_bounds__(256) k_trsm_rlt(double *A, long long ld, int c
         const int c = t / TRSM_ROWS, r = t % TRSM_ROWS;
         Xs[c * XLD + r] = (r < nr) ? A[(long long)(c0 + c) * ld + rbase + r] : 0.0;
     }
+    __shared__ double dinv[IB];   // 1 / L_cc, one division per column
+    __syncthreads();
+    if (threadIdx.x < cb) dinv[threadIdx.x] = 1.0 / Ls[threadIdx.x * IB + threadIdx.x];
     __syncthreads();
     const int row = threadIdx.x % TRSM_ROWS, grp = threadIdx.x / TRSM_ROWS;   // 4 column groups
     for (int c = 0; c < cb; ++c) {
-        if (grp == 0) Xs[c * XLD + row] *= 1.0 / Ls[c * IB + c];
+        if (grp == 0) Xs[c * XLD + row] *= dinv[c];
         __syncthreads();
         const double xc = Xs[c * XLD + row];
         for (int k = c + 1 + grp; k < cb; k += 4) Xs[k * XLD + row] -= xc * Ls[c * IB + k];

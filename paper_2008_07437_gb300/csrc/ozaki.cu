@@ -33,13 +33,15 @@
 //               kept for an output tile follow its operands' magnitudes: with
 //               E the largest row exponent of the launch's A rows plus that of
 //               its B rows, and e_i + e_j the same over the tile's own rows,
-//               the tile keeps the levels l <= S + 1 - floor((E - e_i - e_j) / 7).
-//               A dropped level of such a tile is below 2^(E - 7(S + 1)) times
-//               the digit-product sum, the size of the first level every tile
-//               drops anyway, so each entry's error stays within the bound of
-//               the launch's largest products; tiles whose operands are tiny
-//               against the launch's largest (far from the diagonal in a
-//               spatially ordered covariance) skip levels or vanish entirely.
+//               the tile keeps the levels l <= S + 1 - q, q = floor((E - e_i - e_j) / 7).
+//               A level-l term is at most 2^(e_i + e_j + 14 - 7 l), so the
+//               first level such a tile drops, S + 2 - q, is at most
+//               2^(e_i + e_j + 7 q - 7 S) <= 2^(E - 7 S): no larger than the
+//               first level the launch's largest tile drops without the cut.
+//               Every entry's error thus stays within the bound of the
+//               launch's largest products; tiles whose operands are tiny
+//               against the largest (far from the diagonal in a spatially
+//               ordered covariance) skip levels or vanish entirely.
 //
 // The kernel is persistent (one CTA per SM) over 128 x BN output tiles, the
 // K range in chunks of BK.  TMEM (512 columns) holds 512 / BN level
