@@ -656,16 +656,21 @@ namespace {
 // a CTA: at step k the owner of row k divides by L_kk and publishes w_k, every
 // thread then updates its rows below with column k of L (read along the
 // column, coalesced).  The broadcast buffer is double-buffered, so one barrier
-// per step suffices.
-constexpr int TRTRI_COLS = 8, TRTRI_THREADS = 256, TRTRI_RPT = 4;   // rows per thread: jb <= 1024
+// per step suffices; the reciprocals of the diagonal are taken up front, off
+// the chain of steps.  Four columns per CTA: the FP64 work of a step (two
+// FMAs per clock per SM) is split over jb / 4 CTAs.
+constexpr int TRTRI_COLS = 4, TRTRI_THREADS = 256, TRTRI_RPT = 4;   // rows per thread: jb <= 1024
 
 __global__ void __launch_bounds__(TRTRI_THREADS) k_trtri_neg(const double *__restrict__ L, long long ld, int jb,
                                                           double *W, long long ldw, const DevStatus *st) {
     __shared__ double wk[2][TRTRI_COLS];
+    __shared__ double dinv[TRTRI_THREADS * TRTRI_RPT];
     __shared__ int skip;
     if (threadIdx.x == 0) skip = *(volatile const int *)&st->info;
     __syncthreads();
     if (skip) return;
+    for (int r = threadIdx.x; r < jb; r += TRTRI_THREADS) dinv[r] = 1.0 / L[(long long)r * ld + r];
+    __syncthreads();
     const int c0 = blockIdx.x * TRTRI_COLS;
     const int ncol = min(TRTRI_COLS, jb - c0);
     double w[TRTRI_RPT][TRTRI_COLS];
@@ -677,22 +682,21 @@ __global__ void __launch_bounds__(TRTRI_THREADS) k_trtri_neg(const double *__res
     }
     // column k of L for this thread's rows (and the diagonal entry for the owner of row k),
     // loaded one step ahead so that the load latency is off the chain of barriers
-    double lcol[TRTRI_RPT], ldiag = 0.0;
-    auto load_col = [&](int k, double *dst, double *dg) {
+    double lcol[TRTRI_RPT];
+    auto load_col = [&](int k, double *dst) {
 #pragma unroll
         for (int q = 0; q < TRTRI_RPT; ++q) {
             const int r = threadIdx.x + q * TRTRI_THREADS;
             dst[q] = (k < jb && r >= k && r < jb) ? L[(long long)k * ld + r] : 0.0;
-            if (r == k) *dg = dst[q];
         }
     };
-    load_col(c0, lcol, &ldiag);
+    load_col(c0, lcol);
     for (int k = c0; k < jb; ++k) {
-        double lnext[TRTRI_RPT], dnext = 0.0;
-        load_col(k + 1, lnext, &dnext);
+        double lnext[TRTRI_RPT];
+        load_col(k + 1, lnext);
         const int owner_q = k / TRTRI_THREADS, owner_t = k % TRTRI_THREADS;
         if (threadIdx.x == owner_t) {
-            const double inv = 1.0 / ldiag;
+            const double inv = dinv[k];
 #pragma unroll
             for (int q = 0; q < TRTRI_RPT; ++q)
                 if (q == owner_q) {
@@ -714,7 +718,6 @@ __global__ void __launch_bounds__(TRTRI_THREADS) k_trtri_neg(const double *__res
         }
 #pragma unroll
         for (int q = 0; q < TRTRI_RPT; ++q) lcol[q] = lnext[q];
-        if (threadIdx.x == (k + 1) % TRTRI_THREADS) ldiag = dnext;
     }
 #pragma unroll
     for (int q = 0; q < TRTRI_RPT; ++q) {
