@@ -5,6 +5,8 @@
 // kernel maps one problem (or one 64 x 64 tile of it) to one CTA.
 #include <math.h>
 
+#include <algorithm>
+
 #include <cooperative_groups.h>
 
 #include "geo_internal.cuh"
@@ -23,23 +25,25 @@ namespace {
 // multiples of 64.
 constexpr int BT = 64, BKK = 16;
 
+// K range [kbeg, kend); part == NULL: C = alpha acc + beta C, else the raw
+// sums go to the tile-local partial part[(c - tn) * pw + (r - tm)].
 template <int IM, int JM>
 __device__ __forceinline__ void bgemm_tile(const GemmDesc &g, int tm, int tn, double (*As)[BT + 2],
-                                           double (*Bs)[BT + 2]) {
+                                           double (*Bs)[BT + 2], int kbeg, int kend, double *part, int pw) {
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     double acc[IM][JM];
 #pragma unroll
     for (int i = 0; i < IM; ++i)
 #pragma unroll
         for (int j = 0; j < JM; ++j) acc[i][j] = 0.0;
-    for (int k0 = 0; k0 < g.k; k0 += BKK) {
+    for (int k0 = kbeg; k0 < kend; k0 += BKK) {
         // consecutive threads walk the operand's contiguous index: rows for a
         // row-contiguous slice, K for a K-contiguous one (transposed A, plain B)
         for (int t = threadIdx.x; t < BKK * 16 * IM; t += 256) {
             const int kk = g.ta ? t % BKK : t / (16 * IM), r = g.ta ? t / BKK : t % (16 * IM);
             const int kg = k0 + kk;
             double a = 0.0;
-            if (kg < g.k && tm + r < g.m)
+            if (kg < kend && tm + r < g.m)
                 a = g.ta ? g.A[(long long)(tm + r) * g.lda + kg] : g.A[(long long)kg * g.lda + tm + r];
             As[kk][r] = a;
         }
@@ -47,12 +51,12 @@ __device__ __forceinline__ void bgemm_tile(const GemmDesc &g, int tm, int tn, do
             const int kk = g.tb ? t / (16 * JM) : t % BKK, r = g.tb ? t % (16 * JM) : t / BKK;
             const int kg = k0 + kk;
             double b = 0.0;
-            if (kg < g.k && tn + r < g.n)
+            if (kg < kend && tn + r < g.n)
                 b = g.tb ? g.B[(long long)kg * g.ldb + tn + r] : g.B[(long long)(tn + r) * g.ldb + kg];
             Bs[kk][r] = b;
         }
         __syncthreads();
-        const int kc = min(BKK, g.k - k0);   // uniform over the CTA
+        const int kc = min(BKK, kend - k0);   // uniform over the CTA
         if (kc == BKK) {
 #pragma unroll
             for (int kk = 0; kk < BKK; ++kk) {
@@ -89,6 +93,10 @@ __device__ __forceinline__ void bgemm_tile(const GemmDesc &g, int tm, int tn, do
         for (int i = 0; i < IM; ++i) {
             const int r = tm + ty + 16 * i;
             if (r >= g.m) continue;
+            if (part) {
+                part[(c - tn) * pw + (r - tm)] = acc[i][j];
+                continue;
+            }
             double *p = g.C + (long long)c * g.ldc + r;
             *p = g.alpha * acc[i][j] + (g.beta == 0.0 ? 0.0 : g.beta * *p);
         }
@@ -108,7 +116,7 @@ __global__ void __launch_bounds__(256) k_bgemm(const GemmDesc *__restrict__ d, i
     const int im = min(4, (g.m - tm + 15) / 16), jm = min(4, (g.n - tn + 15) / 16);
     switch ((im - 1) * 4 + (jm - 1)) {
 #define GEO_BGEMM_CASE(I, J) \
-    case (I - 1) * 4 + (J - 1): bgemm_tile<I, J>(g, tm, tn, As, Bs); break;
+    case (I - 1) * 4 + (J - 1): bgemm_tile<I, J>(g, tm, tn, As, Bs, 0, g.k, nullptr, 0); break;
         GEO_BGEMM_CASE(1, 1) GEO_BGEMM_CASE(1, 2) GEO_BGEMM_CASE(1, 3) GEO_BGEMM_CASE(1, 4)
         GEO_BGEMM_CASE(2, 1) GEO_BGEMM_CASE(2, 2) GEO_BGEMM_CASE(2, 3) GEO_BGEMM_CASE(2, 4)
         GEO_BGEMM_CASE(3, 1) GEO_BGEMM_CASE(3, 2) GEO_BGEMM_CASE(3, 3) GEO_BGEMM_CASE(3, 4)
@@ -121,9 +129,12 @@ __global__ void __launch_bounds__(256) k_bgemm(const GemmDesc *__restrict__ d, i
 // The same strips on 32 x 32 (S = 2) or 16 x 16 (S = 1) output tiles: for
 // launches whose 64 x 64 tiles would leave most SMs idle (few output tiles,
 // long K, e.g. the r x r cores V_ik' V_jk with K = nb), 4x or 16x more CTAs
-// share the K loops' FP64 work.
+// share the K loops' FP64 work.  Split-K (ws != NULL): blockIdx.z takes one of
+// zsplit contiguous K ranges and writes its raw sums to its own partial tile
+// ws[((pi zsplit + z) tiles_cap + tile) W^2 ..]; k_bgemm_reduce adds them.
 template <int S>
-__global__ void __launch_bounds__(256) k_bgemm_small(const GemmDesc *__restrict__ d, int count) {
+__global__ void __launch_bounds__(256) k_bgemm_small(const GemmDesc *__restrict__ d, int count, int zsplit,
+                                                     int tiles_cap, double *ws) {
     __shared__ double As[BKK][BT + 2];
     __shared__ double Bs[BKK][BT + 2];
     const int pi = blockIdx.y;
@@ -135,14 +146,45 @@ __global__ void __launch_bounds__(256) k_bgemm_small(const GemmDesc *__restrict_
     if ((int)blockIdx.x >= tiles_m * tiles_n) return;
     const int tm = (blockIdx.x % tiles_m) * W, tn = (blockIdx.x / tiles_m) * W;
     const int im = min(S, (g.m - tm + 15) / 16), jm = min(S, (g.n - tn + 15) / 16);
+    int kbeg = 0, kend = g.k;
+    double *part = nullptr;
+    if (ws) {
+        const int kc = ((g.k + zsplit - 1) / zsplit + BKK - 1) / BKK * BKK;
+        kbeg = min(g.k, (int)blockIdx.z * kc);
+        kend = min(g.k, kbeg + kc);
+        part = ws + (((long long)pi * zsplit + blockIdx.z) * tiles_cap + blockIdx.x) * (W * W);
+    }
     if (S == 1 || (im == 1 && jm == 1))
-        bgemm_tile<1, 1>(g, tm, tn, As, Bs);
+        bgemm_tile<1, 1>(g, tm, tn, As, Bs, kbeg, kend, part, W);
     else if (im == 1)
-        bgemm_tile<1, S == 1 ? 1 : 2>(g, tm, tn, As, Bs);
+        bgemm_tile<1, S == 1 ? 1 : 2>(g, tm, tn, As, Bs, kbeg, kend, part, W);
     else if (jm == 1)
-        bgemm_tile<S == 1 ? 1 : 2, 1>(g, tm, tn, As, Bs);
+        bgemm_tile<S == 1 ? 1 : 2, 1>(g, tm, tn, As, Bs, kbeg, kend, part, W);
     else
-        bgemm_tile<S == 1 ? 1 : 2, S == 1 ? 1 : 2>(g, tm, tn, As, Bs);
+        bgemm_tile<S == 1 ? 1 : 2, S == 1 ? 1 : 2>(g, tm, tn, As, Bs, kbeg, kend, part, W);
+}
+
+// C = alpha (sum of the zsplit partial tiles, in order) + beta C: the same
+// result on every run.
+template <int W>
+__global__ void __launch_bounds__(256) k_bgemm_reduce(const GemmDesc *__restrict__ d, int count, int zsplit,
+                                                      int tiles_cap, const double *__restrict__ ws) {
+    const int pi = blockIdx.y;
+    if (pi >= count) return;
+    const GemmDesc g = d[pi];
+    const int tiles_m = (g.m + W - 1) / W;
+    const int tiles_n = (g.n + W - 1) / W;
+    if ((int)blockIdx.x >= tiles_m * tiles_n) return;
+    const int tm = (blockIdx.x % tiles_m) * W, tn = (blockIdx.x / tiles_m) * W;
+    for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
+        const int i = e % W, j = e / W;
+        if (tm + i >= g.m || tn + j >= g.n) continue;
+        double sum = 0.0;
+        for (int z = 0; z < zsplit; ++z)
+            sum += ws[(((long long)pi * zsplit + z) * tiles_cap + blockIdx.x) * (W * W) + e];
+        double *p = g.C + (long long)(tn + j) * g.ldc + tm + i;
+        *p = g.alpha * sum + (g.beta == 0.0 ? 0.0 : g.beta * *p);
+    }
 }
 
 // ---- Householder QR of an m x r block (m >= r), in place -------------------
@@ -621,20 +663,50 @@ static int device_sms() {
     return n;
 }
 
+thread_local double *t_splitk_ws = nullptr;
+thread_local size_t t_splitk_doubles = 0;
+
+void bgemm_splitk_scratch(double *ws, size_t bytes) {
+    t_splitk_ws = ws;
+    t_splitk_doubles = ws ? bytes / sizeof(double) : 0;
+}
+
 // max_tiles: the largest number of 64 x 64 output tiles of one problem.  A
 // problem has at most 4x (16x) as many 32 x 32 (16 x 16) tiles; the surplus
-// CTAs of the smaller-tile grids return at once.
-cudaError_t launch_bgemm(const GemmDesc *d_desc, int count, int max_tiles, cudaStream_t s, double flops) {
+// CTAs of the smaller-tile grids return at once.  With fewer than two CTAs
+// per SM on the small tiles, a K of at least 512 and a split-K scratch
+// registered on this thread, the K loop is split over up to 16 CTAs per tile.
+cudaError_t launch_bgemm(const GemmDesc *d_desc, int count, int max_tiles, cudaStream_t s, double flops, int kmax) {
     if (count <= 0 || max_tiles <= 0) return cudaSuccess;
     KScope ks(GEO_K_GEMM, s, flops, 0.0);
     const long long ctas = (long long)max_tiles * count;
     const long long sms = device_sms();
-    if (ctas >= sms)
+    if (ctas >= sms) {
         k_bgemm<<<dim3(max_tiles, count), 256, 0, s>>>(d_desc, count);
-    else if (4 * ctas >= sms)
-        k_bgemm_small<2><<<dim3(4 * max_tiles, count), 256, 0, s>>>(d_desc, count);
+        return cudaGetLastError();
+    }
+    const int S = (4 * ctas >= sms) ? 2 : 1;
+    const int W = 16 * S;
+    const long long tiles_cap = (long long)(64 / W) * (64 / W) * max_tiles;
+    int z = 1;
+    if (kmax >= 512 && t_splitk_ws && tiles_cap * count < 2 * sms) {
+        const long long want = (2 * sms + tiles_cap * count - 1) / (tiles_cap * count);
+        z = (int)std::min<long long>(std::min<long long>(want, 16), kmax / 128);
+        while (z >= 2 && (size_t)z * count * tiles_cap * W * W > t_splitk_doubles) --z;
+    }
+    double *ws = z >= 2 ? t_splitk_ws : nullptr;
+    if (z < 2) z = 1;
+    const dim3 grid((unsigned)tiles_cap, count, z);
+    if (S == 2)
+        k_bgemm_small<2><<<grid, 256, 0, s>>>(d_desc, count, z, (int)tiles_cap, ws);
     else
-        k_bgemm_small<1><<<dim3(16 * max_tiles, count), 256, 0, s>>>(d_desc, count);
+        k_bgemm_small<1><<<grid, 256, 0, s>>>(d_desc, count, z, (int)tiles_cap, ws);
+    if (ws) {
+        if (S == 2)
+            k_bgemm_reduce<32><<<dim3((unsigned)tiles_cap, count), 256, 0, s>>>(d_desc, count, z, (int)tiles_cap, ws);
+        else
+            k_bgemm_reduce<16><<<dim3((unsigned)tiles_cap, count), 256, 0, s>>>(d_desc, count, z, (int)tiles_cap, ws);
+    }
     return cudaGetLastError();
 }
 

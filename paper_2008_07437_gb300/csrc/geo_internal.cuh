@@ -245,7 +245,12 @@ struct SvdDesc {            // one-sided Jacobi SVD of M (r x r): M <- M V, V, s
     double *sigma;
     double skip;            // pairs of columns both below this norm are left alone (0 = none)
 };
-cudaError_t launch_bgemm(const GemmDesc *d_desc, int count, int max_tiles, cudaStream_t s, double flops);
+// kmax: the largest K of the batch (0: no split-K).
+cudaError_t launch_bgemm(const GemmDesc *d_desc, int count, int max_tiles, cudaStream_t s, double flops,
+                         int kmax = 0);
+// Scratch for the split-K partial tiles of this thread's launch_bgemm calls (NULL: none).
+void bgemm_splitk_scratch(double *ws, size_t bytes);
+constexpr size_t TLR_SPLITK_BYTES = 8u << 20;
 // mmax, rmax: the largest m and r of the batch (the cluster kernel serves r <= 256).
 cudaError_t launch_house_qr(const QrDesc *d_desc, int count, int mmax, int rmax, cudaStream_t s, double flops);
 // rmax: the largest r of the batch (the cluster kernel serves r <= 256).

@@ -178,6 +178,12 @@ int gemm_tiles(const std::vector<GemmDesc> &v) {
     return mx;
 }
 
+int gemm_kmax(const std::vector<GemmDesc> &v) {
+    int k = 0;
+    for (const GemmDesc &g : v) k = std::max(k, g.k);
+    return k;
+}
+
 double gemm_flops(const std::vector<GemmDesc> &v) {
     double f = 0.0;
     for (const GemmDesc &g : v) f += 2.0 * g.m * g.n * g.k;
@@ -204,8 +210,17 @@ size_t tlr_workspace_bytes(int N, int nb, int kmax) {
                              + T * TLR_MAXK_PER_CHUNK * (size_t)kmax * kmax   // cores
                              + (size_t)TLR_KCHUNK * rmax        // Qc' Omega
                              + T * (size_t)TLR_KCHUNK * rmax)   // P_i' Q_i per tile
-           + T * per_tile + 2 * TLR_ARENA_BYTES + (size_t)N * 2 * sizeof(double) + 16 * 256 + 4096;
+           + T * per_tile + 2 * TLR_ARENA_BYTES + (size_t)N * 2 * sizeof(double) + 16 * 256 + 4096 +
+           TLR_SPLITK_BYTES + 256;
 }
+
+namespace {
+// Registers the split-K scratch of the batched GEMMs for the calls on this thread.
+struct SplitKScope {
+    SplitKScope(void *ws, size_t bytes) { bgemm_splitk_scratch((double *)ws, bytes); }
+    ~SplitKScope() { bgemm_splitk_scratch(nullptr, 0); }
+};
+}  // namespace
 
 cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, const double *ly, void *ws,
                        size_t ws_bytes, void *arena_host, DevStatus *st, DevStatus *h_st, cudaStream_t s) {
@@ -231,6 +246,7 @@ cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, cons
     // per tile: Y, Q, B', Q2 (nb x rmax), M, Vj, Ms, Vs (rmax^2), sigma, tau, v0, spare (rmax), saved Y (nb x rmax)
     const size_t per_tile = 5 * (size_t)nb * rmax + 4 * (size_t)rmax * rmax + 4 * (size_t)rmax;
     double *TW = (double *)take(sizeof(double) * (size_t)T * per_tile);
+    SplitKScope splitk(take(TLR_SPLITK_BYTES), TLR_SPLITK_BYTES);
     Arena arena;
     arena.dev = take(TLR_ARENA_BYTES);
     arena.host = (uint8_t *)arena_host;
@@ -360,12 +376,12 @@ cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, cons
                 if (!dm.empty()) {
                     GemmDesc *d1 = push(arena, dm, s, &ce);
                     if (ce) return ce;
-                    if ((ce = launch_bgemm(d1, (int)dm.size(), gemm_tiles(dm), s, gemm_flops(dm)))) return ce;
+                    if ((ce = launch_bgemm(d1, (int)dm.size(), gemm_tiles(dm), s, gemm_flops(dm), gemm_kmax(dm)))) return ce;
                 }
                 if (!dp.empty()) {
                     GemmDesc *d2 = push(arena, dp, s, &ce);
                     if (ce) return ce;
-                    if ((ce = launch_bgemm(d2, (int)dp.size(), gemm_tiles(dp), s, gemm_flops(dp)))) return ce;
+                    if ((ce = launch_bgemm(d2, (int)dp.size(), gemm_tiles(dp), s, gemm_flops(dp), gemm_kmax(dp)))) return ce;
                 }
                 if ((ce = apply(Kc, has))) return ce;
             }
@@ -382,7 +398,7 @@ cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, cons
             cudaError_t ce;
             GemmDesc *d3 = push(arena, dw, s, &ce);
             if (ce) return ce;
-            return launch_bgemm(d3, (int)dw.size(), gemm_tiles(dw), s, gemm_flops(dw));
+            return launch_bgemm(d3, (int)dw.size(), gemm_tiles(dw), s, gemm_flops(dw), gemm_kmax(dw));
         };
         // the Gaussian test matrix of this column and the raw sketches Y_i = Sigma_ij Omega
         TCK(launch_gaussian(Om, (long long)nb * rmax, 0x5EEDull * (j + 1), s));
@@ -403,7 +419,7 @@ cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, cons
                                1.0, 0.0});
             GemmDesc *g0 = push(arena, dy0, s, &e);
             TCK(e);
-            TCK(launch_bgemm(g0, (int)dy0.size(), gemm_tiles(dy0), s, gemm_flops(dy0)));
+            TCK(launch_bgemm(g0, (int)dy0.size(), gemm_tiles(dy0), s, gemm_flops(dy0), gemm_kmax(dy0)));
         }
         TCK(chunk_loop(all_rows, [&](int Kc, const std::vector<char> &has) -> cudaError_t {
             cudaError_t ce = dense_update(dense_rows, Kc, has);
@@ -416,11 +432,11 @@ cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, cons
                     dy.push_back({mt(i), rmax, Kc, 0, 0, Pof(i), nb, Zb, TLR_KCHUNK, Ysave(i - j - 1), nb, -1.0, 1.0});
             GemmDesc *gz = push(arena, dz, s, &ce);
             if (ce) return ce;
-            if ((ce = launch_bgemm(gz, 1, gemm_tiles(dz), s, gemm_flops(dz)))) return ce;
+            if ((ce = launch_bgemm(gz, 1, gemm_tiles(dz), s, gemm_flops(dz), gemm_kmax(dz)))) return ce;
             if (dy.empty()) return cudaSuccess;
             GemmDesc *gy = push(arena, dy, s, &ce);
             if (ce) return ce;
-            return launch_bgemm(gy, (int)dy.size(), gemm_tiles(dy), s, gemm_flops(dy));
+            return launch_bgemm(gy, (int)dy.size(), gemm_tiles(dy), s, gemm_flops(dy), gemm_kmax(dy));
         }));
         // 3. diagonal tile in FP64
         TCK(chol64_panel(W, ldw, 0, mj, mj, mj, st, s));
@@ -471,7 +487,7 @@ cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, cons
             TCK(launch_house_qr(q1, (int)dq1.size(), nb, r, s, 4.0 * (double)dq1.size() * nb * r * r));
             GemmDesc *g2 = push(arena, db, s, &e);
             TCK(e);
-            TCK(launch_bgemm(g2, (int)db.size(), gemm_tiles(db), s, gemm_flops(db)));
+            TCK(launch_bgemm(g2, (int)db.size(), gemm_tiles(db), s, gemm_flops(db), gemm_kmax(db)));
             // B_i' -= Qc (P_i' Q_i)
             TCK(chunk_loop(rows_b, [&](int Kc, const std::vector<char> &has) -> cudaError_t {
                 std::vector<GemmDesc> dt1, dt2;
@@ -487,10 +503,10 @@ cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, cons
                 cudaError_t ce;
                 GemmDesc *h1 = push(arena, dt1, s, &ce);
                 if (ce) return ce;
-                if ((ce = launch_bgemm(h1, (int)dt1.size(), gemm_tiles(dt1), s, gemm_flops(dt1)))) return ce;
+                if ((ce = launch_bgemm(h1, (int)dt1.size(), gemm_tiles(dt1), s, gemm_flops(dt1), gemm_kmax(dt1)))) return ce;
                 GemmDesc *h2 = push(arena, dt2, s, &ce);
                 if (ce) return ce;
-                return launch_bgemm(h2, (int)dt2.size(), gemm_tiles(dt2), s, gemm_flops(dt2));
+                return launch_bgemm(h2, (int)dt2.size(), gemm_tiles(dt2), s, gemm_flops(dt2), gemm_kmax(dt2));
             }));
             QrDesc *q2 = push(arena, dq2, s, &e);
             TCK(e);
@@ -618,10 +634,10 @@ cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, cons
                 }
                 GemmDesc *g1 = push(arena, du, s, &e);
                 TCK(e);
-                TCK(launch_bgemm(g1, (int)du.size(), gemm_tiles(du), s, gemm_flops(du)));
+                TCK(launch_bgemm(g1, (int)du.size(), gemm_tiles(du), s, gemm_flops(du), gemm_kmax(du)));
                 GemmDesc *g2 = push(arena, dv, s, &e);
                 TCK(e);
-                TCK(launch_bgemm(g2, (int)dv.size(), gemm_tiles(dv), s, gemm_flops(dv)));
+                TCK(launch_bgemm(g2, (int)dv.size(), gemm_tiles(dv), s, gemm_flops(dv), gemm_kmax(dv)));
                 // 5. V_ij <- L_jj^-1 V_ij, 64-row blocks
                 const double *Ljj = F.D + (size_t)j * nb * nb;
                 std::vector<TlrTrsmDesc> dt;
@@ -648,7 +664,7 @@ cudaError_t tlr_factor(TlrFactor &F, const CovParams &cp, const double *lx, cons
                                            x.X + c0, nb, x.X + c0 + cb, nb, -1.0, 1.0});
                         GemmDesc *g3 = push(arena, du2, s, &e);
                         TCK(e);
-                        TCK(launch_bgemm(g3, (int)du2.size(), gemm_tiles(du2), s, gemm_flops(du2)));
+                        TCK(launch_bgemm(g3, (int)du2.size(), gemm_tiles(du2), s, gemm_flops(du2), gemm_kmax(du2)));
                     }
                 }
             }
@@ -676,6 +692,7 @@ cudaError_t tlr_solve(const TlrFactor &F, double *x, bool transpose, void *ws, v
     arena.host = (uint8_t *)arena_host;
     arena.cap = TLR_ARENA_BYTES;
     int *sync = (int *)(arena.dev + TLR_ARENA_BYTES);   // the diagonal solves' sync words
+    SplitKScope splitk((void *)(((uintptr_t)sync + 512 + 255) & ~(uintptr_t)255), TLR_SPLITK_BYTES);
     cudaError_t e = cudaSuccess;
     for (int step = 0; step < T; ++step) {
         const int i = transpose ? T - 1 - step : step;
@@ -699,10 +716,10 @@ cudaError_t tlr_solve(const TlrFactor &F, double *x, bool transpose, void *ws, v
         if (nc > 0) {
             GemmDesc *g1 = push(arena, d1, s, &e);
             if (e) return e;
-            if ((e = launch_bgemm(g1, nc, gemm_tiles(d1), s, gemm_flops(d1)))) return e;
+            if ((e = launch_bgemm(g1, nc, gemm_tiles(d1), s, gemm_flops(d1), gemm_kmax(d1)))) return e;
             GemmDesc *g2 = push(arena, d2, s, &e);
             if (e) return e;
-            if ((e = launch_bgemm(g2, nc, gemm_tiles(d2), s, gemm_flops(d2)))) return e;
+            if ((e = launch_bgemm(g2, nc, gemm_tiles(d2), s, gemm_flops(d2), gemm_kmax(d2)))) return e;
             KScope ks(GEO_K_SOLVE, s);
             k_sub_cols<<<(mt(i) + 255) / 256, 256, 0, s>>>(x + (size_t)i * nb, cbuf, nb, mt(i), nc);
             if ((e = cudaGetLastError())) return e;
@@ -725,7 +742,7 @@ cudaError_t tlr_solve(const TlrFactor &F, double *x, bool transpose, void *ws, v
 size_t tlr_solve_workspace_bytes(int N, int nb, int kmax) {
     (void)kmax;
     const size_t T = ((size_t)N + nb - 1) / nb;
-    return sizeof(double) * (T * (size_t)nb + (size_t)nb * T) + TLR_ARENA_BYTES + 512 + 64;
+    return sizeof(double) * (T * (size_t)nb + (size_t)nb * T) + TLR_ARENA_BYTES + 512 + 64 + TLR_SPLITK_BYTES + 512;
 }
 
 cudaError_t tlr_reduce(const TlrFactor &F, const double *y, const DevStatus *st, DevResults *res, cudaStream_t s) {

@@ -163,3 +163,16 @@ def test_dst_matches_oracle(ctx, dst):
     if dst >= 5:
         dense, _ = geo.geo_loglik(ctx, dev(locs), dev(Z), th, geo.opts(nb=240))
         assert got == pytest.approx(dense, rel=1e-12)
+
+
+def test_tlr_long_k_products_split_k(ctx):
+    # nb = 600: the cores V_ik' V_jk and the other K = nb products of a 6-tile column have few
+    # output tiles, so the batched GEMM splits their K loops; the result must still equal dense
+    # to the tolerance and be the same on every run
+    locs, Z = _problem(1800, TH2, 6)          # N = 3,600
+    ref = oracle.loglik(o_theta(TH2), locs, Z)
+    o = tlr_opts(600, 1e-12, kmax=600)
+    a, _ = geo.geo_loglik(ctx, dev(locs), dev(Z), TH2, o)
+    b, _ = geo.geo_loglik(ctx, dev(locs), dev(Z), TH2, o)
+    assert a == b
+    assert a == pytest.approx(ref.loglik, rel=1e-9)
