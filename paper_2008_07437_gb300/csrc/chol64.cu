@@ -197,7 +197,7 @@ cudaError_t gemm_update(double *A, long long ld, int rC, int cC, int m, int n, i
 // With factor_diag false the diagonal tile must already hold L and only the
 // rows [x0, x1) are solved against it (X <- X L^-T).
 cudaError_t chol64_panel(double *A, long long ld, int j0, int jb, int x0, int x1, DevStatus *st, cudaStream_t s,
-                         bool factor_diag) {
+                         bool factor_diag, const PanelUpdate *upd) {
     const size_t trsm_smem = sizeof(double) * (IB * IB + IB * (TRSM_ROWS + 1));
     cudaError_t e = cudaFuncSetAttribute(k_trsm_rlt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem);
     if (e != cudaSuccess) return e;
@@ -229,7 +229,8 @@ cudaError_t chol64_panel(double *A, long long ld, int j0, int jb, int x0, int x1
         // rest of the panel: cols rows0 .. j0+jb-1
         if (rows0 < j0 + jb) {
             for (int q = 0; q < nrange; ++q) {
-                e = gemm_update(A, ld, ra[q][0], rows0, ra[q][1] - ra[q][0], j0 + jb - rows0, c0, cb, st, s);
+                e = upd ? upd->fn(upd, A, ld, ra[q][0], rows0, ra[q][1] - ra[q][0], j0 + jb - rows0, c0, cb, st, s)
+                        : gemm_update(A, ld, ra[q][0], rows0, ra[q][1] - ra[q][0], j0 + jb - rows0, c0, cb, st, s);
                 if (e != cudaSuccess) return e;
             }
         }

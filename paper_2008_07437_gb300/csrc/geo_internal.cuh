@@ -105,9 +105,16 @@ cudaError_t launch_scatter_vec(const double *in, long long stride, const int *pe
 // are extra right-hand-side rows carried through the factorisation (row N
 // receives (L^-1 z)' when it holds z').  nb = outer tile size.
 cudaError_t chol64_factor(double *A, long long ld, int N, int nrows, int nb, DevStatus *st, cudaStream_t s);
+// The rank-64 updates inside a panel, C[rC.., cC..] (m x n) -= A[rC.., kA..kA+k] A[cC.., kA..kA+k]'
+// (lower part when rC == cC), when they should not run on the FP64 pipe.
+struct PanelUpdate {
+    cudaError_t (*fn)(const PanelUpdate *u, double *A, long long ld, int rC, int cC, int m, int n, int kA, int k,
+                      DevStatus *st, cudaStream_t s);
+    void *ctx;
+};
 // One panel [j0, j0+jb): diagonal tile plus extra rows [x0, x1) carried along.
 cudaError_t chol64_panel(double *A, long long ld, int j0, int jb, int x0, int x1, DevStatus *st, cudaStream_t s,
-                         bool factor_diag = true);
+                         bool factor_diag = true, const PanelUpdate *upd = nullptr);
 // C[rC.., cC..] (m x n) -= A[rC.., kA..kA+k] A[cC.., kA..kA+k]' in FP64.
 cudaError_t chol64_gemm_update(double *A, long long ld, int rC, int cC, int m, int n, int kA, int k, DevStatus *st,
                                cudaStream_t s);

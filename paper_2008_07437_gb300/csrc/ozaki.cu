@@ -739,10 +739,37 @@ cudaError_t launch_trtri_neg(const double *L, long long ld, int jb, double *W, l
 
 }  // namespace
 
+constexpr int OZ_TILE_IB = 64;   // inner block of the diagonal tiles (the rank of their updates)
+
 size_t oz_chol_workspace_bytes(int nrows, int nb, int S) {
     return oz_slices_bytes((long long)nrows + 128, nb, S) + oz_slices_bytes(nb, nb, S) + sizeof(double) * (size_t)nb * nb +
-           1024;
+           oz_slices_bytes(nb, OZ_TILE_IB, S) + 1280;
 }
+
+namespace {
+// The rank-64 updates inside a diagonal tile as emulated products: the rows
+// below the inner block (their columns kA .. kA + k) as digit slices, then the
+// lower triangle of the rest of the tile.  Runs on the side stream with at most
+// `sms` CTAs, beside the trailing update.
+struct TileUpdate {
+    OzSlices sl;
+    int sms;
+};
+
+cudaError_t tile_update(const PanelUpdate *u, double *A, long long ld, int rC, int cC, int m, int n, int kA, int k,
+                        DevStatus *st, cudaStream_t s) {
+    const TileUpdate &t = *(const TileUpdate *)u->ctx;
+    if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
+    if (rC != cC || k > t.sl.K || m > t.sl.rows) return cudaErrorInvalidValue;
+    OzSlices p = t.sl;
+    p.K = k;
+    p.nchunk = (k + p.kchunk - 1) / p.kchunk;
+    p.valid = m;
+    cudaError_t e = oz_slice(A + (long long)kA * ld + rC, ld, m, p, st, s);
+    if (e != cudaSuccess) return e;
+    return oz_update(p, p, A, ld, rC, cC, m, n, rC + m, cC + n, 0, 0, 1, t.sms, st, s, 0, 0);
+}
+}  // namespace
 
 // Right-looking over panels of width nb with a lookahead of one (as the mixed
 // form).  Step j slices its solved panel (the rows below the diagonal tile,
@@ -764,6 +791,9 @@ cudaError_t chol_oz_factor(double *A, long long ld, int N, int nrows, int nb, in
     const OzSlices slw0 = oz_slices_carve((void *)wp, nb, nb, S);
     wp = (wp + oz_slices_bytes(nb, nb, S) + 255) & ~(uintptr_t)255;
     double *W = (double *)wp;   // nb x nb, ld nb
+    wp = (wp + sizeof(double) * (size_t)nb * nb + 255) & ~(uintptr_t)255;
+    TileUpdate tu{oz_slices_carve((void *)wp, nb, OZ_TILE_IB, S), SIDE_SMS};
+    const PanelUpdate tile_upd{tile_update, &tu};
     int prio_lo = 0, prio_hi = 0;
     cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     cudaStream_t s2 = nullptr;
@@ -793,7 +823,7 @@ cudaError_t chol_oz_factor(double *A, long long ld, int N, int nrows, int nb, in
     };
     // native FP64 factorisation of the diagonal tile [t0, t0 + jb) and its inverse
     auto diag = [&](int t0, int jb, cudaStream_t st_) -> cudaError_t {
-        cudaError_t r = chol64_panel(A, ld, t0, jb, t0 + jb, t0 + jb, st, st_);
+        cudaError_t r = chol64_panel(A, ld, t0, jb, t0 + jb, t0 + jb, st, st_, true, &tile_upd);
         if (r != cudaSuccess) return r;
         return launch_trtri_neg(A + (long long)t0 * ld + t0, ld, jb, W, nb, st, st_);
     };
