@@ -433,13 +433,45 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 // bexps[2 chunk bstride + b], and that of its non-zero rows below ref_rows to
 // bexps[(2 chunk + 1) bstride + b] (OZ_E_NONE where there is none).
 // One CTA per 32 rows: a column sweep for the row maxima, then 32 x 32
-// tiles through shared memory so that each slice row is written along K.
+// tiles through shared memory so that each slice row is written along K, four
+// digits (8 bytes) per store.  Everything runs on the integer pipes: the
+// maxima compare the magnitudes' bit patterns (ordered like the values), and
+// X = rint(x 2^(7S - 1 - e)) is the 53-bit significand shifted by the
+// difference of exponents with round-to-nearest-even, the same integer the
+// FP64 product and conversion would give.
+__device__ __forceinline__ long long oz_scaled_int(unsigned long long b, int k) {
+    // rint(x 2^k) for the double with bits b (|x 2^k| < 2^62)
+    const int E = (int)((b >> 52) & 0x7FF);
+    if (E == 0) return 0;   // zero or subnormal: below 2^-1022, far below 1/2 after any scaling used here
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = 1075 - E - k;   // x 2^k = m 2^-sh
+    unsigned long long q;
+    if (sh <= 0) {
+        q = m << (-sh);
+    } else if (sh >= 64) {
+        q = 0;
+    } else {
+        q = m >> sh;
+        const unsigned long long rem = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (q & 1))) ++q;
+    }
+    return (b >> 63) ? -(long long)q : (long long)q;
+}
+
+// BF16 bits of a small integer d, |d| <= 64 (exact: at most 7 significant bits).
+__device__ __forceinline__ unsigned int oz_bf16_bits(int d) {
+    if (d == 0) return 0u;
+    const unsigned int u = (unsigned int)(d < 0 ? -d : d);
+    const int p = 31 - __clz(u);   // 0 .. 6
+    return (d < 0 ? 0x8000u : 0u) | ((unsigned int)(127 + p) << 7) | ((u << (7 - p)) & 0x7Fu);
+}
+
 __global__ void __launch_bounds__(256) k_oz_slice(const double *P, long long ld, int R, int K, int kchunk, int S,
                                                   __nv_bfloat16 *out, long long slice_stride, int Kp, int *exps,
                                                   long long exp_stride, int *bexps, long long bstride, int ref_rows,
                                                   const DevStatus *st) {
-    __shared__ double tile[32][33];
-    __shared__ double red[8][32];
+    __shared__ unsigned long long tile[32][33];
+    __shared__ unsigned long long red[8][32];
     __shared__ int ex[32];
     __shared__ int skip;
     if (threadIdx.x == 0) skip = *(volatile const int *)&st->info;
@@ -449,20 +481,22 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double *P, long long ld,
     const int kbeg = blockIdx.y * kchunk, kend = min(K, kbeg + kchunk);
     const int kpad_end = min(Kp, kbeg + (kchunk + OZ_KALIGN - 1) / OZ_KALIGN * OZ_KALIGN);
     const int rr = threadIdx.x % 32, g = threadIdx.x / 32;
-    double mx = 0.0;
+    const unsigned long long *Pb = reinterpret_cast<const unsigned long long *>(P);
+    constexpr unsigned long long MAG = 0x7FFFFFFFFFFFFFFFull;
+    unsigned long long mx = 0;
     if (r0 + rr < R)
-        for (int k = kbeg + g; k < kend; k += 8) mx = fmax(mx, fabs(P[(long long)k * ld + r0 + rr]));
+        for (int k = kbeg + g; k < kend; k += 8) mx = max(mx, Pb[(long long)k * ld + r0 + rr] & MAG);
     red[g][rr] = mx;
     __syncthreads();
     if (threadIdx.x < 32) {
-        double m = red[0][rr];
-        for (int q = 1; q < 8; ++q) m = fmax(m, red[q][rr]);
+        unsigned long long m = red[0][rr];
+        for (int q = 1; q < 8; ++q) m = max(m, red[q][rr]);
+        // max |x| = f 2^e with f in [1/2, 1): |x| < 2^e on the row (e = biased exponent - 1022)
         int e = 0;
-        if (m > 0.0) frexp(m, &e);   // m = f 2^e, f in [0.5, 1): |x| < 2^e on the row
-        e = max(e, -960);
+        if (m > 0) e = max((int)(m >> 52) - 1022, -960);
         ex[rr] = e;
         if (r0 + rr < R) exps[(long long)blockIdx.y * exp_stride + r0 + rr] = e;
-        const bool live = r0 + rr < R && m > 0.0;
+        const bool live = r0 + rr < R && m > 0;
         int eall = live ? e : OZ_E_NONE, eref = (live && r0 + rr < ref_rows) ? e : OZ_E_NONE;
         for (int o = 16; o > 0; o >>= 1) {
             eall = max(eall, __shfl_xor_sync(0xffffffffu, eall, o));
@@ -474,25 +508,36 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double *P, long long ld,
         }
     }
     __syncthreads();
+    // this thread's row and four consecutive columns of each 32 x 32 tile
+    const int r = threadIdx.x / 8, cq = (threadIdx.x % 8) * 4;
+    const int kshift = 7 * S - 1 - ex[r];
     for (int c0 = kbeg; c0 < kpad_end; c0 += 32) {
         for (int t = threadIdx.x; t < 32 * 32; t += 256) {
-            const int c = t / 32, r = t % 32;
-            tile[c][r] = (r0 + r < R && c0 + c < kend) ? P[(long long)(c0 + c) * ld + r0 + r] : 0.0;
+            const int c = t / 32, rw = t % 32;
+            tile[c][rw] = (r0 + rw < R && c0 + c < kend) ? Pb[(long long)(c0 + c) * ld + r0 + rw] : 0ull;
         }
         __syncthreads();
-        for (int t = threadIdx.x; t < 32 * 32; t += 256) {
-            const int r = t / 32, c = t % 32;
-            if (r0 + r >= R || c0 + c >= Kp) continue;
-            // x 2^(7S - 1 - e) is exact (a power-of-two scaling) and below 2^(7S - 1) in magnitude
-            const double scale = __longlong_as_double((long long)(7 * S - 1 - ex[r] + 1023) << 52);
-            long long X = __double2ll_rn(tile[c][r] * scale);
-            __nv_bfloat16 *o = out + (long long)(r0 + r) * Kp + c0 + c;
-            for (int s = S - 1; s >= 1; --s) {
-                const long long d = ((X + 64) & 127) - 64;   // balanced digit in [-64, 63]
-                o[(long long)s * slice_stride] = __float2bfloat16_rn((float)d);
-                X = (X - d) >> 7;   // exact: X - d is a multiple of 128
+        if (r0 + r < R) {
+            long long X[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) X[i] = oz_scaled_int(tile[cq + i][r], kshift);
+            unsigned int *o = reinterpret_cast<unsigned int *>(out + (long long)(r0 + r) * Kp + c0 + cq);
+            for (int sl = S - 1; sl >= 1; --sl) {
+                int d[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    d[i] = (int)(((X[i] + 64) & 127) - 64);   // balanced digit in [-64, 63]
+                    X[i] = (X[i] - d[i]) >> 7;                 // exact: X - d is a multiple of 128
+                }
+                uint2 v;
+                v.x = oz_bf16_bits(d[0]) | (oz_bf16_bits(d[1]) << 16);
+                v.y = oz_bf16_bits(d[2]) | (oz_bf16_bits(d[3]) << 16);
+                *reinterpret_cast<uint2 *>(o + (long long)sl * slice_stride / 2) = v;
             }
-            o[0] = __float2bfloat16_rn((float)X);   // leading digit, |X| <= 64
+            uint2 v;   // leading digits, |X| <= 64
+            v.x = oz_bf16_bits((int)X[0]) | (oz_bf16_bits((int)X[1]) << 16);
+            v.y = oz_bf16_bits((int)X[2]) | (oz_bf16_bits((int)X[3]) << 16);
+            *reinterpret_cast<uint2 *>(o) = v;
         }
         __syncthreads();
     }
