@@ -79,7 +79,8 @@ constexpr int OZ_KALIGN = 32;     // slice arrays: K padded to a multiple of 32 
 constexpr int OZ_EPI_WARPS = 8;
 constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;
 constexpr int OZ_TMEM_COLS = 512;
-constexpr int OZ_SMEM_CAP = 225 * 1024;
+constexpr int OZ_SMEM_CAP = 216 * 1024;   // the ring of K chunks; the rest holds the level-cut table
+constexpr int OZ_LC_CAP = 8192;           // tiles per CTA whose level cut is computed up front
 constexpr int OZ_GROUP = 8;       // row blocks swept together (operand reuse in L2)
 constexpr int OZ_LPW = 4;         // levels folded into one 64-bit word
 constexpr int OZ_E_NONE = -4096;  // block exponent of rows that are all zero (or absent)
@@ -130,6 +131,8 @@ struct OzArgs {
     unsigned long long *tc_flops;   // tensor-core flops issued, summed over CTAs (may be NULL)
     DevStatus *st;
 };
+
+__device__ __forceinline__ long long ntiles_all(const OzArgs &a) { return (long long)a.mt * a.nt; }
 
 // Highest level an output tile keeps (< 2: the tile is skipped); eref = E_A + E_B.
 template <int S, int BN>
@@ -219,6 +222,23 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         __syncthreads();
     }
     const int eref = emax_a + emax_b;
+    // the level cut of this CTA's tiles (the i-th tile it visits is L = blockIdx.x + i gridDim.x),
+    // computed once here so that no role waits on the exponent loads inside its tile loop
+    __shared__ uint8_t lc_tab[OZ_LC_CAP];
+    if (args.cut) {
+        const long long mine = (ntiles_all(args) - blockIdx.x + gridDim.x - 1) / gridDim.x;
+        for (int i = threadIdx.x; i < OZ_LC_CAP && i < mine; i += OZ_THREADS) {
+            int gr, gc, ar, br;
+            const long long L = blockIdx.x + (long long)i * gridDim.x;
+            lc_tab[i] = oz_tile<BN>(args, L, &gr, &gc, &ar, &br) ? (uint8_t)max(0, oz_lcut<S, BN>(args, ar, br, eref))
+                                                                 : (uint8_t)0;
+        }
+        __syncthreads();
+    }
+    auto tile_lc = [&](long long i, int ar, int br) -> int {
+        if (!args.cut) return S + 1;
+        return i < OZ_LC_CAP ? (int)lc_tab[i] : oz_lcut<S, BN>(args, ar, br, eref);
+    };
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const long long ntiles = (long long)args.mt * args.nt;
 
@@ -249,10 +269,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         if (lane == 0) {
             long long g = 0;   // chunks issued
             bool ok = true;
-            for (long long L = blockIdx.x; L < ntiles && ok; L += gridDim.x) {
+            for (long long L = blockIdx.x, it = 0; L < ntiles && ok; L += gridDim.x, ++it) {
                 int gr, gc, ar, br;
                 if (!oz_tile<BN>(args, L, &gr, &gc, &ar, &br)) continue;
-                const int lc = oz_lcut<S, BN>(args, ar, br, eref);
+                const int lc = tile_lc(it, ar, br);
 #pragma unroll
                 for (int ps = 0; ps < PASSES; ++ps) {
                     if (Cfg::lev_lo(ps) > lc) break;   // every level of this pass (and later ones) is cut
@@ -286,10 +306,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             for (int j = 0; j < NSLOT; ++j) use[j] = 0;
             unsigned long long nmma = 0;
             bool ok = true;
-            for (long long L = blockIdx.x; L < ntiles && ok; L += gridDim.x) {
+            for (long long L = blockIdx.x, it = 0; L < ntiles && ok; L += gridDim.x, ++it) {
                 int gr, gc, ar, br;
                 if (!oz_tile<BN>(args, L, &gr, &gc, &ar, &br)) continue;
-                const int lc = oz_lcut<S, BN>(args, ar, br, eref);
+                const int lc = tile_lc(it, ar, br);
 #pragma unroll
                 for (int ps = 0; ps < PASSES; ++ps) {
                     if (!ok || Cfg::lev_lo(ps) > lc) break;
@@ -355,10 +375,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const int row = q * 32 + lane;
         int job = 0;
         bool ok = true;
-        for (long long L = blockIdx.x; L < ntiles && ok; L += gridDim.x) {
+        for (long long L = blockIdx.x, it = 0; L < ntiles && ok; L += gridDim.x, ++it) {
             int gr, gc, ar, br;
             if (!oz_tile<BN>(args, L, &gr, &gc, &ar, &br)) continue;
-            const int lc = oz_lcut<S, BN>(args, ar, br, eref);
+            const int lc = tile_lc(it, ar, br);
             const int grow = gr + row;
             const int er = (grow < args.m_end) ? args.ea[ar + row] : 0;
 #pragma unroll

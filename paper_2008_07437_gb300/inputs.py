@@ -126,22 +126,22 @@ WORKLOADS = {
     "bivariate-n400": Workload("bivariate-n400", 400, THETA_FIG5, nb=128, loc_seed=1000, z_seed=2000),
     # 20,000 locations (N = 40,000), dense FP64 tiled Cholesky, 2,000 held-out locations to
     # predict; the trailing updates and panel solves emulated on the tensor cores with 8 digit
-    # slices (FP64-class accuracy), tile 512.
+    # slices (FP64-class accuracy), tile 512, with the magnitude-aware level cut.
     "bivariate-n20000": Workload("bivariate-n20000", 20000,
                                  ThetaSpec((1.0, 1.0), 0.03, (0.5, 1.5), (0.5,)),
                                  n_pred=2000, nb=512, loc_seed=1001, z_seed=2001,
-                                 extra={"fp64_gemm": 1, "oz_slices": 8}),
+                                 extra={"fp64_gemm": 1, "oz_slices": 8, "oz_cut": 1}),
     # The same with native FP64 FMA updates, tile 960.
     "bivariate-n20000-native": Workload("bivariate-n20000-native", 20000,
                                         ThetaSpec((1.0, 1.0), 0.03, (0.5, 1.5), (0.5,)),
                                         n_pred=2000, nb=960, loc_seed=1001, z_seed=2001),
     # 50,000 locations (N = 100,000), reduced precision: FP64 diagonal tiles, BF16 tensor cores
     # with a power-of-two scale per row and FP32 accumulation for every other tile, as 5 digit
-    # slices (about 35 bits per operand).
+    # slices (about 35 bits per operand), with the magnitude-aware level cut.
     "bivariate-n50000-mixed": Workload("bivariate-n50000-mixed", 50000,
                                        ThetaSpec((1.0, 1.0), 0.1, (0.5, 1.0), (0.7,)),
                                        nb=768, loc_seed=1002, z_seed=2002,
-                                       extra={"fp64_gemm": 1, "oz_slices": 5}),
+                                       extra={"fp64_gemm": 1, "oz_slices": 5, "oz_cut": 1}),
     # The FP32-class mixed form: FP64 diagonal tiles, FP32 band of 4 tiles, FP16 x 2 tensor cores
     # beyond, 2 refinement sweeps.
     "bivariate-n50000-fp16x2": Workload("bivariate-n50000-fp16x2", 50000,
