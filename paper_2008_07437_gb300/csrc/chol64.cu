@@ -36,8 +36,8 @@ __device__ __forceinline__ void set_info(DevStatus *st, int row1) {
 // Right-looking, two barriers per column: the rows below the pivot are scaled
 // by 1 / L_jj, then the rank-1 update runs with thread (row r, group g)
 // updating columns j + 1 + g, j + 5 + g, ...; the thread that updates the next
-// diagonal entry (it is the last to touch it) takes its square root and
-// reciprocal right away, so the pivot is ready at the next barrier.  The FP64
+// diagonal entry (the only one to touch it) takes its square root and
+// reciprocal right after its columns, so the pivot is ready at the next barrier.  The FP64
 // pipe (two FMAs per clock per SM) bounds the block at cb^3 / 6 FMAs; square
 // roots and divisions are taken once per column, not per thread.
 __global__ void __launch_bounds__(256) k_potrf_diag(double *A, long long ld, int c0, int cb, DevStatus *st) {

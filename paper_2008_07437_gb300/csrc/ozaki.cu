@@ -79,7 +79,7 @@ constexpr int OZ_KALIGN = 32;     // slice arrays: K padded to a multiple of 32 
 constexpr int OZ_EPI_WARPS = 8;
 constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;
 constexpr int OZ_TMEM_COLS = 512;
-constexpr int OZ_SMEM_CAP = 216 * 1024;   // the ring of K chunks; the rest holds the level-cut table
+constexpr int OZ_SMEM_CAP = 200 * 1024;   // the ring of K chunks; the rest: level-cut table, C staging
 constexpr int OZ_LC_CAP = 8192;           // tiles per CTA whose level cut is computed up front
 constexpr int OZ_GROUP = 8;       // row blocks swept together (operand reuse in L2)
 constexpr int OZ_LPW = 4;         // levels folded into one 64-bit word
@@ -133,6 +133,15 @@ struct OzArgs {
 };
 
 __device__ __forceinline__ long long ntiles_all(const OzArgs &a) { return (long long)a.mt * a.nt; }
+
+__device__ __forceinline__ void cp_async8(double *dst, const double *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // Highest level an output tile keeps (< 2: the tile is skipped); eref = E_A + E_B.
 template <int S, int BN>
@@ -225,6 +234,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     // the level cut of this CTA's tiles (the i-th tile it visits is L = blockIdx.x + i gridDim.x),
     // computed once here so that no role waits on the exponent loads inside its tile loop
     __shared__ uint8_t lc_tab[OZ_LC_CAP];
+    __shared__ __align__(16) double c_stage[OZ_EPI_WARPS * 2 * 4 * 32];   // epilogue: C columns in flight
     if (args.cut) {
         const long long mine = (ntiles_all(args) - blockIdx.x + gridDim.x - 1) / gridDim.x;
         for (int i = threadIdx.x; i < OZ_LC_CAP && i < mine; i += OZ_THREADS) {
@@ -375,6 +385,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const int row = q * 32 + lane;
         int job = 0;
         bool ok = true;
+        // C entries of this thread's row, CQ columns at a time, double-buffered through shared
+        // memory by cp.async: the copies for the next columns are in flight while the current
+        // ones are updated, and no register waits on a load of C
+        constexpr int CQ = 4;
+        double *cbuf = &c_stage[(warp - 2) * 2 * CQ * 32];
         for (long long L = blockIdx.x, it = 0; L < ntiles && ok; L += gridDim.x, ++it) {
             int gr, gc, ar, br;
             if (!oz_tile<BN>(args, L, &gr, &gc, &ar, &br)) continue;
@@ -418,19 +433,58 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 ++job;
                 if (grow < args.m_end) {
                     const bool over = args.overwrite && ps == 0;
-#pragma unroll
-                    for (int j = 0; j < CPT; ++j) {
+                    auto live_col = [&](int j) {
                         const int gcol = gc + h * CPT + j;
-                        if (gcol >= args.n_end || (args.tri && grow < gcol)) continue;
-                        const int e = er + args.eb[br + h * CPT + j];
-                        double *pc = args.C + (long long)gcol * args.ldc + grow;
-                        double c = over ? 0.0 : *pc;
+                        return gcol < args.n_end && !(args.tri && grow < gcol);
+                    };
+                    auto stage = [&](int j0, int b) {
 #pragma unroll
-                        for (int wi = WREG - 1; wi >= 0; --wi) {
-                            if (w0 + wi >= Cfg::NWT || 2 + OZ_LPW * (w0 + wi) > lc) continue;
-                            c = fma(-(double)acc[wi][j], pow2i(e + 2 - 7 * Cfg::word_hi(w0 + wi)), c);
+                        for (int jj = 0; jj < CQ; ++jj)
+                            if (live_col(j0 + jj))
+                                cp_async8(&cbuf[(b * CQ + jj) * 32 + lane],
+                                          args.C + (long long)(gc + h * CPT + j0 + jj) * args.ldc + grow);
+                        cp_async_commit();
+                    };
+                    if (!args.cut || over) {
+                        // every level kept: the MMAs, not these loads, set the pace
+#pragma unroll
+                        for (int j = 0; j < CPT; ++j) {
+                            if (!live_col(j)) continue;
+                            const int e = er + args.eb[br + h * CPT + j];
+                            double *pc = args.C + (long long)(gc + h * CPT + j) * args.ldc + grow;
+                            double c = over ? 0.0 : *pc;
+#pragma unroll
+                            for (int wi = WREG - 1; wi >= 0; --wi) {
+                                if (w0 + wi >= Cfg::NWT || 2 + OZ_LPW * (w0 + wi) > lc) continue;
+                                c = fma(-(double)acc[wi][j], pow2i(e + 2 - 7 * Cfg::word_hi(w0 + wi)), c);
+                            }
+                            *pc = c;
                         }
-                        *pc = c;
+                        continue;
+                    }
+                    stage(0, 0);
+#pragma unroll
+                    for (int j0 = 0; j0 < CPT; j0 += CQ) {
+                        const int b = (j0 / CQ) & 1;
+                        if (j0 + CQ < CPT) {
+                            stage(j0 + CQ, b ^ 1);
+                            cp_async_wait<1>();
+                        } else {
+                            cp_async_wait<0>();
+                        }
+#pragma unroll
+                        for (int jj = 0; jj < CQ; ++jj) {
+                            const int j = j0 + jj;
+                            if (!live_col(j)) continue;
+                            const int e = er + args.eb[br + h * CPT + j];
+                            double c = cbuf[(b * CQ + jj) * 32 + lane];
+#pragma unroll
+                            for (int wi = WREG - 1; wi >= 0; --wi) {
+                                if (w0 + wi >= Cfg::NWT || 2 + OZ_LPW * (w0 + wi) > lc) continue;
+                                c = fma(-(double)acc[wi][j], pow2i(e + 2 - 7 * Cfg::word_hi(w0 + wi)), c);
+                            }
+                            args.C[(long long)(gc + h * CPT + j) * args.ldc + grow] = c;
+                        }
                     }
                 }
             }
