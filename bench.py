@@ -928,8 +928,11 @@ def run_mle(args, w, ctx, d_locs, d_z, theta, o, dev):
     t_call = time.perf_counter()
     while len(records) < args.mle:
         if args.mle_budget_s > 0 and records:
-            longest = max(r["seconds"] for r in records)
-            if time.perf_counter() - t_call + longest > args.mle_budget_s:
+            # the first step evaluates the whole starting simplex: the later ones take one to a few
+            # evaluations (a rare shrink more, and the per-step checkpoint bounds what it can lose)
+            later = [r["seconds"] for r in records if r["step"] > 1]
+            guess = max(later) if later else records[0]["seconds"] / max(records[0]["evals"], 1) * 2
+            if time.perf_counter() - t_call + guess > args.mle_budget_s:
                 break
         t0 = time.perf_counter()
         ev0 = st.evals
