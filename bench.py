@@ -127,7 +127,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bivariate-n20000",
-                    choices=sorted(inputs.WORKLOADS) + ["serving", "batch", "mloe", "estimation"])
+                    choices=sorted(inputs.WORKLOADS) + ["serving", "batch", "mloe", "estimation", "gemm"])
     ap.add_argument("--n", type=int, default=0, help="override n (profiling runs on small cases only)")
     ap.add_argument("--n-pred", type=int, default=-1)
     ap.add_argument("--nb", type=int, default=0)
@@ -171,6 +171,8 @@ def parse():
                          "emulated-FP64 l of the same Z")
     ap.add_argument("--oracle-subset", type=int, default=0,
                     help="also compare l with the oracle on the first this-many locations (0 = off)")
+    ap.add_argument("--gemm-mnk", default="8192,8192,512", help="gemm: m,n,k of C -= A B' (FP64 emulated)")
+    ap.add_argument("--gemm-slices", type=int, default=8, help="gemm: digit slices")
     ap.add_argument("--oz-cut", type=int, default=-1, choices=[-1, 0, 1],
                     help="emulated FP64 workloads: magnitude-aware level cut in the trailing updates "
                          "(-1: the workload's setting)")
@@ -620,7 +622,8 @@ def run_ours(args):
            "roofline": {"bound": bound, "kernel": kname,
                         "achieved": dom_tflops, "peak": peak,
                         "unit": "TFLOP/s", "frac": dom_tflops / peak, "peak_source": peak_src,
-                        "traffic": traffic, "fp64_equivalent_tflops": fp64eq_tflops},
+                        "traffic": traffic, "fp64_equivalent_tflops": fp64eq_tflops,
+                        "algorithmic_bytes_per_launch": dk["bytes"] / max(dk["launches"], 1)},
            "gpu_launches": launches,
            "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
            "quality": {"loglik": ll, "mspe": mspe},
@@ -1353,8 +1356,65 @@ def run_serving_reference(args):
     return 0
 
 
+def run_gemm(args):
+    """The emulated FP64 product alone (the GEMM tile task of Sec. 5.1 as one call):
+    C (m x n) -= A (m x k) B (n x k)' through geo_gemm_f64e, inputs resident, CUDA events."""
+    import torch
+
+    import paper_2008_07437_gb300 as geo
+    from paper_2008_07437_gb300 import build as gbuild
+    gbuild.build()
+    torch.cuda.set_device(0)
+    m, n, k = (int(x) for x in args.gemm_mnk.split(","))
+    S = args.gemm_slices
+    ctx = geo.geo_create(0)
+    g = torch.Generator(device="cuda").manual_seed(1)
+    A = torch.randn((k, m), dtype=torch.float64, device="cuda", generator=g).t()
+    B = torch.randn((k, n), dtype=torch.float64, device="cuda", generator=g).t()
+    C = torch.zeros((n, m), dtype=torch.float64, device="cuda").t()
+    for _ in range(args.warmup):
+        geo.geo_gemm_f64e(ctx, A, B, C, slices=S)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    geo.geo_profile_enable(ctx, True)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        geo.geo_gemm_f64e(ctx, A, B, C, slices=S)
+    ev1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    tc = geo.geo_profile_read(ctx)["tcgemm"]
+    geo.geo_profile_enable(ctx, False)
+    fl = 2.0 * m * n * k
+    kernel_ms = tc["ms"] / args.steps
+    bound, peak, peak_src = class_roofline("tcgemm")
+    tensor = tc["tensor_flops"] / args.steps / (kernel_ms * 1e-3) / 1e12
+    out = {"metric": "emulated FP64 GEMM FP64-equivalent TFLOP/s", "value": fl / (ms * 1e-3) / 1e12,
+           "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64 (emulated: bf16 digit products, exact fp32 accumulation, %d slices)" % S,
+           "data": "synthetic", "config": {"workload": "gemm", "m": m, "n": n, "k": k, "slices": S,
+                                           "l2": "C (%.2f GB) larger than L2" % (8.0 * m * n / 1e9)},
+           "roofline": {"bound": bound, "kernel": KERNEL_NAMES["oz"], "achieved": tensor, "peak": peak,
+                        "unit": "TFLOP/s", "frac": tensor / peak, "peak_source": peak_src, "traffic": None,
+                        "kernel_ms": kernel_ms, "fp64_equivalent_tflops": fl / (kernel_ms * 1e-3) / 1e12,
+                        "algorithmic_bytes_per_launch": tc["bytes"] / max(tc["launches"], 1)},
+           "gpu_launches": sum(v["launches"] for v in geo.geo_profile_read(ctx).values()), "clocks": clk}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "gemm":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "gemm mode: a kernel benchmark, no CPU arm"}))
+            return 0
+        return run_gemm(args)
     if args.workload == "serving":
         return run_serving_reference(args) if args.impl == "reference" else run_serving(args)
     if args.workload == "mloe":
