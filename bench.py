@@ -609,7 +609,11 @@ def run_ours(args):
     # (N = 8,000) measured 0.822 x the algorithmic bytes; scaled to this run's
     # average launch (FP64 update kernel only)
     traffic = 0.822 * dk["bytes"] / max(dk["launches"], 1) if dom == "gemm" and not tlr else None
-    # k_oz_update: no DRAM counters of the current kernel yet (null until a capture is taken)
+    if dom == "tcgemm" and emulated and w.extra.get("oz_cut"):
+        # k_oz_update with the level cut: an ncu capture of every launch of one evaluation at
+        # N = 16,000 measured DRAM read + write = 0.967 x the algorithmic bytes the library counts
+        # (16 B per output written, the digit slices); scaled to this run's launches
+        traffic = 0.967 * dk["bytes"] / max(dk["launches"], 1)
     dtype = "f64"
     if emulated:
         dtype = "f64 (emulated: bf16 digit products, exact fp32 accumulation, %d slices)" % w.extra.get("oz_slices", 8)
