@@ -59,7 +59,12 @@
 //   warps 2-9: epilogue; tcgen05.ld of each level, releasing that
 //     accumulator slot as soon as it is read (the MMAs of the next pass or
 //     tile may start into it while the epilogue folds the values in
-//     registers), then the FP64 read-modify-write of C.
+//     registers), then the FP64 read-modify-write of C (with the level cut,
+//     C comes through shared memory by cp.async, four columns at a time,
+//     double-buffered, so that no register waits on a load of C).
+// With the level cut each CTA first computes the cut of all its tiles into a
+// shared-memory table, and the MMA thread counts the products it issues
+// (the device-side tensor work of the profile).
 // Every mbarrier wait is bounded; on expiry the thread records a code in the
 // status word, the CTA drains what it has in flight, frees TMEM and returns.
 #include <cuda.h>
