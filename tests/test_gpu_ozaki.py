@@ -369,6 +369,21 @@ def test_emulated_not_positive_definite_reports_and_recovers(ctx):
     assert got == pytest.approx(ref.loglik, rel=1e-10)
 
 
+def test_mloe_mmom_level_cut_equals_native(ctx):
+    # a short range at N = 4,000: the cut drops levels of the far tiles in both factorisations; the
+    # m cross-covariance rows ride along as right-hand-side rows and keep every level
+    n, m = 2000, 30
+    allp = inputs.jittered_grid(n + m, 67)
+    locs, pred = allp[:n], allp[n:]
+    tht = geo.Theta((1.0, 1.0), 0.03, (0.5, 1.5), 0.5)
+    tha = geo.Theta((1.1, 0.9), 0.036, (0.45, 1.35), 0.4)
+    a = geo.geo_mloe_mmom(ctx, dev(locs), dev(pred), tht, tha, geo.opts(nb=256))
+    b = geo.geo_mloe_mmom(ctx, dev(locs), dev(pred), tht, tha, emu(256, oz_cut=1))
+    assert b[0] == pytest.approx(a[0], rel=1e-9, abs=1e-13)
+    assert b[1] == pytest.approx(a[1], rel=1e-9, abs=1e-13)
+    np.testing.assert_allclose(b[2], a[2], rtol=1e-8, atol=1e-12)
+
+
 def test_mloe_mmom_emulated_equals_native(ctx):
     n, m = 300, 20
     allp = inputs.jittered_grid(n + m, 61)
