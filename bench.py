@@ -609,10 +609,11 @@ def run_ours(args):
     # (N = 8,000) measured 0.822 x the algorithmic bytes; scaled to this run's
     # average launch (FP64 update kernel only)
     traffic = 0.822 * dk["bytes"] / max(dk["launches"], 1) if dom == "gemm" and not tlr else None
-    if dom == "tcgemm" and emulated and w.extra.get("oz_cut"):
+    if dom == "tcgemm" and emulated and w.extra.get("oz_cut") and w.extra.get("oz_slices", 8) == 8:
         # k_oz_update with the level cut: an ncu capture of every launch of one evaluation at
         # N = 16,000 measured DRAM read + write = 0.967 x the algorithmic bytes the library counts
-        # (16 B per output written, the digit slices); scaled to this run's launches
+        # (16 B per output written, the digit slices); scaled to this run's launches (8 slices, the
+        # captured kernel; other slice counts have no capture: null)
         traffic = 0.967 * dk["bytes"] / max(dk["launches"], 1)
     dtype = "f64"
     if emulated:

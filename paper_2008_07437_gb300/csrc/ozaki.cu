@@ -638,20 +638,28 @@ cudaError_t launch_oz_kernel(const CUtensorMap &ma, const CUtensorMap &mb, const
 // with 6 or more slices the 128-column tile in passes of four levels keeps the
 // tensor pipe busiest (8 slices: 1,290 against 1,063 TFLOP/s of BF16 work for
 // the single-pass 64-column tile); with fewer the passes get short and the
-// 64-column single pass wins (5 slices: 902 against 655).
+// 64-column single pass wins (5 slices: 902 against 655).  With the level cut
+// at 5 slices the 128-column tile wins again: the second pass (the last
+// level) is cut on most tiles, so the epilogue, which sets the pace of cut
+// tiles, works on half as many C entries per MMA (N = 100,000: 4.3 against
+// 5.8 s per factorisation).
 struct OzShape {
     int bn, bk;
 };
 
-OzShape oz_shape(int S) { return S >= 6 ? OzShape{128, 16} : OzShape{64, 32}; }
+OzShape oz_shape(int S, int cut) { return (S >= 6 || (S == 5 && cut)) ? OzShape{128, 16} : OzShape{64, 32}; }
 
 template <int S>
 cudaError_t launch_oz_shape(OzShape sh, const CUtensorMap &ma, const CUtensorMap &mb, const OzArgs &a, int grid,
                             cudaStream_t s) {
-    if constexpr (S >= 6)
+    if constexpr (S >= 6) {
         return launch_oz_kernel<S, 128, 16>(ma, mb, a, grid, s);
-    else
+    } else if constexpr (S == 5) {
+        if (sh.bn == 128) return launch_oz_kernel<S, 128, 16>(ma, mb, a, grid, s);
         return launch_oz_kernel<S, 64, 32>(ma, mb, a, grid, s);
+    } else {
+        return launch_oz_kernel<S, 64, 32>(ma, mb, a, grid, s);
+    }
 }
 
 // 3-D tensor map over the slices: (k, row, slice), box bk x rows_box x 1,
@@ -726,7 +734,7 @@ cudaError_t oz_update(const OzSlices &A, const OzSlices &B, double *C, long long
     a.c0 = c0;
     a.m_end = m_end;
     a.n_end = n_end;
-    const OzShape sh = oz_shape(S);
+    const OzShape sh = oz_shape(S, cut);
     a.mt = (rows + OZ_BM - 1) / OZ_BM;
     a.nt = (cols + sh.bn - 1) / sh.bn;
     a.tri = tri;
