@@ -81,3 +81,23 @@ def test_mle_checkpoint_round_trip(tmp_path):
     st2, recs2 = bench._mle_load(path, geo)
     assert bytes(st2) == bytes(st) and recs2 == recs
     assert st2.evals == 17 and st2.iter == 3
+
+
+def test_workload_overrides_for_the_emulated_form():
+    """--oz-cut switches the level cut of the emulated workloads (and names the variant);
+    the configuration the bench prints says which form ran."""
+    sys.path.insert(0, ROOT)
+    import argparse
+
+    import bench
+    base = dict(workload="bivariate-n20000", n=0, n_pred=-1, nb=0, tlr_tol=0.0, dst=0, oz_cut=-1,
+                tlr_z="model")
+    w = bench.workload(argparse.Namespace(**base))
+    assert w.extra.get("oz_cut") == 1 and w.extra.get("oz_slices") == 8
+    assert "level cut" in bench.config_json(w, argparse.Namespace(**base))["form"]
+    w0 = bench.workload(argparse.Namespace(**dict(base, oz_cut=0)))
+    assert w0.name.endswith("-nocut") and w0.extra["oz_cut"] == 0
+    assert "level cut" not in bench.config_json(w0, argparse.Namespace(**base))["form"]
+    # the native form has no cut to switch
+    wn = bench.workload(argparse.Namespace(**dict(base, workload="bivariate-n20000-native", oz_cut=1)))
+    assert "oz_cut" not in wn.extra and "fp64_gemm" not in wn.extra
