@@ -260,6 +260,16 @@ void geo_factor_free(geo_factor *factor);
 int geo_morton_order(const double *locs_host, int n, int *perm_host);
 
 /*
+ * Layout check for bindings (host only, no device): writes up to n values to
+ * out (host): the sizes in bytes of geo_theta, geo_opts, geo_factor_stats,
+ * geo_mle_state, geo_batch_item, geo_request, geo_result and geo_kstat, then
+ * the offsets of geo_opts.oz_slices, geo_opts.oz_cut and
+ * geo_kstat.tensor_flops.  Returns the number of values the library has
+ * (11), or GEO_EINVAL for a NULL out with n > 0.
+ */
+int geo_abi_layout(long long *out, int n);
+
+/*
  * Maximum likelihood by the Nelder-Mead simplex method (the paper maximises
  * Eq. 1 with NLopt, Sec. 5.1; the algorithm is not named).  The state is a
  * plain host struct owned by the caller: it can be copied, saved and

@@ -110,6 +110,7 @@ SIGNATURES = {
     "geo_factor_read": (_I, [_P, _I, _LL, _LL, _LL, _LL, _P]),
     "geo_factor_free": (None, [_P]),
     "geo_morton_order": (_I, [_P, _I, _P]),
+    "geo_abi_layout": (_I, [_P, _I]),
     "geo_mle_init": (_I, [ctypes.POINTER(geo_mle_state), ctypes.POINTER(geo_theta), _D]),
     "geo_mle_init_profile": (_I, [ctypes.POINTER(geo_mle_state), ctypes.POINTER(geo_theta), _D]),
     "geo_sigma2_hat": (_I, [_P, _P, _I, _P, ctypes.POINTER(geo_theta), ctypes.POINTER(geo_opts), _P,

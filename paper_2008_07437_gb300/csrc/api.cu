@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstdio>
 #include <map>
 #include <mutex>
@@ -1616,6 +1617,19 @@ int geo_profile_read(geo_ctx *ctx, geo_kstat *out) {
         CK(cudaMemcpy(&tc, ctx->prof.d_tc_flops, sizeof(tc), cudaMemcpyDeviceToHost));
     out[GEO_K_TCGEMM].tensor_flops = (double)tc;
     return GEO_OK;
+}
+
+int geo_abi_layout(long long *out, int n) {
+    const long long v[] = {(long long)sizeof(geo_theta),        (long long)sizeof(geo_opts),
+                           (long long)sizeof(geo_factor_stats), (long long)sizeof(geo_mle_state),
+                           (long long)sizeof(geo_batch_item),   (long long)sizeof(geo_request),
+                           (long long)sizeof(geo_result),       (long long)sizeof(geo_kstat),
+                           (long long)offsetof(geo_opts, oz_slices), (long long)offsetof(geo_opts, oz_cut),
+                           (long long)offsetof(geo_kstat, tensor_flops)};
+    const int count = (int)(sizeof(v) / sizeof(v[0]));
+    if (n > 0 && !out) return GEO_EINVAL;
+    for (int k = 0; k < n && k < count; ++k) out[k] = v[k];
+    return count;
 }
 
 int geo_morton_order(const double *locs_host, int n, int *perm_host) {

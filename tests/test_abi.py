@@ -135,3 +135,18 @@ def test_noalloc_wrapper_checks_shapes_before_any_launch():
         geo.geo_loglik_noalloc(locs, z, th, out, torch.zeros(1, dtype=torch.int64))
     with pytest.raises(TypeError, match="CUDA"):
         geo.geo_loglik_noalloc(locs, z, th, out, info)
+
+
+def test_struct_layouts_match_the_library(lib):
+    """The ctypes structures of the binding have the sizes and field offsets of the C ABI."""
+    import ctypes
+    out = (ctypes.c_longlong * 16)()
+    count = lib.geo_abi_layout(out, 16)
+    assert count == 11
+    py = [ctypes.sizeof(geo.geo_theta), ctypes.sizeof(geo.geo_opts), ctypes.sizeof(geo.geo_factor_stats),
+          ctypes.sizeof(geo.geo_mle_state), ctypes.sizeof(geo.geo_batch_item), ctypes.sizeof(geo.geo_request),
+          ctypes.sizeof(geo.geo_result), ctypes.sizeof(geo.geo_kstat),
+          geo.geo_opts.oz_slices.offset, geo.geo_opts.oz_cut.offset, geo.geo_kstat.tensor_flops.offset]
+    assert list(out[:count]) == py
+    assert lib.geo_abi_layout(None, 0) == 11
+    assert lib.geo_abi_layout(None, 3) == geo.GEO_EINVAL
