@@ -5,7 +5,8 @@ Default workload "bivariate-n20000": the parsimonious bivariate Matern model
 at n = 20,000 jittered-grid locations (N = 40,000), theta = (1, 1, 0.03, 0.5,
 1.5, 0.5), dense FP64 tiled Cholesky (tile 512) whose trailing updates and
 panel solves run emulated on the BF16 tensor cores (8 digit slices, FP64-class
-accuracy), plus cokriging of 2,000 held-out locations.  One step = one full
+accuracy, with the magnitude-aware level cut: ``--oz-cut 0`` turns it off),
+plus cokriging of 2,000 held-out locations.  One step = one full
 evaluation: Eq. 2 covariance generation, tiled Cholesky, L^-1 Z,
 log-determinant and Eq. 1, backward solve and the Eq. 3 predictor at the
 2,000 new locations.  Inputs are synthetic: locations from a seeded jittered
@@ -16,6 +17,12 @@ updates is timed once beside it (``fp64_dense``: time, l and |dl| / |l|).
 Output: one JSON line (rank 0).  ``--impl reference`` times the CPU FP64
 oracle on a bounded sample of the same workload instead (this repository has
 no other reference implementation: the paper ships no code).
+
+Other workloads (``--workload``): the reduced form at N = 100,000
+(bivariate-n50000-mixed), tile low rank at N = 180,000 (trivariate-n60000-tlr;
+``--mle K`` runs K Nelder-Mead steps instead, ``--mle-checkpoint F`` saves the
+state after every step and resumes from F), serving, batch (also batched
+cokriging), mloe, gemm (the emulated FP64 product alone).
 
 Multi-GPU: one process per GPU under torchrun; each rank evaluates its own
 replica (independent likelihood evaluations, no collective on the data path);
