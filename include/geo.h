@@ -194,15 +194,15 @@ int geo_predict(geo_ctx *ctx, const geo_factor *factor, const double *new_locs_d
                 void *stream);
 
 /*
- * Batched cokriging (Eq. 3 / Eq. 4) on many kept factors in one launch: entry k
+ * Batched cokriging (Eq. 3 / Eq. 4) on many factors kept by this context, in one launch: entry k
  * predicts the m[k] new locations new_locs_dev[k] (m[k] x 2, device) on
  * factors[k] into zhat_dev[k] (p m[k] doubles, device, Representation I),
  * exactly as geo_predict would (bit-identical).  Factors of any forms, sizes
  * and theta may be mixed; each factor's weights Sigma^-1 Z are computed on its
  * first prediction, as in geo_predict.  The work is enqueued on `stream`
  * (the descriptors are staged in pinned memory of the context: the call waits
- * for the stream's previous work before reusing them).  GEO_EINVAL for a bad
- * entry (named in geo_last_error).
+ * for the stream's previous work before reusing them).  The zhat_dev buffers
+ * must not overlap.  GEO_EINVAL for a bad entry (named in geo_last_error).
  */
 int geo_predict_batch(geo_ctx *ctx, int count, const geo_factor *const *factors, const double *const *new_locs_dev,
                       const int *m, double *const *zhat_dev, void *stream);
