@@ -316,7 +316,17 @@ def oracle_full_config0():
     t0 = time.perf_counter()
     r = oracle.loglik(th, locs, Z)
     t = time.perf_counter() - t0
-    return {"workload": w0.name, "N": spec.p * w0.n, "seconds": t, "evals_per_s": 1.0 / t, "loglik": r.loglik}
+    # the same on one core
+    cores = oracle.num_threads()
+    oracle.set_threads(1)
+    try:
+        t1 = time.perf_counter()
+        oracle.loglik(th, locs, Z)
+        t_one = time.perf_counter() - t1
+    finally:
+        oracle.set_threads(cores)
+    return {"workload": w0.name, "N": spec.p * w0.n, "seconds": t, "evals_per_s": 1.0 / t, "loglik": r.loglik,
+            "cores": cores, "seconds_1_core": t_one}
 
 
 def cpu_baseline_json(w, n_s, m_s, t_full, det, cores):
