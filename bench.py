@@ -329,8 +329,26 @@ def oracle_full_config0():
             "cores": cores, "seconds_1_core": t_one}
 
 
+def host_cpu() -> str:
+    """The host's architecture and CPU model (the model name where the kernel reports one, else the
+    implementer / part codes of an Arm core)."""
+    import platform
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    model = fields.get("model name") or ("implementer %s part %s" % (fields.get("CPU implementer", "?"),
+                                                                     fields.get("CPU part", "?")))
+    return "%s, %s, %d logical CPUs" % (platform.machine(), model, os.cpu_count() or 0)
+
+
 def cpu_baseline_json(w, n_s, m_s, t_full, det, cores):
-    return {"value": 1.0 / t_full, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": 1.0 / t_full, "unit": UNIT, "cores": cores, "kind": "oracle", "host": host_cpu(),
             "extrapolated": True, "sample_N": w.theta.p * det["n_sample"], "sample_m": det["m_sample"],
             "sample_seconds": det["sample_s"],
             "sample": ("oracle (C, OpenMP, FP64) on the first %d observed + %d held-out locations "
